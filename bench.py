@@ -1,0 +1,327 @@
+"""Benchmark of the X stage (cross-multiply-accumulate) on GB300.
+
+Workload (the streamed real-time correlator): 64 inputs (32 dual-pol antennas), 768
+channels, 1000 samples per dump, 200 dumps, complex 8-bit Gaussian samples (sigma 16,
+clipped to +-127) with a common correlated component rho = 0.1, generated on the device
+from a seeded generator.  One step = the whole job: all 200 dumps through the library's
+X stage (unpack + tensor-core cross-multiply-accumulate + int64 dump), one batched call.
+
+Printed on rank 0 as one JSON line:
+  value        TeraCMAC/s of the whole job, inputs resident in HBM, device-timed
+  e2e          same metric through the C ABI with host (pinned) buffers: H2D of the packed
+               samples and D2H of the visibilities inside the timed region
+  fp32_path    the CUDA-core FP32 engine on the same job, and value / fp32 value
+  roofline     the dominant kernel against measured HBM bandwidth
+  cpu_baseline the CPU oracle on a bounded sample of the same workload
+Options: --gpus N (torchrun, one rank per GPU, weak scaling: every rank runs the whole
+job on its own GPU), --steps K, --warmup W, --impl reference (the CPU oracle arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_INPUTS, N_CHAN, N_TIME, N_DUMPS, BITS = 64, 768, 1000, 200, 8
+SIGMA, RHO, SEED = 16.0, 0.1, 2000
+CHANNEL_RATE_HZ = 1.28e6 / 128.0
+WORKLOAD = "stream64_8bit: 64 inputs x 768 channels x 1000 samples/dump x 200 dumps, 8-bit complex Gaussian sigma=16 rho=0.1"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The C oracle (OpenMP over the host's cores) on a bounded channel sample of the workload."""
+    import numpy as np
+
+    import oracle
+    from paper_0906_1887_gb300 import synth
+    re, im = synth.correlated_gaussian(SEED, N_TIME, 64, N_INPUTS, SIGMA, RHO, 127)
+    packed = synth.pack(re, im, BITS)
+    threads = oracle.threads_used(0)
+    n = 2
+    while True:
+        chans = np.arange(n, dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.xcorr_int(packed, N_INPUTS, 64, N_TIME, BITS, chans=chans)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or n >= 64:
+            break
+        n = min(64, max(n * 2, int(n * target_s / 4 / max(dt, 1e-3))))
+    cm = N_INPUTS * (N_INPUTS + 1) // 2 * n * N_TIME
+    return {"value": cm / dt / 1e12, "unit": "TeraCMAC/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} of 768 channels of one 1000-sample dump (64 inputs, 8-bit), numpy PCG64 seed {SEED}",
+            "seconds": dt}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_0906_1887_gb300 import synth
+    re, im = synth.correlated_gaussian(SEED, N_TIME, 64, N_INPUTS, SIGMA, RHO, 127)
+    packed = synth.pack(re, im, BITS)
+    chans = np.arange(16, dtype=np.int32)        # a bounded sample of the job per step
+    threads = oracle.threads_used(0)
+    for _ in range(args.warmup):
+        oracle.xcorr_int(packed, N_INPUTS, 64, N_TIME, BITS, chans=chans[:2])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.xcorr_int(packed, N_INPUTS, 64, N_TIME, BITS, chans=chans)
+    dt = (time.perf_counter() - t0) / args.steps
+    cm = N_INPUTS * (N_INPUTS + 1) // 2 * len(chans) * N_TIME
+    v = cm / dt / 1e12
+    line = {"metric": "X-engine TeraCMAC/s", "value": v, "unit": "TeraCMAC/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": "16 channels of one dump"},
+            "cpu_baseline": {"value": v, "unit": "TeraCMAC/s", "cores": threads, "kind": "oracle",
+                             "sample": "16 of 768 channels of one 1000-sample dump per step"},
+            "e2e": {"value": v, "unit": "TeraCMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    corr.lib()
+    plan = corr.Plan(N_INPUTS, N_CHAN, N_TIME, BITS)
+    P = plan.n_baselines
+    packed = synth.torch_correlated_gaussian_packed8(N_DUMPS, N_TIME, N_CHAN, N_INPUTS, SIGMA, RHO,
+                                                     SEED + 7919 * rank, dev)
+    vis = plan.empty_vis(N_DUMPS, dev)
+    ws = plan.empty_workspace(corr.ENGINE_TC, N_DUMPS, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step_tc():
+        plan.run(packed, vis, ws, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
+
+    # warm-up
+    for _ in range(args.warmup):
+        step_tc()
+    barrier()
+    if plan.check_device() != 0:
+        raise RuntimeError("device-side wait gave up during warm-up")
+
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    time.sleep(0.3)
+    # device-timed region: K whole-job steps (inputs 19.7 GB >> L2, no flush needed)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_tc()
+    ev1.record(stream)
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    # per-kernel split (same stream): unpack alone and cross-multiply alone
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    kms_unpack, kms_x = [], []
+    for _ in range(max(2, args.steps // 2)):
+        e[0].record(stream)
+        plan.unpack(packed, ws, n_dumps=N_DUMPS, stream=stream)
+        e[1].record(stream)
+        plan.run_planes(ws, vis, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        kms_unpack.append(e[0].elapsed_time(e[1]))
+        kms_x.append(e[1].elapsed_time(e[2]))
+    clk = clocks.stop()
+    if plan.check_device() != 0:
+        raise RuntimeError("device-side wait gave up in the timed region")
+
+    ms_step = max_over_ranks(ms_total / args.steps)
+    cm_step = P * N_CHAN * N_TIME * N_DUMPS
+    value = cm_step * world / (ms_step / 1e3) / 1e12
+    rtf = (N_TIME * N_DUMPS / CHANNEL_RATE_HZ) / (ms_step / 1e3)
+
+    # FP32 CUDA-core engine on the same job
+    ws32 = ws  # same plane layout and size for integer samples
+    for _ in range(1):
+        plan.run(packed, vis, ws32, engine=corr.ENGINE_FP32, n_dumps=N_DUMPS, stream=stream)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.fp32_steps):
+        plan.run(packed, vis, ws32, engine=corr.ENGINE_FP32, n_dumps=N_DUMPS, stream=stream)
+    ev1.record(stream)
+    barrier()
+    ms32 = max_over_ranks(ev0.elapsed_time(ev1) / args.fp32_steps)
+    value32 = cm_step * world / (ms32 / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers: H2D packed, run, D2H visibilities
+    host_in = torch.empty(packed.shape, dtype=torch.uint8, pin_memory=True)
+    host_in.copy_(packed)
+    host_out = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+    dev_in = torch.empty_like(packed)
+    for _ in range(1):
+        dev_in.copy_(host_in, non_blocking=True)
+        plan.run(dev_in, vis, ws, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
+        host_out.copy_(vis, non_blocking=True)
+    barrier()
+    e2e_steps = max(1, min(args.steps, 3))
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        dev_in.copy_(host_in, non_blocking=True)
+        plan.run(dev_in, vis, ws, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
+        host_out.copy_(vis, non_blocking=True)
+    ev1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / e2e_steps)
+    e2e_value = cm_step * world / (ms_e2e / 1e3) / 1e12
+    del dev_in, host_in
+
+    # roofline of the dominant kernel: the cross-multiply over fp16 planes is HBM-bound here
+    hbm_peak, bf16_peak, peak_src = _peaks()
+    ms_x = statistics.median(kms_x)
+    ms_u = statistics.median(kms_unpack)
+    kp = (N_TIME + 63) // 64 * 64
+    x_bytes = N_DUMPS * N_CHAN * (128 * kp * 2 + P * 16)            # planes read + int64 dump written
+    x_gbs = x_bytes / (ms_x / 1e3) / 1e9
+    flops = 8.0 * cm_step
+    roofline = {"bound": "hbm", "kernel": "xeng_tc_kernel", "achieved": x_gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": x_gbs / hbm_peak, "traffic": None,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                "tensor_tflops": flops / (ms_x / 1e3) / 1e12, "tensor_frac_of_bf16_burst": flops / (ms_x / 1e3) / 1e12 / bf16_peak,
+                "kernel_ms": ms_x, "unpack_ms": ms_u,
+                "algorithmic_bytes_per_launch": x_bytes}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": "X-engine TeraCMAC/s", "value": value, "unit": "TeraCMAC/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME,
+                   "n_dumps": N_DUMPS, "sample_bits": BITS, "engine": "tcgen05 fp16 operands, fp32 accum, exact int64",
+                   "l2": "inputs (19.7 GB per step) far larger than L2; no flush", "parallelism": f"replicas{world}"},
+        "real_time_factor": rtf,
+        "fp32_path": {"value": value32, "unit": "TeraCMAC/s", "ms_per_step": ms32, "speedup_tc_over_fp32": value / value32},
+        "e2e": {"value": e2e_value, "unit": "TeraCMAC/s", "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": int(packed.numel()), "d2h_bytes_per_step": int(vis.numel() * vis.element_size())},
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

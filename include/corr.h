@@ -1,0 +1,166 @@
+/*
+ * corr.h -- C ABI of the GB300 X-stage correlator library (libcorr.so).
+ *
+ * The X stage of an FX correlator (Wayth, Greenhill & Briggs, Sec. 2): for every
+ * frequency channel c and every input pair i <= j (N(N+1)/2 products including the
+ * N autos, Sec. 2), multiply the first spectrum by the complex conjugate of the
+ * second and add the product into an accumulator over the samples of one dump:
+ *
+ *     V_ij(c) = sum_t x_i(c,t) * conj(x_j(c,t))
+ *
+ * The matrix over (i, j) is the outer product of one channel's sample vector with
+ * its conjugate (Sec. 4, Fig. 2); its lower half is the conjugate of the upper half,
+ * so only i <= j is formed and stored.  The problem is stated by the number of
+ * inputs N_I, the number of channels N_C, the samples per batch and the sample mode
+ * (Sec. 4 and Sec. 5); corr_plan_create takes exactly these.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Packed input, one dump:   [n_time][n_chan][n_inputs] complex samples, input index
+ *                            fastest (Sec. 3: the samples of one time instant are
+ *                            grouped together; the F stage has already produced the
+ *                            channel axis).
+ *      sample_bits = 4 : 1 byte per sample, high nibble = re, low nibble = im, two's
+ *                        complement in [-8, 7] (the "1-byte mode" of Sec. 5).
+ *      sample_bits = 8 : 2 bytes per sample, re byte then im byte, int8 [-128, 127].
+ *      sample_bits = 32: 8 bytes per sample, float32 re then float32 im.
+ *  Visibilities, one dump:   [n_chan][P][2], P = N(N+1)/2, baseline
+ *                            b(i,j) = i*N - i*(i-1)/2 + (j - i) for i <= j (row-major
+ *                            upper triangle), last axis (re, im).  int64 for 4/8-bit
+ *                            samples (exact sums), float32 for float samples.
+ *  Several dumps:            dumps are consecutive in memory, packed input
+ *                            [n_dumps][T][C][N], visibilities [n_dumps][C][P][2].
+ *  Pointers:                 d_* arguments are device pointers (or pointers the GPU
+ *                            can dereference), 16-byte aligned; the caller owns them
+ *                            and the library never frees them.
+ *  Streams:                  `stream` is a cudaStream_t passed as void* (NULL = the
+ *                            legacy default stream).  Every run call is asynchronous
+ *                            on that stream.
+ *  Errors:                   every call returns a corr_status and never aborts;
+ *                            corr_last_error() gives the calling thread's last message.
+ *                            Launch-time CUDA errors return CORR_ECUDA; faults that
+ *                            surface later appear at the caller's next synchronise.
+ *                            Device-side bounded waits that give up are recorded in
+ *                            the plan and reported by corr_plan_check().
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CORR_OK = 0,
+    CORR_EINVAL = 1,       /* invalid argument, size or pointer                        */
+    CORR_ENOMEM = 2,       /* device or host allocation failed                         */
+    CORR_ECUDA = 3,        /* a CUDA runtime/driver call failed                        */
+    CORR_EBUSY = 4,        /* not admitted: the job does not fit the HBM budget now    */
+    CORR_ETIMEOUT = 5,     /* a bounded device or host wait gave up                    */
+    CORR_PENDING = 6,      /* corr_poll: the job has not finished yet                  */
+    CORR_EUNSUPPORTED = 7  /* engine/sample-mode combination not provided              */
+} corr_status;
+
+typedef enum {
+    /* Tensor-core X stage (tcgen05 MMA, accumulators in tensor memory).  Integer
+     * samples run exactly: 4/8-bit values are exact in fp16 and the fp32 partial
+     * sums stay below 2^24 within each flushed time chunk, so the int64 result is
+     * bit-identical to the definition.  Not valid for float samples. */
+    CORR_ENGINE_TC = 0,
+    /* CUDA-core FP32 X stage (the plain form).  Exact for integer samples (time
+     * chunks flushed to int64); fp32 arithmetic with two-level summation for float
+     * samples. */
+    CORR_ENGINE_FP32 = 1,
+    /* Float samples on the tensor cores: x = h + l with h = bf16(x),
+     * l = bf16(x - h); V ~= h h^H + h l^H + l h^H with fp32 accumulation. */
+    CORR_ENGINE_BF16X3 = 2
+} corr_engine;
+
+typedef struct corr_plan_s *corr_plan;   /* opaque, owned by the library */
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int corr_version(void);
+
+/* Last error message of the calling thread ("" if none).  Valid until the next call
+ * on this thread. */
+const char *corr_last_error(void);
+
+/*
+ * Create a plan for n_inputs inputs (N_I, >= 1), n_chan channels (N_C, >= 1),
+ * n_time samples per dump (>= 1) and a sample mode (4, 8 or 32).  The paper's
+ * prototype is n_inputs = 64 (32 antennas x 2 polarisations), n_chan = 128
+ * (Sec. 4, Sec. 5).  Allocates a small device status block on the current device.
+ * Errors: CORR_EINVAL on bad sizes/modes or an out-of-range problem (N <= 8192,
+ * products that would overflow 64-bit indexing); CORR_ENOMEM, CORR_ECUDA.
+ */
+corr_status corr_plan_create(corr_plan *out, int n_inputs, int n_chan, int n_time, int sample_bits);
+
+/* Destroy a plan (waits for nothing; the caller must have synchronised its work). */
+corr_status corr_plan_destroy(corr_plan plan);
+
+/* Sizes of one dump: number of baselines P, bytes of the packed input and of the
+ * visibilities.  Any output pointer may be NULL. */
+corr_status corr_plan_info(corr_plan plan, int64_t *n_baselines, size_t *packed_bytes, size_t *vis_bytes);
+
+/* Device workspace (bytes) corr_xengine_run_batch needs for `engine` and n_dumps
+ * dumps.  0 means the engine needs none (d_workspace may be NULL). */
+corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t *bytes);
+
+/*
+ * Unpack/transpose step on its own (Sec. 4: reorder the time-ordered block so each
+ * input's samples become contiguous, converting to a floating-point format).
+ * Writes d_planes, laid out [n_dumps][n_chan][NB][128][Kp] with NB = ceil(N/64) input
+ * blocks of 64 and Kp = n_time rounded up to a multiple of 64: row r < 64 holds the
+ * real parts of input 64*nb + r, row 64 + r its imaginary parts, one element per
+ * time sample, zero for padded inputs and samples.  Element type: fp16 for 4/8-bit
+ * samples (exact), fp32 for float samples.  Size: corr_workspace_size(FP32 engine).
+ */
+corr_status corr_unpack(corr_plan plan, const void *d_packed, int n_dumps, void *d_planes, void *stream);
+
+/*
+ * The X stage of one dump: V = sum over the dump's n_time samples, in baseline order.
+ *   d_packed    packed input of one dump (layout above)
+ *   d_vis       [n_chan][P][2] output; int64 for 4/8-bit samples, float32 for float
+ *   d_workspace corr_workspace_size(engine, 1) bytes, or NULL when that is 0
+ *   accumulate  0: overwrite d_vis;  1: add into d_vis (cross-dump accumulation in
+ *               int64, Fig. 1: accumulators are read out and reset by the caller)
+ *   engine      a corr_engine value
+ */
+corr_status corr_xengine_run(corr_plan plan, const void *d_packed, void *d_vis, void *d_workspace,
+                             int accumulate, int engine, void *stream);
+
+/* n_dumps consecutive dumps in one call (one launch per kernel for all dumps). */
+corr_status corr_xengine_run_batch(corr_plan plan, const void *d_packed, int n_dumps, void *d_vis,
+                                   void *d_workspace, int accumulate, int engine, void *stream);
+
+/*
+ * The cross-multiply-accumulate step alone, on sample planes that corr_unpack already
+ * wrote (Sec. 4, step 3): d_planes as corr_unpack describes, n_dumps dumps; d_vis,
+ * accumulate and engine as for corr_xengine_run.  CORR_ENGINE_TC and CORR_ENGINE_FP32
+ * only (BF16X3 needs its own split planes and runs through corr_xengine_run).
+ */
+corr_status corr_xengine_run_planes(corr_plan plan, const void *d_planes, int n_dumps, void *d_vis,
+                                    int accumulate, int engine, void *stream);
+
+/*
+ * Read and clear the plan's device status block (synchronises with the device).
+ * *device_error receives 0, or the code a kernel recorded when one of its bounded
+ * waits gave up.  Returns CORR_ETIMEOUT in that case, else CORR_OK / CORR_ECUDA.
+ */
+corr_status corr_plan_check(corr_plan plan, int *device_error);
+
+/*
+ * Divide int64 visibilities by the number of accumulated dumps, on the host, in
+ * float64 (Fig. 1: accumulators are divided by the number of times they were
+ * updated).  n_values = 2 * P * n_chan * n_dumps.  No GPU work.
+ */
+corr_status corr_average_host(const int64_t *vis, size_t n_values, int64_t n_accum, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

@@ -1,0 +1,177 @@
+"""ctypes binding of libcorr.so (the C ABI in include/corr.h).
+
+Argument marshalling only: every step of the X stage runs in the library's CUDA
+kernels.  PyTorch is used for device memory and streams; tensors are passed as raw
+device pointers.  If the library has not been built, ``lib()`` raises -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcorr.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, PENDING, EUNSUPPORTED = range(8)
+ENGINE_TC, ENGINE_FP32, ENGINE_BF16X3 = 0, 1, 2
+STATUS_NAMES = {OK: "CORR_OK", EINVAL: "CORR_EINVAL", ENOMEM: "CORR_ENOMEM", ECUDA: "CORR_ECUDA",
+                EBUSY: "CORR_EBUSY", ETIMEOUT: "CORR_ETIMEOUT", PENDING: "CORR_PENDING",
+                EUNSUPPORTED: "CORR_EUNSUPPORTED"}
+
+_lib = None
+
+_c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+_P = ctypes.POINTER
+
+# name -> (restype, argtypes); the exported surface of include/corr.h
+SIGNATURES = {
+    "corr_version": (_c_int, []),
+    "corr_last_error": (ctypes.c_char_p, []),
+    "corr_plan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int, _c_int]),
+    "corr_plan_destroy": (_c_int, [_vp]),
+    "corr_plan_info": (_c_int, [_vp, _P(_c_i64), _P(_c_sz), _P(_c_sz)]),
+    "corr_workspace_size": (_c_int, [_vp, _c_int, _c_int, _P(_c_sz)]),
+    "corr_unpack": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
+    "corr_xengine_run": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "corr_xengine_run_batch": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
+    "corr_xengine_run_planes": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int, _vp]),
+    "corr_plan_check": (_c_int, [_vp, _P(_c_int)]),
+    "corr_average_host": (_c_int, [_vp, _c_sz, _c_i64, _vp]),
+}
+
+
+class CorrError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libcorr.so (raises if it is missing; build it with paper_0906_1887_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcorr.so not built ({LIB_PATH}); run paper_0906_1887_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().corr_last_error().decode(errors="replace")
+
+
+def check(status: int, where: str):
+    if status != OK:
+        raise CorrError(status, where, last_error())
+    return status
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A correlation plan: n_inputs (N_I), n_chan (N_C), n_time samples per dump, sample mode."""
+
+    def __init__(self, n_inputs: int, n_chan: int, n_time: int, sample_bits: int):
+        h = ctypes.c_void_p()
+        check(lib().corr_plan_create(ctypes.byref(h), n_inputs, n_chan, n_time, sample_bits), "corr_plan_create")
+        self._h = h
+        self.n_inputs, self.n_chan, self.n_time, self.sample_bits = n_inputs, n_chan, n_time, sample_bits
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().corr_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        nb, pk, vb = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().corr_plan_info(self._h, ctypes.byref(nb), ctypes.byref(pk), ctypes.byref(vb)), "corr_plan_info")
+        return nb.value, pk.value, vb.value
+
+    @property
+    def n_baselines(self) -> int:
+        return self.info()[0]
+
+    def workspace_size(self, engine: int, n_dumps: int = 1) -> int:
+        b = ctypes.c_size_t()
+        check(lib().corr_workspace_size(self._h, engine, n_dumps, ctypes.byref(b)), "corr_workspace_size")
+        return b.value
+
+    def unpack(self, packed, planes, n_dumps: int = 1, stream=None):
+        check(lib().corr_unpack(self._h, _ptr(packed), n_dumps, _ptr(planes), _stream_handle(stream)), "corr_unpack")
+
+    def run(self, packed, vis, workspace=None, accumulate: bool = False, engine: int = ENGINE_TC,
+            n_dumps: int = 1, stream=None):
+        check(lib().corr_xengine_run_batch(self._h, _ptr(packed), n_dumps, _ptr(vis), _ptr(workspace),
+                                           1 if accumulate else 0, engine, _stream_handle(stream)),
+              "corr_xengine_run_batch")
+
+    def run_planes(self, planes, vis, accumulate: bool = False, engine: int = ENGINE_TC, n_dumps: int = 1,
+                   stream=None):
+        check(lib().corr_xengine_run_planes(self._h, _ptr(planes), n_dumps, _ptr(vis), 1 if accumulate else 0,
+                                            engine, _stream_handle(stream)), "corr_xengine_run_planes")
+
+    def check_device(self) -> int:
+        code = ctypes.c_int(0)
+        st = lib().corr_plan_check(self._h, ctypes.byref(code))
+        if st not in (OK, ETIMEOUT):
+            check(st, "corr_plan_check")
+        return code.value
+
+    # ---- torch conveniences (allocation only) ----
+    def vis_dtype(self):
+        import torch
+        return torch.float32 if self.sample_bits == 32 else torch.int64
+
+    def empty_vis(self, n_dumps: int = 1, device="cuda"):
+        import torch
+        return torch.empty((n_dumps, self.n_chan, self.n_baselines, 2), dtype=self.vis_dtype(), device=device)
+
+    def empty_workspace(self, engine: int, n_dumps: int = 1, device="cuda"):
+        import torch
+        n = self.workspace_size(engine, n_dumps)
+        return torch.empty(max(n, 16), dtype=torch.uint8, device=device) if n else None
+
+
+def version() -> int:
+    return int(lib().corr_version())
+
+
+def average_host(vis_int64, n_accum: int):
+    """int64 visibilities (numpy) divided by the number of accumulated dumps, in float64, on the host."""
+    import numpy as np
+    v = np.ascontiguousarray(vis_int64, dtype=np.int64)
+    out = np.empty(v.shape, dtype=np.float64)
+    check(lib().corr_average_host(v.ctypes.data, v.size, int(n_accum), out.ctypes.data), "corr_average_host")
+    return out

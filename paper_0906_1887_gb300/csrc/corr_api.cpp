@@ -1,0 +1,231 @@
+// C ABI of libcorr: plans, validation, dispatch of the X-stage engines.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "corr_internal.h"
+
+namespace corr {
+
+static thread_local char g_msg[512] = "";
+
+corr_status set_error(corr_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+corr_status cuda_error(cudaError_t e, const char* what) {
+    return set_error(CORR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t plane_elem_bytes(const Plan& p) { return p.sample_bits == 32 ? 4 : 2; }
+
+size_t planes_bytes(const Plan& p, int n_dumps) {
+    return (size_t)n_dumps * (size_t)p.n_chan * (size_t)p.nb * kBlockRows * (size_t)p.kp * plane_elem_bytes(p);
+}
+
+static size_t packed_bytes_one(const Plan& p) {
+    size_t per = p.sample_bits == 4 ? 1 : (p.sample_bits == 8 ? 2 : 8);
+    return (size_t)p.n_time * (size_t)p.n_chan * (size_t)p.n_inputs * per;
+}
+
+static size_t vis_bytes_one(const Plan& p) {
+    size_t per = p.sample_bits == 32 ? 8 : 16;
+    return (size_t)p.n_baselines * (size_t)p.n_chan * per;
+}
+
+static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+}  // namespace corr
+
+using namespace corr;
+
+extern "C" {
+
+int corr_version(void) { return 100; }  // 0.1.0
+
+const char* corr_last_error(void) { return g_msg; }
+
+corr_status corr_plan_create(corr_plan* out, int n_inputs, int n_chan, int n_time, int sample_bits) {
+    g_msg[0] = 0;
+    if (!out) return set_error(CORR_EINVAL, "corr_plan_create: out is NULL");
+    *out = nullptr;
+    if (n_inputs < 1 || n_inputs > kMaxInputs)
+        return set_error(CORR_EINVAL, "n_inputs=%d outside [1, %d]", n_inputs, kMaxInputs);
+    if (n_chan < 1) return set_error(CORR_EINVAL, "n_chan=%d must be >= 1", n_chan);
+    if (n_time < 1) return set_error(CORR_EINVAL, "n_time=%d must be >= 1", n_time);
+    if (sample_bits != 4 && sample_bits != 8 && sample_bits != 32)
+        return set_error(CORR_EINVAL, "sample_bits=%d must be 4, 8 or 32", sample_bits);
+    Plan tmp;
+    tmp.n_inputs = n_inputs;
+    tmp.n_chan = n_chan;
+    tmp.n_time = n_time;
+    tmp.sample_bits = sample_bits;
+    tmp.nb = (n_inputs + kBlockInputs - 1) / kBlockInputs;
+    tmp.kp = (n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    tmp.n_baselines = n_baselines(n_inputs);
+    // keep every element index of a dump's planes and visibilities inside int64 comfortably
+    double planes = (double)n_chan * tmp.nb * kBlockRows * (double)tmp.kp;
+    double vis = (double)n_chan * (double)tmp.n_baselines * 2.0;
+    if (planes > 4.0e15 || vis > 4.0e15) return set_error(CORR_EINVAL, "problem too large");
+    cudaError_t e = cudaGetDevice(&tmp.device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&tmp.n_sm, cudaDevAttrMultiProcessorCount, tmp.device);
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+    e = cudaMalloc((void**)&tmp.d_status, 4 * sizeof(int));
+    if (e != cudaSuccess) return set_error(CORR_ENOMEM, "cudaMalloc(status): %s", cudaGetErrorString(e));
+    e = cudaMemset(tmp.d_status, 0, 4 * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(tmp.d_status);
+        return cuda_error(e, "cudaMemset(status)");
+    }
+    Plan* p = new (std::nothrow) Plan(tmp);
+    if (!p) {
+        cudaFree(tmp.d_status);
+        return set_error(CORR_ENOMEM, "host allocation of plan failed");
+    }
+    *out = reinterpret_cast<corr_plan>(p);
+    return CORR_OK;
+}
+
+corr_status corr_plan_destroy(corr_plan plan) {
+    if (!plan) return set_error(CORR_EINVAL, "corr_plan_destroy: plan is NULL");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (p->d_status) cudaFree(p->d_status);
+    delete p;
+    return CORR_OK;
+}
+
+corr_status corr_plan_info(corr_plan plan, int64_t* n_bl, size_t* packed_bytes, size_t* vis_bytes) {
+    if (!plan) return set_error(CORR_EINVAL, "corr_plan_info: plan is NULL");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (n_bl) *n_bl = p->n_baselines;
+    if (packed_bytes) *packed_bytes = packed_bytes_one(*p);
+    if (vis_bytes) *vis_bytes = vis_bytes_one(*p);
+    return CORR_OK;
+}
+
+corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t* bytes) {
+    if (!plan || !bytes) return set_error(CORR_EINVAL, "corr_workspace_size: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    switch (engine) {
+        case CORR_ENGINE_TC:
+        case CORR_ENGINE_FP32:
+            *bytes = planes_bytes(*p, n_dumps);
+            return CORR_OK;
+        case CORR_ENGINE_BF16X3:
+            // hi and lo bf16 planes
+            *bytes = (size_t)n_dumps * p->n_chan * (size_t)p->nb * kBlockRows * (size_t)p->kp * 2 * 2;
+            return CORR_OK;
+        default:
+            return set_error(CORR_EINVAL, "unknown engine %d", engine);
+    }
+}
+
+corr_status corr_unpack(corr_plan plan, const void* d_packed, int n_dumps, void* d_planes, void* stream) {
+    if (!plan || !d_packed || !d_planes) return set_error(CORR_EINVAL, "corr_unpack: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    if (!aligned16(d_packed) || !aligned16(d_planes))
+        return set_error(CORR_EINVAL, "corr_unpack: pointers must be 16-byte aligned");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = p->sample_bits == 32 ? launch_unpack_f32(*p, d_packed, n_dumps, d_planes, s)
+                                         : launch_unpack_fp16(*p, d_packed, n_dumps, d_planes, s);
+    if (e != cudaSuccess) return cuda_error(e, "unpack launch");
+    return CORR_OK;
+}
+
+corr_status corr_xengine_run_batch(corr_plan plan, const void* d_packed, int n_dumps, void* d_vis,
+                                   void* d_workspace, int accumulate, int engine, void* stream) {
+    if (!plan || !d_packed || !d_vis) return set_error(CORR_EINVAL, "corr_xengine_run: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    if (accumulate != 0 && accumulate != 1) return set_error(CORR_EINVAL, "accumulate must be 0 or 1");
+    if (!aligned16(d_packed) || !aligned16(d_vis) || (d_workspace && !aligned16(d_workspace)))
+        return set_error(CORR_EINVAL, "corr_xengine_run: pointers must be 16-byte aligned");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t need = 0;
+    corr_status st = corr_workspace_size(plan, engine, n_dumps, &need);
+    if (st != CORR_OK) return st;
+    if (need && !d_workspace) return set_error(CORR_EINVAL, "engine %d needs %zu bytes of workspace", engine, need);
+    cudaError_t e = cudaSuccess;
+    if (engine == CORR_ENGINE_TC) {
+        if (p->sample_bits == 32)
+            return set_error(CORR_EUNSUPPORTED, "float samples run on CORR_ENGINE_BF16X3 or CORR_ENGINE_FP32");
+        e = launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
+        if (e == cudaSuccess) e = launch_xeng_tc(*p, d_workspace, nullptr, n_dumps, d_vis, accumulate, s);
+    } else if (engine == CORR_ENGINE_FP32) {
+        e = p->sample_bits == 32 ? launch_unpack_f32(*p, d_packed, n_dumps, d_workspace, s)
+                                 : launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
+        if (e == cudaSuccess) e = launch_xeng_fp32(*p, d_workspace, n_dumps, d_vis, accumulate, s);
+    } else if (engine == CORR_ENGINE_BF16X3) {
+        if (p->sample_bits != 32)
+            return set_error(CORR_EUNSUPPORTED, "CORR_ENGINE_BF16X3 takes float samples (sample_bits=32)");
+        char* hi = static_cast<char*>(d_workspace);
+        char* lo = hi + need / 2;
+        e = launch_unpack_bf16x2(*p, d_packed, n_dumps, hi, lo, s);
+        if (e == cudaSuccess) e = launch_xeng_tc(*p, hi, lo, n_dumps, d_vis, accumulate, s);
+    } else {
+        return set_error(CORR_EINVAL, "unknown engine %d", engine);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "X-stage launch");
+    return CORR_OK;
+}
+
+corr_status corr_xengine_run_planes(corr_plan plan, const void* d_planes, int n_dumps, void* d_vis, int accumulate,
+                                    int engine, void* stream) {
+    if (!plan || !d_planes || !d_vis) return set_error(CORR_EINVAL, "corr_xengine_run_planes: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    if (accumulate != 0 && accumulate != 1) return set_error(CORR_EINVAL, "accumulate must be 0 or 1");
+    if (!aligned16(d_planes) || !aligned16(d_vis))
+        return set_error(CORR_EINVAL, "corr_xengine_run_planes: pointers must be 16-byte aligned");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (engine == CORR_ENGINE_TC) {
+        if (p->sample_bits == 32)
+            return set_error(CORR_EUNSUPPORTED, "float samples run on CORR_ENGINE_BF16X3 or CORR_ENGINE_FP32");
+        e = launch_xeng_tc(*p, d_planes, nullptr, n_dumps, d_vis, accumulate, s);
+    } else if (engine == CORR_ENGINE_FP32) {
+        e = launch_xeng_fp32(*p, d_planes, n_dumps, d_vis, accumulate, s);
+    } else {
+        return set_error(CORR_EUNSUPPORTED, "corr_xengine_run_planes takes CORR_ENGINE_TC or CORR_ENGINE_FP32");
+    }
+    if (e != cudaSuccess) return cuda_error(e, "X-stage launch");
+    return CORR_OK;
+}
+
+corr_status corr_xengine_run(corr_plan plan, const void* d_packed, void* d_vis, void* d_workspace, int accumulate,
+                             int engine, void* stream) {
+    return corr_xengine_run_batch(plan, d_packed, 1, d_vis, d_workspace, accumulate, engine, stream);
+}
+
+corr_status corr_plan_check(corr_plan plan, int* device_error) {
+    if (!plan) return set_error(CORR_EINVAL, "corr_plan_check: plan is NULL");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+    e = cudaMemcpy(h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(status)");
+    e = cudaMemset(p->d_status, 0, sizeof(h));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemset(status)");
+    if (device_error) *device_error = h[0];
+    if (h[0] != 0) return set_error(CORR_ETIMEOUT, "device reported error %d (detail %d)", h[0], h[1]);
+    return CORR_OK;
+}
+
+corr_status corr_average_host(const int64_t* vis, size_t n_values, int64_t n_accum, double* out) {
+    if (!vis || !out) return set_error(CORR_EINVAL, "corr_average_host: NULL argument");
+    if (n_accum < 1) return set_error(CORR_EINVAL, "n_accum=%lld must be >= 1", (long long)n_accum);
+    const double n = (double)n_accum;
+    for (size_t k = 0; k < n_values; ++k) out[k] = (double)vis[k] / n;
+    return CORR_OK;
+}
+
+}  // extern "C"

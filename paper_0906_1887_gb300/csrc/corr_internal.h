@@ -1,0 +1,61 @@
+// Internal declarations shared by the host runtime and the CUDA kernels of libcorr.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/corr.h"
+
+namespace corr {
+
+constexpr int kBlockInputs = 64;      // inputs per operand block (rows 0..63 re, 64..127 im)
+constexpr int kBlockRows = 128;       // rows of one plane block
+constexpr int kTimeBlock = 64;        // samples per pipeline stage (one 128-byte fp16 row)
+constexpr int kMaxInputs = 8192;
+
+// Device error codes written to the plan's status block.
+enum DeviceError : int {
+    kDevOk = 0,
+    kDevTimeoutFull = 1,      // MMA waited too long for a loaded stage
+    kDevTimeoutEmpty = 2,     // producer waited too long for a free stage
+    kDevTimeoutAccFull = 3,   // epilogue waited too long for an accumulator
+    kDevTimeoutAccEmpty = 4,  // MMA waited too long for a drained accumulator
+    kDevBadItem = 5,          // a work item decoded outside its problem
+};
+
+struct Plan {
+    int n_inputs = 0;
+    int n_chan = 0;
+    int n_time = 0;
+    int sample_bits = 0;
+    int nb = 0;              // ceil(N / 64)
+    int kp = 0;              // n_time rounded up to 64
+    int64_t n_baselines = 0;
+    int device = 0;
+    int n_sm = 0;
+    int* d_status = nullptr; // [4] device status words
+};
+
+inline int64_t n_baselines(int64_t n) { return n * (n + 1) / 2; }
+
+// Host-side error reporting (thread-local message).
+corr_status set_error(corr_status st, const char* fmt, ...);
+corr_status cuda_error(cudaError_t e, const char* what);
+
+size_t plane_elem_bytes(const Plan& p);              // 2 (fp16) or 4 (fp32)
+size_t planes_bytes(const Plan& p, int n_dumps);     // one set of planes
+
+// Kernel launchers (return cudaSuccess or the launch error).
+cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps, void* d_planes,
+                               cudaStream_t s);
+cudaError_t launch_unpack_f32(const Plan& p, const void* d_packed, int n_dumps, void* d_planes,
+                              cudaStream_t s);
+cudaError_t launch_unpack_bf16x2(const Plan& p, const void* d_packed, int n_dumps, void* d_hi,
+                                 void* d_lo, cudaStream_t s);
+cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, void* d_vis,
+                             int accumulate, cudaStream_t s);
+cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_planes_lo, int n_dumps,
+                           void* d_vis, int accumulate, cudaStream_t s);
+
+}  // namespace corr

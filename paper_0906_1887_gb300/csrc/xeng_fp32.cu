@@ -1,0 +1,194 @@
+// CUDA-core FP32 X stage: the plain form of the cross-multiply-accumulate.
+//
+// The paper's group-parallel design (Sec. 4) shares input samples between threads
+// through shared memory so each global read feeds several products, with consecutive
+// threads on consecutive data so every access is coalesced, and accumulates over a
+// large batch in registers (Sec. 4, last paragraphs).  The same ideas, sized for an
+// sm_103a SM: a block owns a 64 x 64 tile of input pairs of one channel, stages 32
+// time samples of both 64-input blocks in shared memory, and each thread keeps a 4 x 4
+// register tile of complex accumulators (16 products per 16 shared-memory reads per
+// sample).  Tiles cover the upper triangle i <= j only.
+//
+// Integer samples: fp32 partial sums cover at most 64 samples (|Re| <= 64 * 2 * 128^2
+// = 2^21 < 2^24, so every partial sum is an exact integer) and are then added into
+// int64 totals, so the result equals the int64 definition bit for bit.  Float samples:
+// the 64-sample partials are added into fp32 totals (two-level summation).
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "corr_internal.h"
+
+namespace corr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTC = 32;            // time samples per shared-memory chunk
+constexpr int kStride = kBlockRows + 1;
+constexpr int kFlushChunks = 2;    // 2 * 32 = 64 samples per fp32 partial
+
+template <typename InT>
+__device__ __forceinline__ void load_chunk(const InT* __restrict__ rows, int kp, int t0, float* __restrict__ s) {
+    // rows: 128 plane rows of one input block; copy samples [t0, t0+32) transposed into s[t][row]
+    if constexpr (sizeof(InT) == 2) {
+        for (int q = threadIdx.x; q < kBlockRows * 4; q += kThreads) {
+            const int r = q >> 2, part = q & 3;
+            uint4 v = *reinterpret_cast<const uint4*>(rows + (int64_t)r * kp + t0 + part * 8);
+            const __half* h = reinterpret_cast<const __half*>(&v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[(part * 8 + e) * kStride + r] = __half2float(h[e]);
+        }
+    } else {
+        for (int q = threadIdx.x; q < kBlockRows * 8; q += kThreads) {
+            const int r = q >> 3, part = q & 7;
+            float4 v = *reinterpret_cast<const float4*>(rows + (int64_t)r * kp + t0 + part * 4);
+            s[(part * 4 + 0) * kStride + r] = v.x;
+            s[(part * 4 + 1) * kStride + r] = v.y;
+            s[(part * 4 + 2) * kStride + r] = v.z;
+            s[(part * 4 + 3) * kStride + r] = v.w;
+        }
+    }
+}
+
+// tile index -> (I, J) with I <= J over nb blocks, row-major upper triangle
+__device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
+    int i = 0, rem = tile;
+    while (rem >= nb - i) {
+        rem -= nb - i;
+        ++i;
+    }
+    I = i;
+    J = i + rem;
+}
+
+template <typename InT, bool INT_OUT>
+__global__ void __launch_bounds__(kThreads, 2)
+    xeng_fp32_kernel(const InT* __restrict__ planes, int n_inputs, int n_chan, int nb, int kp, int64_t n_items,
+                     int n_tiles, void* __restrict__ vis, int accumulate) {
+    __shared__ float sI[kTC * kStride];
+    __shared__ float sJ[kTC * kStride];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t P = (int64_t)n_inputs * (n_inputs + 1) / 2;
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int tile = (int)(item % n_tiles);
+        const int64_t dc = item / n_tiles;  // dump * n_chan + chan
+        int I, J;
+        tile_coords(tile, nb, I, J);
+        const InT* rowsI = planes + ((dc * nb + I) * (int64_t)kBlockRows) * kp;
+        const InT* rowsJ = planes + ((dc * nb + J) * (int64_t)kBlockRows) * kp;
+
+        float pr[4][4], pi[4][4];
+        typename std::conditional<INT_OUT, long long, float>::type tr[4][4], ti[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                pr[a][b] = pi[a][b] = 0.f;
+                tr[a][b] = ti[a][b] = 0;
+            }
+
+        int chunk = 0;
+        for (int t0 = 0; t0 < kp; t0 += kTC) {
+            load_chunk<InT>(rowsI, kp, t0, sI);
+            load_chunk<InT>(rowsJ, kp, t0, sJ);
+            __syncthreads();
+#pragma unroll 4
+            for (int t = 0; t < kTC; ++t) {
+                float ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    ar[a] = sI[t * kStride + ty + 16 * a];
+                    ai[a] = sI[t * kStride + kBlockInputs + ty + 16 * a];
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    br[b] = sJ[t * kStride + tx + 16 * b];
+                    bi[b] = sJ[t * kStride + kBlockInputs + tx + 16 * b];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        // x_i * conj(x_j): re = ar*br + ai*bi, im = ai*br - ar*bi
+                        pr[a][b] = fmaf(ar[a], br[b], pr[a][b]);
+                        pr[a][b] = fmaf(ai[a], bi[b], pr[a][b]);
+                        pi[a][b] = fmaf(ai[a], br[b], pi[a][b]);
+                        pi[a][b] = fmaf(-ar[a], bi[b], pi[a][b]);
+                    }
+            }
+            __syncthreads();
+            if (++chunk == kFlushChunks || t0 + kTC >= kp) {
+                chunk = 0;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        if constexpr (INT_OUT) {
+                            tr[a][b] += __float2ll_rn(pr[a][b]);
+                            ti[a][b] += __float2ll_rn(pi[a][b]);
+                        } else {
+                            tr[a][b] += pr[a][b];
+                            ti[a][b] += pi[a][b];
+                        }
+                        pr[a][b] = pi[a][b] = 0.f;
+                    }
+            }
+        }
+
+        // dump in baseline order: vis[dc][b(i,j)][re, im] for i <= j < N
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = I * kBlockInputs + ty + 16 * a;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = J * kBlockInputs + tx + 16 * b;
+                if (i <= j && j < n_inputs) {
+                    const int64_t bl = (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 + (j - i);
+                    const int64_t o = (dc * P + bl);
+                    if constexpr (INT_OUT) {
+                        longlong2* dst = reinterpret_cast<longlong2*>(vis) + o;
+                        longlong2 v = make_longlong2(tr[a][b], ti[a][b]);
+                        if (accumulate) {
+                            longlong2 old = *dst;
+                            v.x += old.x;
+                            v.y += old.y;
+                        }
+                        *dst = v;
+                    } else {
+                        float2* dst = reinterpret_cast<float2*>(vis) + o;
+                        float2 v = make_float2(tr[a][b], ti[a][b]);
+                        if (accumulate) {
+                            float2 old = *dst;
+                            v.x += old.x;
+                            v.y += old.y;
+                        }
+                        *dst = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, void* d_vis, int accumulate,
+                             cudaStream_t s) {
+    const int n_tiles = p.nb * (p.nb + 1) / 2;
+    const int64_t n_items = (int64_t)n_dumps * p.n_chan * n_tiles;
+    const int64_t cap = (int64_t)p.n_sm * 2 * 16;
+    const int grid = (int)(n_items < cap ? n_items : cap);
+    if (p.sample_bits == 32) {
+        xeng_fp32_kernel<float, false><<<grid, kThreads, 0, s>>>(static_cast<const float*>(d_planes), p.n_inputs,
+                                                                  p.n_chan, p.nb, p.kp, n_items, n_tiles, d_vis,
+                                                                  accumulate);
+    } else {
+        xeng_fp32_kernel<__half, true><<<grid, kThreads, 0, s>>>(static_cast<const __half*>(d_planes), p.n_inputs,
+                                                                  p.n_chan, p.nb, p.kp, n_items, n_tiles, d_vis,
+                                                                  accumulate);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace corr

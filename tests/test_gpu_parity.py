@@ -1,0 +1,146 @@
+"""GPU parity: the CUDA X stage against the CPU oracle, through the C ABI.
+
+Integer samples: bit-exact int64 equality with the oracle (the definition V_ij =
+sum_t x_i conj(x_j), Sec. 2 / Fig. 2).  Float samples: the normwise error against the
+float64 oracle, max |V - V64| / sqrt(V64_ii V64_jj), must stay within 1e-6 for the FP32
+engine and 1e-2 for BF16x3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0906_1887_gb300 import synth
+from _gpu_helpers import int_case, normwise_error, run_engine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TC, FP32, BF16X3 = 0, 1, 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0906_1887_gb300 import corr
+    corr.lib()
+
+
+@pytest.mark.parametrize("engine", [TC, FP32])
+def test_mwa32t_4bit_bit_exact(engine):
+    re, im, bits, (n, c, t) = synth.workload("mwa32t_4bit")
+    p = synth.pack(re, im, bits)
+    v = run_engine(p, n, c, t, bits, engine)[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
+
+
+CASES = [  # (n, c, t, bits): ragged inputs, tails, several tiles, chunk boundaries
+    (1, 1, 1, 8), (2, 3, 33, 4), (3, 2, 64, 8), (17, 2, 100, 4), (63, 1, 65, 8), (64, 2, 127, 8),
+    (65, 2, 70, 4), (100, 1, 200, 8), (130, 2, 129, 8), (200, 1, 64, 4), (64, 1, 1025, 8),
+    (70, 1, 2100, 8), (257, 1, 96, 8),
+]
+
+
+@pytest.mark.parametrize("engine", [TC, FP32])
+@pytest.mark.parametrize("n,c,t,bits", CASES)
+def test_small_ragged_bit_exact(engine, n, c, t, bits):
+    p = int_case(1000 + n + 7 * c + t, n, c, t, bits)
+    v = run_engine(p, n, c, t, bits, engine)[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
+
+
+@pytest.mark.parametrize("engine", [TC, FP32])
+@pytest.mark.parametrize("t", [1023, 1024, 1025, 2048, 3000])
+def test_extreme_magnitudes_chunk_flush(engine, t):
+    # every sample -128 - 128j except a -128 + 127j input: partial sums reach 2^24 per chunk
+    n = 66
+    re = np.full((t, 1, n), -128, np.int16)
+    im = np.full((t, 1, n), -128, np.int16)
+    im[:, 0, 5] = 127
+    p = synth.pack(re, im, 8)
+    v = run_engine(p, n, 1, t, 8, engine)[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, 1, t, 8))
+
+
+@pytest.mark.parametrize("engine", [TC, FP32])
+def test_int64_beyond_int32(engine):
+    t = 65536 + 64
+    re = np.full((t, 1, 2), -128, np.int16)
+    im = np.full((t, 1, 2), -128, np.int16)
+    p = synth.pack(re, im, 8)
+    v = run_engine(p, 2, 1, t, 8, engine)[0]
+    ref = oracle.xcorr_int(p, 2, 1, t, 8)
+    assert ref[0, 0, 0] > 2 ** 31 and np.array_equal(v, ref)
+
+
+@pytest.mark.parametrize("engine", [TC, FP32])
+def test_batch_of_dumps_and_accumulate(engine):
+    n, c, t, d = 72, 3, 150, 3
+    packs = [int_case(40 + k, n, c, t, 8) for k in range(d)]
+    allp = np.concatenate([x.reshape(-1) for x in packs])
+    v = run_engine(allp, n, c, t, 8, engine, n_dumps=d)
+    refs = [oracle.xcorr_int(x, n, c, t, 8) for x in packs]
+    for k in range(d):
+        assert np.array_equal(v[k], refs[k])
+    # accumulate=1 adds into the caller's accumulators (cross-dump accumulation in int64)
+    init = np.stack(refs).astype(np.int64)
+    v2 = run_engine(allp, n, c, t, 8, engine, n_dumps=d, accumulate=True, vis_init=init)
+    assert np.array_equal(v2, 2 * init)
+
+
+def test_unpack_planes_match_oracle_unpack():
+    from paper_0906_1887_gb300 import corr
+    for bits in (4, 8):
+        n, c, t = 70, 3, 100
+        p = int_case(5 + bits, n, c, t, bits)
+        plan = corr.Plan(n, c, t, bits)
+        x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
+        planes = torch.empty(plan.workspace_size(FP32) // 2, dtype=torch.float16, device="cuda")
+        plan.unpack(x, planes)
+        torch.cuda.synchronize()
+        nb, kp = (n + 63) // 64, (t + 63) // 64 * 64
+        got = planes.cpu().float().numpy().reshape(c, nb, 128, kp)
+        re, im = oracle.unpack(p, n, c, t, bits)                 # [T][C][N]
+        want = np.zeros((c, nb, 128, kp), np.float32)
+        for i in range(n):
+            want[:, i // 64, i % 64, :t] = re[:, :, i].T
+            want[:, i // 64, 64 + i % 64, :t] = im[:, :, i].T
+        assert np.array_equal(got, want)
+        plan.close()
+
+
+def test_float_engines_error_vs_float64():
+    re, im = synth.correlated_gaussian(2001, 1000, 4, 64, 16.0, 0.1, as_float=True)
+    x = synth.packf32(re, im)
+    ref = oracle.xcorr_f64(x, 64, 4, 1000)
+    v32 = run_engine(x, 64, 4, 1000, 32, FP32)[0]
+    vbf = run_engine(x, 64, 4, 1000, 32, BF16X3)[0]
+    e32 = normwise_error(v32, ref, 64)
+    ebf = normwise_error(vbf, ref, 64)
+    assert e32 <= 1e-6, e32
+    assert ebf <= 1e-2, ebf
+
+
+@pytest.mark.parametrize("n,c,t", [(1, 1, 1), (65, 2, 130), (130, 1, 70)])
+def test_float_engines_ragged(n, c, t):
+    re, im = synth.correlated_gaussian(77 + n, t, c, n, 1.0, 0.3, as_float=True)
+    x = synth.packf32(re, im)
+    ref = oracle.xcorr_f64(x, n, c, t)
+    assert normwise_error(run_engine(x, n, c, t, 32, FP32)[0], ref, n) <= 1e-6
+    assert normwise_error(run_engine(x, n, c, t, 32, BF16X3)[0], ref, n) <= 1e-2
+
+
+def test_invalid_arguments_rejected():
+    from paper_0906_1887_gb300 import corr
+    with pytest.raises(corr.CorrError):
+        corr.Plan(0, 1, 1, 8)
+    with pytest.raises(corr.CorrError):
+        corr.Plan(4, 1, 1, 6)
+    plan = corr.Plan(4, 1, 16, 32)
+    x = torch.zeros(4 * 16 * 8, dtype=torch.uint8, device="cuda")
+    vis = plan.empty_vis(1, "cuda")
+    with pytest.raises(corr.CorrError):            # TC engine takes integer samples only
+        plan.run(x, vis, plan.empty_workspace(TC, 1), engine=TC)
+    with pytest.raises(corr.CorrError):            # missing workspace
+        plan.run(x, vis, None, engine=FP32)
+    plan.close()
