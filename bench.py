@@ -155,6 +155,7 @@ def reference_arm(args):
 
 
 def main():
+    global N_DUMPS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -162,6 +163,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--dumps", type=int, default=N_DUMPS,
+                    help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -171,6 +174,10 @@ def main():
     import torch
 
     from paper_0906_1887_gb300 import corr, synth
+
+    if args.dumps != N_DUMPS:
+        WORKLOAD = WORKLOAD.replace("x 200 dumps", f"x {args.dumps} dumps (reduced for profiling)")
+        N_DUMPS = args.dumps
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
