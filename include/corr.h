@@ -146,6 +146,29 @@ corr_status corr_xengine_run_planes(corr_plan plan, const void *d_planes, int n_
                                     int accumulate, int engine, void *stream);
 
 /*
+ * The tensor-core X stage of one dump of 4/8-bit samples without allocating device
+ * memory.  The paper has no counterpart: this call exists for callers that cannot call
+ * cudaMalloc -- a real-time loop that must never pay the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or a host framework that owns all device memory and forbids its
+ * plug-ins from allocating.  No plan is needed (a plan allocates a status block); the
+ * problem is given directly.  d_packed, d_vis, accumulate and stream are as for
+ * corr_xengine_run (engine: CORR_ENGINE_TC).
+ *
+ * Scratch: the unpacked sample planes (corr_unpack's layout, n_chan * ceil(N/64) * 128 *
+ * Kp * 2 bytes) live in a fixed 64 MiB array inside the library; every GPU that loads the
+ * library holds it until the process exits.  Larger dumps return CORR_EINVAL with a
+ * message naming the size.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  The call itself calls no cudaMalloc, cudaFree or allocating
+ * library routine.  All calls share the array and its contents persist between calls:
+ * calls whose GPU work overlaps (other streams or host threads on the same device) race
+ * and must be serialised by the caller.  Bounded-wait failures inside the kernels leave
+ * the output incomplete and are not reported by this call.
+ */
+corr_status corr_xengine_run_static(const void *d_packed, int n_inputs, int n_chan, int n_time,
+                                    int sample_bits, void *d_vis, int accumulate, void *stream);
+
+/*
  * Read and clear the plan's device status block (synchronises with the device).
  * *device_error receives 0, or the code a kernel recorded when one of its bounded
  * waits gave up.  Returns CORR_ETIMEOUT in that case, else CORR_OK / CORR_ECUDA.
