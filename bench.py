@@ -4,7 +4,7 @@ Workload (the streamed real-time correlator): 64 inputs (32 dual-pol antennas), 
 channels, 1000 samples per dump, 200 dumps, complex 8-bit Gaussian samples (sigma 16,
 clipped to +-127) with a common correlated component rho = 0.1, generated on the device
 from a seeded generator.  One step = the whole job: all 200 dumps through the library's
-X stage (unpack + tensor-core cross-multiply-accumulate + int64 dump), one batched call.
+X stage (fused unpack + tensor-core cross-multiply-accumulate + int64 dump), one launch.
 
 Printed on rank 0 as one JSON line:
   value        TeraCMAC/s of the whole job, inputs resident in HBM, device-timed
@@ -101,27 +101,26 @@ class ClockSampler:
 
 
 def cpu_baseline(target_s: float = 12.0):
-    """The C oracle (OpenMP over the host's cores) on a bounded channel sample of the workload."""
-    import numpy as np
-
+    """The C oracle (OpenMP over the host's cores) on a bounded sample of the workload:
+    repeated passes over one full 768-channel dump until about target_s seconds."""
     import oracle
     from paper_0906_1887_gb300 import synth
-    re, im = synth.correlated_gaussian(SEED, N_TIME, 64, N_INPUTS, SIGMA, RHO, 127)
+    re, im = synth.correlated_gaussian(SEED, N_TIME, N_CHAN, N_INPUTS, SIGMA, RHO, 127)
     packed = synth.pack(re, im, BITS)
+    del re, im
     threads = oracle.threads_used(0)
-    n = 2
-    while True:
-        chans = np.arange(n, dtype=np.int32)
-        t0 = time.perf_counter()
-        oracle.xcorr_int(packed, N_INPUTS, 64, N_TIME, BITS, chans=chans)
-        dt = time.perf_counter() - t0
-        if dt > target_s / 4 or n >= 64:
-            break
-        n = min(64, max(n * 2, int(n * target_s / 4 / max(dt, 1e-3))))
-    cm = N_INPUTS * (N_INPUTS + 1) // 2 * n * N_TIME
+    t0 = time.perf_counter()
+    oracle.xcorr_int(packed, N_INPUTS, N_CHAN, N_TIME, BITS)
+    one = time.perf_counter() - t0
+    reps = max(1, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.xcorr_int(packed, N_INPUTS, N_CHAN, N_TIME, BITS)
+    dt = time.perf_counter() - t0
+    cm = N_INPUTS * (N_INPUTS + 1) // 2 * N_CHAN * N_TIME * reps
     return {"value": cm / dt / 1e12, "unit": "TeraCMAC/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} of 768 channels of one 1000-sample dump (64 inputs, 8-bit), numpy PCG64 seed {SEED}",
-            "seconds": dt}
+            "sample": f"{reps} passes over one full dump (64 inputs x 768 channels x 1000 samples, 8-bit, "
+                      f"numpy PCG64 seed {SEED})", "seconds": dt}
 
 
 def reference_arm(args):
@@ -134,7 +133,7 @@ def reference_arm(args):
     from paper_0906_1887_gb300 import synth
     re, im = synth.correlated_gaussian(SEED, N_TIME, 64, N_INPUTS, SIGMA, RHO, 127)
     packed = synth.pack(re, im, BITS)
-    chans = np.arange(16, dtype=np.int32)        # a bounded sample of the job per step
+    chans = np.arange(64, dtype=np.int32)        # a bounded sample of the job per step
     threads = oracle.threads_used(0)
     for _ in range(args.warmup):
         oracle.xcorr_int(packed, N_INPUTS, 64, N_TIME, BITS, chans=chans[:2])
@@ -147,9 +146,9 @@ def reference_arm(args):
     line = {"metric": "X-engine TeraCMAC/s", "value": v, "unit": "TeraCMAC/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": "16 channels of one dump"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": "64 channels of one dump"},
             "cpu_baseline": {"value": v, "unit": "TeraCMAC/s", "cores": threads, "kind": "oracle",
-                             "sample": "16 of 768 channels of one 1000-sample dump per step"},
+                             "sample": "64 of 768 channels of one 1000-sample dump per step"},
             "e2e": {"value": v, "unit": "TeraCMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -208,7 +207,7 @@ def main():
     packed = synth.torch_correlated_gaussian_packed8(N_DUMPS, N_TIME, N_CHAN, N_INPUTS, SIGMA, RHO,
                                                      SEED + 7919 * rank, dev)
     vis = plan.empty_vis(N_DUMPS, dev)
-    ws = plan.empty_workspace(corr.ENGINE_TC, N_DUMPS, dev)
+    ws = plan.empty_workspace(corr.ENGINE_TC, N_DUMPS, dev)     # None: packed samples feed the kernel directly
     stream = torch.cuda.current_stream(dev)
 
     def step_tc():
@@ -221,31 +220,20 @@ def main():
     if plan.check_device() != 0:
         raise RuntimeError("device-side wait gave up during warm-up")
 
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    # device-timed region: K whole-job steps (inputs 19.7 GB >> L2, no flush needed)
+    # device-timed region: K whole-job steps (inputs 19.7 GB per step >> L2, no flush needed)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
         step_tc()
-    ev1.record(stream)
+        ev[k + 1].record(stream)
     barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    # per-kernel split (same stream): unpack alone and cross-multiply alone
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    kms_unpack, kms_x = [], []
-    for _ in range(max(2, args.steps // 2)):
-        e[0].record(stream)
-        plan.unpack(packed, ws, n_dumps=N_DUMPS, stream=stream)
-        e[1].record(stream)
-        plan.run_planes(ws, vis, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
-        e[2].record(stream)
-        torch.cuda.synchronize(dev)
-        kms_unpack.append(e[0].elapsed_time(e[1]))
-        kms_x.append(e[1].elapsed_time(e[2]))
     clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms_total = ev[0].elapsed_time(ev[-1])
     if plan.check_device() != 0:
         raise RuntimeError("device-side wait gave up in the timed region")
 
@@ -254,10 +242,10 @@ def main():
     value = cm_step * world / (ms_step / 1e3) / 1e12
     rtf = (N_TIME * N_DUMPS / CHANNEL_RATE_HZ) / (ms_step / 1e3)
 
-    # FP32 CUDA-core engine on the same job
-    ws32 = ws  # same plane layout and size for integer samples
-    for _ in range(1):
-        plan.run(packed, vis, ws32, engine=corr.ENGINE_FP32, n_dumps=N_DUMPS, stream=stream)
+    # FP32 CUDA-core engine on the same job (unpack to fp16 planes + CUDA-core cross-multiply)
+    ws32 = plan.empty_workspace(corr.ENGINE_FP32, N_DUMPS, dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.run(packed, vis, ws32, engine=corr.ENGINE_FP32, n_dumps=N_DUMPS, stream=stream)
     barrier()
     ev0.record(stream)
     for _ in range(args.fp32_steps):
@@ -266,16 +254,17 @@ def main():
     barrier()
     ms32 = max_over_ranks(ev0.elapsed_time(ev1) / args.fp32_steps)
     value32 = cm_step * world / (ms32 / 1e3) / 1e12
+    del ws32
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: H2D packed, run, D2H visibilities
     host_in = torch.empty(packed.shape, dtype=torch.uint8, pin_memory=True)
     host_in.copy_(packed)
     host_out = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
     dev_in = torch.empty_like(packed)
-    for _ in range(1):
-        dev_in.copy_(host_in, non_blocking=True)
-        plan.run(dev_in, vis, ws, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
-        host_out.copy_(vis, non_blocking=True)
+    dev_in.copy_(host_in, non_blocking=True)
+    plan.run(dev_in, vis, ws, engine=corr.ENGINE_TC, n_dumps=N_DUMPS, stream=stream)
+    host_out.copy_(vis, non_blocking=True)
     barrier()
     e2e_steps = max(1, min(args.steps, 3))
     ev0.record(stream)
@@ -287,22 +276,22 @@ def main():
     barrier()
     ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / e2e_steps)
     e2e_value = cm_step * world / (ms_e2e / 1e3) / 1e12
-    del dev_in, host_in
+    del dev_in, host_in, host_out
 
-    # roofline of the dominant kernel: the cross-multiply over fp16 planes is HBM-bound here
+    # roofline of the step's one kernel (the fused tensor-core X stage): HBM-bound here
     hbm_peak, bf16_peak, peak_src = _peaks()
-    ms_x = statistics.median(kms_x)
-    ms_u = statistics.median(kms_unpack)
-    kp = (N_TIME + 63) // 64 * 64
-    x_bytes = N_DUMPS * N_CHAN * (128 * kp * 2 + P * 16)            # planes read + int64 dump written
+    ms_x = statistics.median(step_ms)
+    in_bytes = N_DUMPS * N_TIME * N_CHAN * N_INPUTS * 2
+    out_bytes = N_DUMPS * N_CHAN * P * 16
+    x_bytes = in_bytes + out_bytes                 # packed samples read once + int64 visibilities written
     x_gbs = x_bytes / (ms_x / 1e3) / 1e9
     flops = 8.0 * cm_step
-    roofline = {"bound": "hbm", "kernel": "xeng_tc_kernel", "achieved": x_gbs, "peak": hbm_peak,
+    roofline = {"bound": "hbm", "kernel": "xeng_tc_kernel<raw8>", "achieved": x_gbs, "peak": hbm_peak,
                 "unit": "GB/s", "frac": x_gbs / hbm_peak, "traffic": None,
-                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-                "tensor_tflops": flops / (ms_x / 1e3) / 1e12, "tensor_frac_of_bf16_burst": flops / (ms_x / 1e3) / 1e12 / bf16_peak,
-                "kernel_ms": ms_x, "unpack_ms": ms_u,
-                "algorithmic_bytes_per_launch": x_bytes}
+                "peak_source": ("measured: MEASURED_PEAKS.json hbm_gbs" if peak_src == "measured" else peak_src),
+                "algorithmic_bytes_per_launch": x_bytes, "kernel_ms": ms_x,
+                "tensor_tflops_algorithmic": flops / (ms_x / 1e3) / 1e12,
+                "tensor_frac_of_measured_bf16_burst": flops / (ms_x / 1e3) / 1e12 / bf16_peak}
 
     if rank != 0:
         if dist is not None:
@@ -314,14 +303,14 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME,
-                   "n_dumps": N_DUMPS, "sample_bits": BITS, "engine": "tcgen05 fp16 operands, fp32 accum, exact int64",
+                   "n_dumps": N_DUMPS, "sample_bits": BITS, "engine": "fused tcgen05 X stage: packed 8-bit -> fp16 in shared memory, fp32 accum, exact int64",
                    "l2": "inputs (19.7 GB per step) far larger than L2; no flush", "parallelism": f"replicas{world}"},
         "real_time_factor": rtf,
         "fp32_path": {"value": value32, "unit": "TeraCMAC/s", "ms_per_step": ms32, "speedup_tc_over_fp32": value / value32},
         "e2e": {"value": e2e_value, "unit": "TeraCMAC/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(packed.numel()), "d2h_bytes_per_step": int(vis.numel() * vis.element_size())},
         "roofline": roofline,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "clocks": clk,
         "cpu_baseline": cpu,
     }

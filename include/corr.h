@@ -113,9 +113,9 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t 
  * Unpack/transpose step on its own (Sec. 4: reorder the time-ordered block so each
  * input's samples become contiguous, converting to a floating-point format).
  * Writes d_planes, laid out [n_dumps][n_chan][NB][128][Kp] with NB = ceil(N/64) input
- * blocks of 64 and Kp = n_time rounded up to a multiple of 64: row r < 64 holds the
- * real parts of input 64*nb + r, row 64 + r its imaginary parts, one element per
- * time sample, zero for padded inputs and samples.  Element type: fp16 for 4/8-bit
+ * blocks of 64 and Kp = n_time rounded up to a multiple of 64: row 2r holds the real
+ * parts of input 64*nb + r and row 2r + 1 its imaginary parts, one element per time
+ * sample, zero for padded inputs and samples.  Element type: fp16 for 4/8-bit
  * samples (exact), fp32 for float samples.  Size: corr_workspace_size(FP32 engine).
  */
 corr_status corr_unpack(corr_plan plan, const void *d_packed, int n_dumps, void *d_planes, void *stream);

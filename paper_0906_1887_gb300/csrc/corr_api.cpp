@@ -115,6 +115,9 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t*
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     switch (engine) {
         case CORR_ENGINE_TC:
+            // packed samples feed the tensor-core kernel directly when TMA can address them
+            *bytes = tc_raw_supported(*p) ? 0 : planes_bytes(*p, n_dumps);
+            return CORR_OK;
         case CORR_ENGINE_FP32:
             *bytes = planes_bytes(*p, n_dumps);
             return CORR_OK;
@@ -157,8 +160,12 @@ corr_status corr_xengine_run_batch(corr_plan plan, const void* d_packed, int n_d
     if (engine == CORR_ENGINE_TC) {
         if (p->sample_bits == 32)
             return set_error(CORR_EUNSUPPORTED, "float samples run on CORR_ENGINE_BF16X3 or CORR_ENGINE_FP32");
-        e = launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
-        if (e == cudaSuccess) e = launch_xeng_tc(*p, d_workspace, nullptr, n_dumps, d_vis, accumulate, s);
+        if (tc_raw_supported(*p)) {
+            e = launch_xeng_tc_raw(*p, d_packed, n_dumps, d_vis, accumulate, s);
+        } else {
+            e = launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
+            if (e == cudaSuccess) e = launch_xeng_tc(*p, d_workspace, nullptr, n_dumps, d_vis, accumulate, s);
+        }
     } else if (engine == CORR_ENGINE_FP32) {
         e = p->sample_bits == 32 ? launch_unpack_f32(*p, d_packed, n_dumps, d_workspace, s)
                                  : launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);

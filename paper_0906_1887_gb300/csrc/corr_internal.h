@@ -57,5 +57,9 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
                              int accumulate, cudaStream_t s);
 cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_planes_lo, int n_dumps,
                            void* d_vis, int accumulate, cudaStream_t s);
+// Fused path: packed 4/8-bit samples straight into the tensor-core kernel (no planes).
+bool tc_raw_supported(const Plan& p);
+cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                               cudaStream_t s);
 
 }  // namespace corr

@@ -6,9 +6,9 @@
 // staged through shared memory so both the reads (consecutive inputs) and the writes
 // (consecutive time samples of one plane row) are coalesced.
 //
-// Output planes: [dump][chan][NB][128][Kp]; rows 0..63 real parts of the block's 64
-// inputs, rows 64..127 imaginary parts; Kp = n_time rounded up to 64; padded inputs and
-// samples are zero.
+// Output planes: [dump][chan][NB][128][Kp]; row 2r holds the real parts and row 2r + 1
+// the imaginary parts of input r of the block's 64 inputs; Kp = n_time rounded up to 64;
+// padded inputs and samples are zero.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(const unsigned char* _
         const int64_t row0 = ((dc * nb_count) + nb) * (int64_t)kBlockRows;
         for (int q = threadIdx.x; q < kBlockRows * (kTimeBlock / 8); q += kThreads) {
             const int r = q >> 3, ch = q & 7;
-            const float* src = (r < kBlockInputs ? s_re : s_im) + (r & (kBlockInputs - 1)) * kPad + ch * 8;
+            const float* src = ((r & 1) ? s_im : s_re) + (r >> 1) * kPad + ch * 8;
             const int64_t off = (row0 + r) * (int64_t)kp + tb * kTimeBlock + ch * 8;
             if constexpr (OUT == kOutF16) {
                 __align__(16) __half v[8];

@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(kThreads, 2)
                 float ar[4], ai[4], br[4], bi[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    ar[a] = sI[t * kStride + ty + 16 * a];
-                    ai[a] = sI[t * kStride + kBlockInputs + ty + 16 * a];
+                    ar[a] = sI[t * kStride + 2 * (ty + 16 * a)];
+                    ai[a] = sI[t * kStride + 2 * (ty + 16 * a) + 1];
                 }
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    br[b] = sJ[t * kStride + tx + 16 * b];
-                    bi[b] = sJ[t * kStride + kBlockInputs + tx + 16 * b];
+                    br[b] = sJ[t * kStride + 2 * (tx + 16 * b)];
+                    bi[b] = sJ[t * kStride + 2 * (tx + 16 * b) + 1];
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)

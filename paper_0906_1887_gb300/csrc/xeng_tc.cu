@@ -2,36 +2,50 @@
 //
 // For one channel the correlation matrix is the outer product of the sample vector with
 // its conjugate, summed over time (Sec. 4, Fig. 2) -- a Hermitian rank-k update, i.e. a
-// dense contraction over the time axis.  Write X_r, X_i for the real and imaginary
-// sample matrices (inputs x time).  A 64-input block I is stacked as A = [X_r,I ; X_i,I]
-// (128 rows), a 64-input block J gives B_r = X_r,J and B_i = X_i,J, and two MMAs per
-// K-step accumulate
-//     D1 = A B_r^T = [ Xr_I Xr_J^T ; Xi_I Xr_J^T ]     D2 = A B_i^T = [ Xr_I Xi_J^T ; Xi_I Xi_J^T ]
-// so that, for i in I and j in J,
-//     Re V_ij = D1[re row i][j] + D2[im row i][j]      Im V_ij = D1[im row i][j] - D2[re row i][j]
-// which is x_i conj(x_j) summed over time (Sec. 2).  Only blocks with I <= J (the
-// upper triangle of input pairs) are scheduled.
+// dense contraction over the time axis.  A 64-input block is held as 128 operand rows,
+// interleaved: row 2m carries the real parts and row 2m+1 the imaginary parts of input m,
+// one column per time sample.  With A = block I and B = block J in that form, one MMA per
+// 16 samples accumulates D = A B^T (M = N = 128), whose 2 x 2 sub-blocks are
+//     D[2i][2j] = sum xr_i xr_j    D[2i][2j+1] = sum xr_i xi_j
+//     D[2i+1][2j] = sum xi_i xr_j  D[2i+1][2j+1] = sum xi_i xi_j
+// so that Re V_ij = D[2i][2j] + D[2i+1][2j+1] and Im V_ij = D[2i+1][2j] - D[2i][2j+1]:
+// x_i conj(x_j) summed over time (Sec. 2).  Rows 2i and 2i+1 sit in adjacent tensor-memory
+// lanes, so the epilogue combines them with one lane-pair shuffle.  Only blocks with
+// I <= J (the upper triangle of input pairs) are scheduled.
 //
 // Exactness for integer samples: 4/8-bit values are exact in fp16, their products
-// (|p| <= 2^14) are exact, and each D element sums one product per sample, so a chunk
-// of at most 1024 samples keeps every partial sum at or below 2^24 in magnitude, where
-// fp32 holds every integer.  Chunks are flushed to int64; results are bit-exact.
+// (|p| <= 2^14) are exact, and each D element sums one product per sample, so a chunk of
+// at most 1024 samples keeps every partial sum at or below 2^24 in magnitude, where fp32
+// holds every integer.  Each D element is converted to int64 before the re/im sums, and
+// chunks are flushed to int64; results are bit-exact.
 //
-// Float samples (BF16x3): x = h + l with bf16 h, l; each MMA pair runs for h*h^T,
-// h*l^T and l*h^T with fp32 accumulation.
+// Float samples (BF16x3): x = h + l with bf16 h, l; MMAs for h h^T, h l^T and l h^T with
+// fp32 accumulation.
+//
+// Two ways to feed the operands:
+//   planes  -- the unpack kernel has written fp16 (or bf16 hi/lo) sample planes in the
+//              interleaved row order; TMA loads 128-row x 64-sample tiles with 128-byte
+//              swizzle straight into the operand ring.
+//   raw     -- (4/8-bit samples) TMA loads the packed [time][chan][input] bytes of a
+//              64-input x 64-sample block and four converter warps turn them into the
+//              swizzled fp16 operand tiles in shared memory: the unpack/transpose step
+//              (Sec. 4) fused into the X kernel, so the samples cross HBM once.
 //
 // CTA roles (one CTA per SM, persistent over work items = (dump, channel, I, J)):
-//   warp 0      TMA producer: 128-row x 64-sample fp16 tiles into a 4-stage ring
-//   warp 1      tensor-memory allocator and single-thread MMA issuer
-//   warps 2..5  epilogue: tensor memory -> registers -> combine -> int64 -> global,
-//               written in baseline order with coalesced 16-byte stores
-// Tensor memory holds two accumulator sets (D1, D2: 64 columns each) so the epilogue of
-// one item overlaps the MMAs of the next.  Every wait is bounded.
+//   warp 0       TMA producer
+//   warp 1       tensor-memory allocator and single-thread MMA issuer
+//   warps 2..5   epilogue: tensor memory -> registers -> lane-pair combine -> int64 ->
+//                baseline order, stored straight from registers
+//   warps 6..9   (raw only) converters: packed bytes -> fp16 K-major swizzled tiles
+// Shared memory is carved at launch: when the array has a single 64-input block every
+// item is a diagonal tile (B = A), so stages hold one tile and the rings get deeper.
+// Tensor memory holds two accumulators (128 columns each) so the epilogue of one item
+// overlaps the MMAs of the next.  Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
-#include <cstdio>
 #include <mutex>
 
 #include "corr_internal.h"
@@ -40,34 +54,45 @@
 namespace corr {
 namespace {
 
-constexpr int kThreads = 192;
 constexpr int kTileBytes = kBlockRows * kTimeBlock * 2;     // 16 KB: 128 rows x 64 fp16
-constexpr int kStagingStride = kBlockInputs + 1;            // 16-byte entries per staging row
-constexpr int kStagingBytes = kBlockInputs * kStagingStride * 16;
-constexpr uint32_t kTmemCols = 256;                         // 2 buffers x (D1 64 + D2 64)
+constexpr uint32_t kTmemCols = 256;                         // 2 accumulators x 128 columns
 constexpr uint64_t kWaitLimitNs = 2000000000ull;            // 2 s per wait
+constexpr int kMaxOpStages = 16;
+constexpr int kMaxRawStages = 32;
+constexpr int kBarBytes = 8 * (2 * kMaxOpStages + 2 * kMaxRawStages + 5) + 16;
+constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after barriers and alignment
 
-template <bool SPLIT>
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
+
+template <int MODE>
 struct Cfg {
-    static constexpr int kStages = SPLIT ? 2 : 4;
-    static constexpr int kTilesPerStage = SPLIT ? 4 : 2;     // A, B (+ A_lo, B_lo)
-    static constexpr int kStageBytes = kTilesPerStage * kTileBytes;
-    static constexpr int kRingBytes = kStages * kStageBytes;
-    static constexpr int kBarOffset = kRingBytes + kStagingBytes;
-    static constexpr int kSmemBytes = kBarOffset + 256 + 1024;  // barriers + alignment slack
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4);
+    static constexpr bool kSplit = (MODE == kPlanesBF16x3);
+    static constexpr int kThreads = kRaw ? 320 : 192;
+    static constexpr int kBps = MODE == kRaw8 ? 2 : 1;                    // packed bytes per sample
+    static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
+    static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
 };
 
 struct TcParams {
     int n_inputs;
     int n_chan;
     int nb;
-    int kp;
+    int kp;             // samples per dump rounded up to 64
     int n_tiles;
     int64_t n_items;
-    int chunk_kb;       // k-blocks (64 samples) per exactly-flushed chunk
+    int chunk_kb;       // 64-sample blocks per exactly-flushed chunk
     int accumulate;
     void* vis;
     int* status;
+    // shared-memory carve-up (bytes; ring base is 1024-aligned)
+    int op_stages;
+    int op_stage_bytes;  // operand tiles of one stage: A (+ B when I != J) (x2 for hi/lo)
+    int b_offset;        // offset of the B tile(s) inside an op stage (0: B = A)
+    int raw_stages;
+    int raw_stage_bytes;
+    int raw_offset;      // start of the raw ring
+    int bar_offset;      // start of the barriers
 };
 
 __device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
@@ -85,31 +110,131 @@ __device__ __forceinline__ void record_error(int* status, volatile int* abort, i
     if (atomicCAS(status, 0, code) == 0) status[1] = detail;
 }
 
-template <bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
-    xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
+// byte offset of 16-byte chunk q (0..7) of row r in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw128_offset(int r, int q) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
+}
+
+// Two samples (t, t+1) of byte lane `sel` of words a, b (biased by +bias) -> half2 of the
+// signed values: fp16(1024 + u) has bit pattern 0x6400 | u for 0 <= u < 1024.
+__device__ __forceinline__ uint32_t pair_to_half2(uint32_t a, uint32_t b, uint32_t sel, __half2 bias) {
+    uint32_t r = __byte_perm(a, b, sel);
+    r = (r & 0x00FF00FFu) | 0x64006400u;
+    __half2 h = __hsub2(*reinterpret_cast<__half2*>(&r), bias);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ uint32_t lane_selector(int k) {
+    return (uint32_t)(k | (k << 4) | ((k + 4) << 8) | ((k + 4) << 12));
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Packed 8-bit tile [64 t][64 inputs][re, im] -> interleaved fp16 operand tile.
+// 128 converter threads; thread (cw, l) takes inputs 2l, 2l+1 and sample groups cw, cw + 4.
+// Byte lane k of a loaded word is re(2l), im(2l), re(2l+1), im(2l+1) = operand row 4l + k;
+// lanes start at different k so a quarter-warp's stores spread over the swizzle.
+__device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t dst, int ct) {
+    const int l = ct & 31, cw = ct >> 5;
+    const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
+#pragma unroll
+    for (int qq = 0; qq < 2; ++qq) {
+        const int q = cw + 4 * qq;
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(raw + (uint32_t)((8 * q + e) * 128 + 4 * l)) ^ 0x80808080u;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int k = (kk + l) & 3;
+            const uint32_t sel = lane_selector(k);
+            st_shared_v4(dst + sw128_offset(4 * l + k, q), pair_to_half2(w[0], w[1], sel, bias),
+                         pair_to_half2(w[2], w[3], sel, bias), pair_to_half2(w[4], w[5], sel, bias),
+                         pair_to_half2(w[6], w[7], sel, bias));
+        }
+    }
+}
+
+// Packed 4-bit tile [64 t][64 inputs] (high nibble re, low nibble im) -> interleaved fp16
+// operand tile.  Thread (cw, l): inputs 4m .. 4m+3 (m = l & 15), sample group 2cw + (l >> 4).
+__device__ __forceinline__ void convert_tile4(uint32_t raw, uint32_t dst, int ct) {
+    const int l = ct & 31, cw = ct >> 5;
+    const int m = l & 15, q = 2 * cw + (l >> 4);
+    const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t w = ld_shared_u32(raw + (uint32_t)((8 * q + e) * 64 + 4 * m)) ^ 0x88888888u;
+        hi[e] = (w >> 4) & 0x0F0F0F0Fu;  // re + 8 per byte
+        lo[e] = w & 0x0F0F0F0Fu;         // im + 8 per byte
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = (kk + m) & 3;
+        const uint32_t sel = lane_selector(k);
+        const int row = 2 * (4 * m + k);
+        st_shared_v4(dst + sw128_offset(row, q), pair_to_half2(hi[0], hi[1], sel, bias),
+                     pair_to_half2(hi[2], hi[3], sel, bias), pair_to_half2(hi[4], hi[5], sel, bias),
+                     pair_to_half2(hi[6], hi[7], sel, bias));
+        st_shared_v4(dst + sw128_offset(row + 1, q), pair_to_half2(lo[0], lo[1], sel, bias),
+                     pair_to_half2(lo[2], lo[3], sel, bias), pair_to_half2(lo[4], lo[5], sel, bias),
+                     pair_to_half2(lo[6], lo[7], sel, bias));
+    }
+}
+
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
+    xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
                    const TcParams prm) {
-    using C = Cfg<SPLIT>;
+    using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* ring = smem;
-    uint8_t* staging = smem + C::kRingBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kBarOffset);
-    // bars: full[S], empty[S], acc_full[2], acc_empty[2], drain
-    const uint32_t bar_full = ptx::smem_u32(bars);
-    const uint32_t bar_empty = bar_full + 8 * C::kStages;
-    const uint32_t bar_acc_full = bar_empty + 8 * C::kStages;
+    uint8_t* rawring = smem + prm.raw_offset;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + prm.bar_offset);
+    const int OS = prm.op_stages, RS = prm.raw_stages;
+    // barriers: op_full[OS], op_empty[OS], raw_full[RS], raw_empty[RS], acc_full[2], acc_empty[2], drain
+    const uint32_t bar_op_full = ptx::smem_u32(bars);
+    const uint32_t bar_op_empty = bar_op_full + 8 * OS;
+    const uint32_t bar_raw_full = bar_op_empty + 8 * OS;
+    const uint32_t bar_raw_empty = bar_raw_full + 8 * RS;
+    const uint32_t bar_acc_full = bar_raw_empty + 8 * RS;
     const uint32_t bar_acc_empty = bar_acc_full + 16;
     const uint32_t bar_drain = bar_acc_empty + 16;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * OS + 2 * RS + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::kStages; ++s) {
-            ptx::mbar_init(bar_full + 8 * s, 1);
-            ptx::mbar_init(bar_empty + 8 * s, 1);
+        for (int s = 0; s < OS; ++s) {
+            ptx::mbar_init(bar_op_full + 8 * s, C::kRaw ? 4 : 1);
+            ptx::mbar_init(bar_op_empty + 8 * s, 1);
+        }
+        for (int s = 0; s < RS; ++s) {
+            ptx::mbar_init(bar_raw_full + 8 * s, 1);
+            ptx::mbar_init(bar_raw_empty + 8 * s, 4);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(bar_acc_full + 8 * b, 1);
@@ -118,8 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::mbar_init(bar_drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
-        ptx::prefetch_tensormap(&tmap_hi);
-        if (SPLIT) ptx::prefetch_tensormap(&tmap_lo);
+        ptx::prefetch_tensormap(&tmap_a);
+        if (C::kSplit) ptx::prefetch_tensormap(&tmap_b);
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(tmem_slot), kTmemCols);
@@ -135,20 +260,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            const int S = C::kRaw ? RS : OS;
+            const uint32_t bar_full = C::kRaw ? bar_raw_full : bar_op_full;
+            const uint32_t bar_empty = C::kRaw ? bar_raw_empty : bar_op_empty;
             int s = 0;
             uint32_t ph = 0;
-            uint32_t issued_parity[4] = {0, 0, 0, 0};
-            bool issued[4] = {false, false, false, false};
+            int64_t n_issued = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
                 const int tile = (int)(item % prm.n_tiles);
                 const int64_t dc = item / prm.n_tiles;
                 int I, J;
                 tile_coords(tile, prm.nb, I, J);
-                const int rowA = (int)((dc * prm.nb + I) * kBlockRows);
-                const int rowB = (int)((dc * prm.nb + J) * kBlockRows);
                 const bool same = (I == J);
-                const uint32_t bytes = (same ? 1u : 2u) * (SPLIT ? 2u : 1u) * (uint32_t)kTileBytes;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!ptx::mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, abort_flag, kWaitLimitNs)) {
                         record_error(prm.status, abort_flag, kDevTimeoutEmpty, kb);
@@ -156,31 +280,49 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     const uint32_t fb = bar_full + 8 * s;
-                    const uint32_t st = ptx::smem_u32(ring + s * C::kStageBytes);
-                    ptx::mbar_expect_tx(fb, bytes);
-                    ptx::tma_load_2d(st, &tmap_hi, kb * kTimeBlock, rowA, fb);
-                    if (!same) ptx::tma_load_2d(st + kTileBytes, &tmap_hi, kb * kTimeBlock, rowB, fb);
-                    if (SPLIT) {
-                        ptx::tma_load_2d(st + 2 * kTileBytes, &tmap_lo, kb * kTimeBlock, rowA, fb);
-                        if (!same) ptx::tma_load_2d(st + 3 * kTileBytes, &tmap_lo, kb * kTimeBlock, rowB, fb);
+                    if constexpr (C::kRaw) {
+                        const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
+                        const int d = (int)(dc / prm.n_chan), c = (int)(dc % prm.n_chan);
+                        ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)C::kRawTileBytes);
+                        tma_load_4d(st, &tmap_a, I * kBlockInputs * C::kBps, c, kb * kTimeBlock, d, fb);
+                        if (!same)
+                            tma_load_4d(st + C::kRawTileBytes, &tmap_a, J * kBlockInputs * C::kBps, c, kb * kTimeBlock,
+                                        d, fb);
+                    } else {
+                        const uint32_t st = ptx::smem_u32(ring + s * prm.op_stage_bytes);
+                        const int rowA = (int)((dc * prm.nb + I) * kBlockRows);
+                        const int rowB = (int)((dc * prm.nb + J) * kBlockRows);
+                        const uint32_t bo = (uint32_t)prm.b_offset;
+                        ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)(C::kTilesPerOperand * kTileBytes));
+                        ptx::tma_load_2d(st, &tmap_a, kb * kTimeBlock, rowA, fb);
+                        if (!same) ptx::tma_load_2d(st + bo, &tmap_a, kb * kTimeBlock, rowB, fb);
+                        if (C::kSplit) {
+                            ptx::tma_load_2d(st + kTileBytes, &tmap_b, kb * kTimeBlock, rowA, fb);
+                            if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &tmap_b, kb * kTimeBlock, rowB, fb);
+                        }
                     }
-                    issued[s] = true;
-                    issued_parity[s] = ph;
-                    if (++s == C::kStages) {
+                    ++n_issued;
+                    if (++s == S) {
                         s = 0;
                         ph ^= 1u;
                     }
                 }
             }
-            // make sure no copy of ours is still landing in shared memory when the CTA exits
-            for (int k = 0; k < C::kStages; ++k)
-                if (issued[k]) ptx::mbar_wait_bounded(bar_full + 8 * k, issued_parity[k], abort_flag, kWaitLimitNs);
+            // no copy of ours may still be landing in shared memory when the CTA exits:
+            // wait for the last phase issued on each stage
+            const int64_t n_last = n_issued < S ? n_issued : S;
+            for (int64_t k = 0; k < n_last; ++k) {
+                const int64_t idx = n_issued - 1 - k;           // k-th most recent issue
+                const int st = (int)(idx % S);
+                const uint32_t par = (uint32_t)((idx / S) & 1);
+                ptx::mbar_wait_bounded(bar_full + 8 * st, par, abort_flag, kWaitLimitNs);
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_f16(128, 64, SPLIT);
+            constexpr uint32_t idesc = ptx::idesc_f16(128, 128, C::kSplit);
             int s = 0;
             uint32_t ph = 0;
             int abuf = 0;
@@ -200,41 +342,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t d1 = tmem_base + (uint32_t)(abuf * 128);
-                    const uint32_t d2 = d1 + 64;
+                    const uint32_t d = tmem_base + (uint32_t)(abuf * 128);
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!ptx::mbar_wait_bounded(bar_full + 8 * s, ph, abort_flag, kWaitLimitNs)) {
+                        if (!ptx::mbar_wait_bounded(bar_op_full + 8 * s, ph, abort_flag, kWaitLimitNs)) {
                             record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
                             ok = false;
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t a_hi = ptx::smem_u32(ring + s * C::kStageBytes);
-                        const uint32_t b_hi = same ? a_hi : a_hi + kTileBytes;
-                        const uint32_t a_lo = a_hi + 2 * kTileBytes;
-                        const uint32_t b_lo = same ? a_lo : a_lo + kTileBytes;
+                        const uint32_t a_hi = ptx::smem_u32(ring + s * prm.op_stage_bytes);
+                        const uint32_t b_hi = same ? a_hi : a_hi + (uint32_t)prm.b_offset;
 #pragma unroll
                         for (int k = 0; k < kTimeBlock / 16; ++k) {
                             const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-                            const uint32_t ko = 32u * k;  // 16 fp16 = 32 bytes along the swizzled row
+                            const uint32_t ko = 32u * k;  // 16 elements = 32 bytes along the swizzled row
                             const uint64_t da = ptx::sw128_kmajor_desc(a_hi + ko);
-                            const uint64_t dbr = ptx::sw128_kmajor_desc(b_hi + ko);
-                            const uint64_t dbi = ptx::sw128_kmajor_desc(b_hi + 8192 + ko);
-                            ptx::mma_f16(d1, da, dbr, idesc, acc);
-                            ptx::mma_f16(d2, da, dbi, idesc, acc);
-                            if (SPLIT) {
-                                const uint64_t dal = ptx::sw128_kmajor_desc(a_lo + ko);
-                                const uint64_t dblr = ptx::sw128_kmajor_desc(b_lo + ko);
-                                const uint64_t dbli = ptx::sw128_kmajor_desc(b_lo + 8192 + ko);
-                                ptx::mma_f16(d1, da, dblr, idesc, 1u);   // h_i l_j
-                                ptx::mma_f16(d2, da, dbli, idesc, 1u);
-                                ptx::mma_f16(d1, dal, dbr, idesc, 1u);   // l_i h_j
-                                ptx::mma_f16(d2, dal, dbi, idesc, 1u);
+                            const uint64_t db = ptx::sw128_kmajor_desc(b_hi + ko);
+                            ptx::mma_f16(d, da, db, idesc, acc);
+                            if constexpr (C::kSplit) {
+                                const uint32_t a_lo = a_hi + kTileBytes;
+                                const uint32_t b_lo = b_hi + kTileBytes;
+                                ptx::mma_f16(d, da, ptx::sw128_kmajor_desc(b_lo + ko), idesc, 1u);   // h_i l_j
+                                ptx::mma_f16(d, ptx::sw128_kmajor_desc(a_lo + ko), db, idesc, 1u);   // l_i h_j
                             }
                         }
                         any = true;
-                        ptx::mma_commit(bar_empty + 8 * s);
-                        if (++s == C::kStages) {
+                        ptx::mma_commit(bar_op_empty + 8 * s);
+                        if (++s == OS) {
                             s = 0;
                             ph ^= 1u;
                         }
@@ -254,13 +388,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < 6) {
         // ---------------- epilogue (warps 2..5) ----------------
-        const int q = warp & 3;                  // tensor-memory lane quadrant of this warp
-        const int ew = warp - 2;                 // 0..3 within the epilogue group
-        const bool re_rows = q < 2;              // lanes 0..63 hold the real-part rows of A
-        const int i_loc = (q & 1) * 32 + lane;   // input within block I
+        // Lane L of quadrant q holds operand row 32q + L: input i_loc = 16q + L/2, real part
+        // for even L, imaginary part for odd L.  Per 32 columns (16 inputs j, re/im each)
+        // the even lane finishes j = 0..7 and the odd lane j = 8..15 of the chunk.
+        const int q = warp & 3;
+        const int i_loc = 16 * q + (lane >> 1);
+        const bool odd = lane & 1;
         const int64_t P = (int64_t)prm.n_inputs * (prm.n_inputs + 1) / 2;
+        constexpr bool kIntOut = !C::kSplit;
         int abuf = 0;
         uint32_t aph = 0;
         bool ok = true;
@@ -269,58 +406,72 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t dc = item / prm.n_tiles;
             int I, J;
             tile_coords(tile, prm.nb, I, J);
+            const int i = I * kBlockInputs + i_loc;
+            const bool row_ok = i < prm.n_inputs;
+            const int64_t row_base = dc * P + (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 - i;  // + j
             for (int kb0 = 0; kb0 < nkb; kb0 += prm.chunk_kb) {
-                bool got = ptx::mbar_wait_bounded(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
-                if (!got) record_error(prm.status, abort_flag, kDevTimeoutAccFull, kb0);
-                ptx::named_bar_sync(1, 128);
-                if (*abort_flag) {
+                // every lane observes the phase; the warp decides as one
+                const bool got = ptx::mbar_wait_bounded(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutAccFull, kb0);
                     ok = false;
                     break;
                 }
                 ptx::tc_fence_after();
+                const bool add = prm.accumulate || kb0 > 0;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * 128);
-                // two passes: real-part rows write, then imaginary-part rows add
-                for (int pass = 0; pass < 2; ++pass) {
-                    if ((pass == 0) == re_rows) {
 #pragma unroll 1
-                        for (int m = 0; m < 2; ++m) {
-                            uint32_t v1[32], v2[32];
-                            ptx::tmem_ld32(tbase + 32u * m, v1);
-                            ptx::tmem_ld32(tbase + 64u + 32u * m, v2);
-                            ptx::tmem_wait_ld();
-                            uint8_t* rowp = staging + (size_t)i_loc * kStagingStride * 16;
+                for (int m = 0; m < 4; ++m) {
+                    uint32_t v[32];
+                    __syncwarp();
+                    ptx::tmem_ld32(tbase + 32u * m, v);
+                    ptx::tmem_wait_ld();
+                    // exchange: the even lane keeps j-slots 0..7 and receives the odd lane's
+                    // (xi_i xr_j, xi_i xi_j) for them; the odd lane keeps 8..15 likewise
+                    uint32_t own0[8], own1[8], oth0[8], oth1[8];
 #pragma unroll
-                            for (int e = 0; e < 32; ++e) {
-                                const float f1 = __uint_as_float(v1[e]);
-                                const float f2 = __uint_as_float(v2[e]);
-                                const int jl = 32 * m + e;
-                                if constexpr (!SPLIT) {
-                                    longlong2* p = reinterpret_cast<longlong2*>(rowp) + jl;
-                                    if (re_rows) {
-                                        *p = make_longlong2(__float2ll_rn(f1), -__float2ll_rn(f2));
-                                    } else {
-                                        longlong2 o = *p;
-                                        o.x += __float2ll_rn(f2);
-                                        o.y += __float2ll_rn(f1);
-                                        *p = o;
-                                    }
-                                } else {
-                                    float2* p = reinterpret_cast<float2*>(rowp + 16 * jl);
-                                    if (re_rows) {
-                                        *p = make_float2(f1, -f2);
-                                    } else {
-                                        float2 o = *p;
-                                        o.x += f2;
-                                        o.y += f1;
-                                        *p = o;
-                                    }
-                                }
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t s0 = odd ? v[2 * k] : v[2 * k + 16];
+                        const uint32_t s1 = odd ? v[2 * k + 1] : v[2 * k + 17];
+                        oth0[k] = __shfl_xor_sync(0xffffffffu, s0, 1);
+                        oth1[k] = __shfl_xor_sync(0xffffffffu, s1, 1);
+                        own0[k] = odd ? v[2 * k + 16] : v[2 * k];
+                        own1[k] = odd ? v[2 * k + 17] : v[2 * k + 1];
+                    }
+                    const int j0 = J * kBlockInputs + 16 * m + (odd ? 8 : 0);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int j = j0 + k;
+                        if (!row_ok || j < i || j >= prm.n_inputs) continue;
+                        // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row
+                        const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                        const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                        const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                        const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
+                        if constexpr (kIntOut) {
+                            longlong2 val = make_longlong2(__float2ll_rn(rr) + __float2ll_rn(ii),
+                                                           __float2ll_rn(ir) - __float2ll_rn(ri));
+                            longlong2* dst = reinterpret_cast<longlong2*>(prm.vis) + row_base + j;
+                            if (add) {
+                                const longlong2 old = *dst;
+                                val.x += old.x;
+                                val.y += old.y;
                             }
+                            *dst = val;
+                        } else {
+                            float2 val = make_float2(rr + ii, ir - ri);
+                            float2* dst = reinterpret_cast<float2*>(prm.vis) + row_base + j;
+                            if (add) {
+                                const float2 old = *dst;
+                                val.x += old.x;
+                                val.y += old.y;
+                            }
+                            *dst = val;
                         }
                     }
-                    ptx::named_bar_sync(1, 128);
                 }
-                // accumulator drained: hand the tensor-memory buffer back to the MMA warp
+                // accumulator drained (the loads completed at tcgen05.wait::ld): hand the
+                // tensor-memory buffer back to the MMA warp
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(bar_acc_empty + 8 * abuf);
@@ -328,41 +479,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                     abuf = 0;
                     aph ^= 1u;
                 }
-                // write the tile's valid baselines: row i, columns j in [max(J0, i), min(J0 + 64, N))
-                const bool add = prm.accumulate || kb0 > 0;
-                for (int r = ew; r < kBlockInputs; r += 4) {
-                    const int i = I * kBlockInputs + r;
-                    if (i >= prm.n_inputs) break;
-                    const int j_lo = max(J * kBlockInputs, i);
-                    const int j_hi = min(J * kBlockInputs + kBlockInputs, prm.n_inputs);
-                    if (j_lo >= j_hi) continue;
-                    const int64_t b0 = (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 + (j_lo - i);
-                    const int64_t o0 = dc * P + b0;
-                    const uint8_t* rowp = staging + (size_t)r * kStagingStride * 16;
-                    for (int j = j_lo + lane; j < j_hi; j += 32) {
-                        const int jl = j - J * kBlockInputs;
-                        if constexpr (!SPLIT) {
-                            longlong2 v = *reinterpret_cast<const longlong2*>(rowp + 16 * jl);
-                            longlong2* dst = reinterpret_cast<longlong2*>(prm.vis) + o0 + (j - j_lo);
-                            if (add) {
-                                longlong2 old = *dst;
-                                v.x += old.x;
-                                v.y += old.y;
-                            }
-                            *dst = v;
-                        } else {
-                            float2 v = *reinterpret_cast<const float2*>(rowp + 16 * jl);
-                            float2* dst = reinterpret_cast<float2*>(prm.vis) + o0 + (j - j_lo);
-                            if (add) {
-                                float2 old = *dst;
-                                v.x += old.x;
-                                v.y += old.y;
-                            }
-                            *dst = v;
-                        }
-                    }
+            }
+        }
+    } else if constexpr (C::kRaw) {
+        // ---------------- converters (warps 6..9) ----------------
+        const int ct = threadIdx.x - 192;   // 0..127
+        int rs = 0, os = 0;
+        uint32_t rph = 0, oph = 0;
+        bool ok = true;
+        for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
+            const int tile = (int)(item % prm.n_tiles);
+            int I, J;
+            tile_coords(tile, prm.nb, I, J);
+            const bool same = (I == J);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const bool got = ptx::mbar_wait_bounded(bar_raw_full + 8 * rs, rph, abort_flag, kWaitLimitNs) &&
+                                 ptx::mbar_wait_bounded(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, got)) {   // the warp decides as one
+                    if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
+                    ok = false;
+                    break;
                 }
-                ptx::named_bar_sync(1, 128);  // staging free for the next accumulator
+                const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes);
+                const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
+                if constexpr (MODE == kRaw8) {
+                    convert_tile8(raw, dst, ct);
+                    if (!same) convert_tile8(raw + C::kRawTileBytes, dst + prm.b_offset, ct);
+                } else {
+                    convert_tile4(raw, dst, ct);
+                    if (!same) convert_tile4(raw + C::kRawTileBytes, dst + prm.b_offset, ct);
+                }
+                fence_async_shared();   // generic-proxy writes -> visible to the tensor core
+                __syncwarp();
+                if (lane == 0) {
+                    ptx::mbar_arrive(bar_op_full + 8 * os);
+                    ptx::mbar_arrive(bar_raw_empty + 8 * rs);
+                }
+                if (++rs == RS) {
+                    rs = 0;
+                    rph ^= 1u;
+                }
+                if (++os == OS) {
+                    os = 0;
+                    oph ^= 1u;
+                }
             }
         }
     }
@@ -403,20 +563,26 @@ bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CU
     return r == CUDA_SUCCESS;
 }
 
-template <bool SPLIT>
-cudaError_t launch_impl(const Plan& p, const void* hi, const void* lo, int n_dumps, void* vis, int accumulate,
-                        cudaStream_t s) {
-    using C = Cfg<SPLIT>;
-    const int64_t rows = (int64_t)n_dumps * p.n_chan * p.nb * kBlockRows;
-    if (rows >= (int64_t)1 << 31) return cudaErrorInvalidValue;   // TMA row coordinates are int32
-    CUtensorMap mh, ml;
-    const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    if (!make_plane_map(&mh, hi, p.kp, rows, dt)) return cudaErrorInvalidValue;
-    if (SPLIT) {
-        if (!make_plane_map(&ml, lo, p.kp, rows, dt)) return cudaErrorInvalidValue;
-    } else {
-        ml = mh;
-    }
+// 4-D map over packed bytes [dump][time][chan][input*bps]; box = 64 inputs x 1 chan x 64 samples.
+// Out-of-range inputs (ragged last block) and samples (ragged last block) read as zero.
+bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, int n_time, int n_dumps, int bps) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t row = (cuuint64_t)n_inputs * bps;
+    cuuint64_t dims[4] = {row, (cuuint64_t)n_chan, (cuuint64_t)n_time, (cuuint64_t)n_dumps};
+    cuuint64_t strides[3] = {row, row * n_chan, row * n_chan * n_time};
+    cuuint32_t box[4] = {(cuuint32_t)(kBlockInputs * bps), 1, (cuuint32_t)kTimeBlock, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const Plan& p, const CUtensorMap& ma, const CUtensorMap& mb, int n_dumps, void* vis,
+                        int accumulate, cudaStream_t s) {
+    using C = Cfg<MODE>;
     TcParams prm;
     prm.n_inputs = p.n_inputs;
     prm.n_chan = p.n_chan;
@@ -425,15 +591,34 @@ cudaError_t launch_impl(const Plan& p, const void* hi, const void* lo, int n_dum
     prm.n_tiles = p.nb * (p.nb + 1) / 2;
     prm.n_items = (int64_t)n_dumps * p.n_chan * prm.n_tiles;
     // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
-    prm.chunk_kb = SPLIT ? (p.kp / kTimeBlock) : (p.sample_bits == 4 ? 2048 : 16);
+    prm.chunk_kb = C::kSplit ? (p.kp / kTimeBlock) : (p.sample_bits == 4 ? 2048 : 16);
     prm.accumulate = accumulate;
     prm.vis = vis;
     prm.status = p.d_status;
-    cudaError_t e = cudaFuncSetAttribute(xeng_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::kSmemBytes);
+    // shared-memory carve-up: a single input block means every tile is diagonal (B = A)
+    const bool diag_only = p.nb == 1;
+    const int operand_bytes = C::kTilesPerOperand * kTileBytes;
+    prm.op_stage_bytes = (diag_only ? 1 : 2) * operand_bytes;
+    prm.b_offset = diag_only ? 0 : operand_bytes;
+    if (C::kRaw) {
+        prm.raw_stage_bytes = (diag_only ? 1 : 2) * C::kRawTileBytes;
+        prm.op_stages = diag_only ? 4 : 3;
+        const int raw_space = kSmemBudget - prm.op_stages * prm.op_stage_bytes;
+        prm.raw_stages = raw_space / prm.raw_stage_bytes;
+        if (prm.raw_stages > kMaxRawStages) prm.raw_stages = kMaxRawStages;
+    } else {
+        prm.raw_stage_bytes = 0;
+        prm.raw_stages = 0;
+        prm.op_stages = kSmemBudget / prm.op_stage_bytes;
+        if (prm.op_stages > kMaxOpStages) prm.op_stages = kMaxOpStages;
+    }
+    prm.raw_offset = prm.op_stages * prm.op_stage_bytes;
+    prm.bar_offset = prm.raw_offset + prm.raw_stages * prm.raw_stage_bytes;
+    const int smem_bytes = prm.bar_offset + kBarBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(xeng_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
     const int grid = (int)(prm.n_items < p.n_sm ? prm.n_items : p.n_sm);
-    xeng_tc_kernel<SPLIT><<<grid, kThreads, C::kSmemBytes, s>>>(mh, ml, prm);
+    xeng_tc_kernel<MODE><<<grid, C::kThreads, smem_bytes, s>>>(ma, mb, prm);
     return cudaGetLastError();
 }
 
@@ -441,8 +626,34 @@ cudaError_t launch_impl(const Plan& p, const void* hi, const void* lo, int n_dum
 
 cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_planes_lo, int n_dumps, void* d_vis,
                            int accumulate, cudaStream_t s) {
-    if (d_planes_lo) return launch_impl<true>(p, d_planes, d_planes_lo, n_dumps, d_vis, accumulate, s);
-    return launch_impl<false>(p, d_planes, nullptr, n_dumps, d_vis, accumulate, s);
+    const int64_t rows = (int64_t)n_dumps * p.n_chan * p.nb * kBlockRows;
+    if (rows >= (int64_t)1 << 31) return cudaErrorInvalidValue;   // TMA row coordinates are int32
+    CUtensorMap mh, ml;
+    if (d_planes_lo) {
+        if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) ||
+            !make_plane_map(&ml, d_planes_lo, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16))
+            return cudaErrorInvalidValue;
+        return launch_mode<kPlanesBF16x3>(p, mh, ml, n_dumps, d_vis, accumulate, s);
+    }
+    if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16)) return cudaErrorInvalidValue;
+    return launch_mode<kPlanesF16>(p, mh, mh, n_dumps, d_vis, accumulate, s);
+}
+
+bool tc_raw_supported(const Plan& p) {
+    // TMA needs every global stride (the packed row of N samples) to be a multiple of 16 bytes
+    if (p.sample_bits != 4 && p.sample_bits != 8) return false;
+    const int64_t row = (int64_t)p.n_inputs * (p.sample_bits == 8 ? 2 : 1);
+    return row % 16 == 0;
+}
+
+cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                               cudaStream_t s) {
+    if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
+    CUtensorMap m;
+    const int bps = p.sample_bits == 8 ? 2 : 1;
+    if (!make_raw_map(&m, d_packed, p.n_inputs, p.n_chan, p.n_time, n_dumps, bps)) return cudaErrorInvalidValue;
+    if (p.sample_bits == 8) return launch_mode<kRaw8>(p, m, m, n_dumps, d_vis, accumulate, s);
+    return launch_mode<kRaw4>(p, m, m, n_dumps, d_vis, accumulate, s);
 }
 
 }  // namespace corr

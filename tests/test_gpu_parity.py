@@ -38,6 +38,9 @@ CASES = [  # (n, c, t, bits): ragged inputs, tails, several tiles, chunk boundar
     (1, 1, 1, 8), (2, 3, 33, 4), (3, 2, 64, 8), (17, 2, 100, 4), (63, 1, 65, 8), (64, 2, 127, 8),
     (65, 2, 70, 4), (100, 1, 200, 8), (130, 2, 129, 8), (200, 1, 64, 4), (64, 1, 1025, 8),
     (70, 1, 2100, 8), (257, 1, 96, 8),
+    # shapes whose packed rows are 16-byte multiples take the fused packed-sample path
+    (8, 2, 100, 8), (16, 3, 64, 4), (32, 2, 1000, 8), (96, 2, 130, 8), (96, 1, 77, 4), (128, 2, 256, 4),
+    (192, 1, 65, 8), (200, 1, 100, 8), (64, 3, 2049, 8), (48, 2, 300, 4),
 ]
 
 
@@ -88,6 +91,25 @@ def test_batch_of_dumps_and_accumulate(engine):
     assert np.array_equal(v2, 2 * init)
 
 
+@pytest.mark.parametrize("n,c,t,bits", [(128, 2, 200, 8), (64, 3, 1100, 8), (80, 2, 70, 4)])
+def test_plane_path_tc_and_fp32(n, c, t, bits):
+    # the unpack + cross-multiply split (the path for shapes TMA cannot address directly)
+    from paper_0906_1887_gb300 import corr
+    p = int_case(300 + n + t, n, c, t, bits)
+    ref = oracle.xcorr_int(p, n, c, t, bits)
+    plan = corr.Plan(n, c, t, bits)
+    x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
+    planes = torch.empty(plan.workspace_size(FP32), dtype=torch.uint8, device="cuda")
+    plan.unpack(x, planes)
+    for engine in (TC, FP32):
+        vis = plan.empty_vis(1, "cuda")
+        plan.run_planes(planes, vis, engine=engine)
+        torch.cuda.synchronize()
+        assert plan.check_device() == 0
+        assert np.array_equal(vis.cpu().numpy()[0], ref), engine
+    plan.close()
+
+
 def test_unpack_planes_match_oracle_unpack():
     from paper_0906_1887_gb300 import corr
     for bits in (4, 8):
@@ -102,9 +124,9 @@ def test_unpack_planes_match_oracle_unpack():
         got = planes.cpu().float().numpy().reshape(c, nb, 128, kp)
         re, im = oracle.unpack(p, n, c, t, bits)                 # [T][C][N]
         want = np.zeros((c, nb, 128, kp), np.float32)
-        for i in range(n):
-            want[:, i // 64, i % 64, :t] = re[:, :, i].T
-            want[:, i // 64, 64 + i % 64, :t] = im[:, :, i].T
+        for i in range(n):                                       # row 2r: re, row 2r + 1: im
+            want[:, i // 64, 2 * (i % 64), :t] = re[:, :, i].T
+            want[:, i // 64, 2 * (i % 64) + 1, :t] = im[:, :, i].T
         assert np.array_equal(got, want)
         plan.close()
 
