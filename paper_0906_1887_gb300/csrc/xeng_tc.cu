@@ -36,7 +36,7 @@
 //   warp 1       tensor-memory allocator and single-thread MMA issuer
 //   warps 2..5   epilogue: tensor memory -> registers -> lane-pair combine -> int64 ->
 //                baseline order, stored straight from registers
-//   warps 6..9   (raw only) converters: packed bytes -> fp16 K-major swizzled tiles
+//   warps 6..13  (raw only) converters: packed bytes -> fp16 K-major swizzled tiles
 // Shared memory is carved at launch: when the array has a single 64-input block every
 // item is a diagonal tile (B = A), so stages hold one tile and the rings get deeper.
 // Tensor memory holds two accumulators (128 columns each) so the epilogue of one item
@@ -55,7 +55,6 @@ namespace corr {
 namespace {
 
 constexpr int kTileBytes = kBlockRows * kTimeBlock * 2;     // 16 KB: 128 rows x 64 fp16
-constexpr uint32_t kTmemCols = 256;                         // 2 accumulators x 128 columns
 constexpr uint64_t kWaitLimitNs = 2000000000ull;            // 2 s per wait
 constexpr int kMaxOpStages = 16;
 constexpr int kMaxRawStages = 32;
@@ -68,7 +67,8 @@ template <int MODE>
 struct Cfg {
     static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4);
     static constexpr bool kSplit = (MODE == kPlanesBF16x3);
-    static constexpr int kThreads = kRaw ? 320 : 192;
+    static constexpr int kConvWarps = 8;
+    static constexpr int kThreads = kRaw ? 192 + 32 * kConvWarps : 192;
     static constexpr int kBps = MODE == kRaw8 ? 2 : 1;                    // packed bytes per sample
     static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
@@ -80,8 +80,11 @@ struct TcParams {
     int nb;
     int kp;             // samples per dump rounded up to 64
     int n_tiles;
-    int64_t n_items;
+    int cpi;            // channels per work item (2: adjacent channel pair, single-block arrays)
+    int n_groups;       // channel groups per dump = ceil(n_chan / cpi)
+    int64_t n_items;    // n_dumps * n_groups * n_tiles
     int chunk_kb;       // 64-sample blocks per exactly-flushed chunk
+    uint32_t tmem_cols; // 256 or 512 (two accumulator sets of cpi x 128 columns)
     int accumulate;
     void* vis;
     int* status;
@@ -115,11 +118,13 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int q) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
-// Two samples (t, t+1) of byte lane `sel` of words a, b (biased by +bias) -> half2 of the
-// signed values: fp16(1024 + u) has bit pattern 0x6400 | u for 0 <= u < 1024.
-__device__ __forceinline__ uint32_t pair_to_half2(uint32_t a, uint32_t b, uint32_t sel, __half2 bias) {
-    uint32_t r = __byte_perm(a, b, sel);
-    r = (r & 0x00FF00FFu) | 0x64006400u;
+// Two samples (t, t+1) taken from byte lane `sel` of words a, b -> half2 of the signed
+// values.  fp16(1024 + u) has bit pattern 0x6400 | u for 0 <= u < 1024; `flip` both inserts
+// the 0x64 exponent bytes and turns the two's-complement byte into u = x + offset
+// ((r & 0x00FF00FF) ^ flip is a single LOP3), and `bias` = 1024 + offset removes it again.
+__device__ __forceinline__ uint32_t pair_to_half2(uint32_t a, uint32_t b, uint32_t sel, uint32_t flip,
+                                                  __half2 bias) {
+    uint32_t r = (__byte_perm(a, b, sel) & 0x00FF00FFu) ^ flip;
     __half2 h = __hsub2(*reinterpret_cast<__half2*>(&r), bias);
     return *reinterpret_cast<uint32_t*>(&h);
 }
@@ -139,54 +144,52 @@ __device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
     return v;
 }
 
-// Packed 8-bit tile [64 t][64 inputs][re, im] -> interleaved fp16 operand tile.
-// 128 converter threads; thread (cw, l) takes inputs 2l, 2l+1 and sample groups cw, cw + 4.
+// Packed 8-bit tile [64 t][64 inputs][re, im] (t rows `pitch` bytes apart) -> interleaved fp16 operand tile.
+// Lane l of a converter warp takes inputs 2l, 2l+1 of sample group q (8 samples).
 // Byte lane k of a loaded word is re(2l), im(2l), re(2l+1), im(2l+1) = operand row 4l + k;
 // lanes start at different k so a quarter-warp's stores spread over the swizzle.
-__device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t dst, int ct) {
-    const int l = ct & 31, cw = ct >> 5;
+// `q` selects the group of 8 samples, so a tile is 8 groups x 32 threads.
+__device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t pitch, uint32_t dst, int l, int q) {
     const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
+    const uint32_t flip = 0x64806480u;   // exponent bytes 0x64, sign bit of each sample byte flipped
+    uint32_t w[8];
 #pragma unroll
-    for (int qq = 0; qq < 2; ++qq) {
-        const int q = cw + 4 * qq;
-        uint32_t w[8];
+    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(raw + (uint32_t)(8 * q + e) * pitch + 4u * l);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(raw + (uint32_t)((8 * q + e) * 128 + 4 * l)) ^ 0x80808080u;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const int k = (kk + l) & 3;
-            const uint32_t sel = lane_selector(k);
-            st_shared_v4(dst + sw128_offset(4 * l + k, q), pair_to_half2(w[0], w[1], sel, bias),
-                         pair_to_half2(w[2], w[3], sel, bias), pair_to_half2(w[4], w[5], sel, bias),
-                         pair_to_half2(w[6], w[7], sel, bias));
-        }
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = (kk + l) & 3;
+        const uint32_t sel = lane_selector(k);
+        st_shared_v4(dst + sw128_offset(4 * l + k, q), pair_to_half2(w[0], w[1], sel, flip, bias),
+                     pair_to_half2(w[2], w[3], sel, flip, bias), pair_to_half2(w[4], w[5], sel, flip, bias),
+                     pair_to_half2(w[6], w[7], sel, flip, bias));
     }
 }
 
-// Packed 4-bit tile [64 t][64 inputs] (high nibble re, low nibble im) -> interleaved fp16
-// operand tile.  Thread (cw, l): inputs 4m .. 4m+3 (m = l & 15), sample group 2cw + (l >> 4).
-__device__ __forceinline__ void convert_tile4(uint32_t raw, uint32_t dst, int ct) {
-    const int l = ct & 31, cw = ct >> 5;
-    const int m = l & 15, q = 2 * cw + (l >> 4);
+// Packed 4-bit tile [64 t][64 inputs] (rows `pitch` apart; high nibble re, low nibble im) ->
+// interleaved fp16 operand tile, in 4 slices of 32 lanes: lane l of slice s takes inputs
+// 4m .. 4m+3 (m = l & 15) of sample group q = 2s + (l >> 4).
+__device__ __forceinline__ void convert_tile4(uint32_t raw, uint32_t pitch, uint32_t dst, int l, int slice) {
+    const int m = l & 15, q = 2 * slice + (l >> 4);
     const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
+    const uint32_t flip = 0x64086408u;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const uint32_t w = ld_shared_u32(raw + (uint32_t)((8 * q + e) * 64 + 4 * m)) ^ 0x88888888u;
-        hi[e] = (w >> 4) & 0x0F0F0F0Fu;  // re + 8 per byte
-        lo[e] = w & 0x0F0F0F0Fu;         // im + 8 per byte
+        const uint32_t w = ld_shared_u32(raw + (uint32_t)(8 * q + e) * pitch + 4u * m);
+        hi[e] = (w >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
+        lo[e] = w & 0x0F0F0F0Fu;         // im nibble per byte
     }
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int k = (kk + m) & 3;
         const uint32_t sel = lane_selector(k);
         const int row = 2 * (4 * m + k);
-        st_shared_v4(dst + sw128_offset(row, q), pair_to_half2(hi[0], hi[1], sel, bias),
-                     pair_to_half2(hi[2], hi[3], sel, bias), pair_to_half2(hi[4], hi[5], sel, bias),
-                     pair_to_half2(hi[6], hi[7], sel, bias));
-        st_shared_v4(dst + sw128_offset(row + 1, q), pair_to_half2(lo[0], lo[1], sel, bias),
-                     pair_to_half2(lo[2], lo[3], sel, bias), pair_to_half2(lo[4], lo[5], sel, bias),
-                     pair_to_half2(lo[6], lo[7], sel, bias));
+        st_shared_v4(dst + sw128_offset(row, q), pair_to_half2(hi[0], hi[1], sel, flip, bias),
+                     pair_to_half2(hi[2], hi[3], sel, flip, bias), pair_to_half2(hi[4], hi[5], sel, flip, bias),
+                     pair_to_half2(hi[6], hi[7], sel, flip, bias));
+        st_shared_v4(dst + sw128_offset(row + 1, q), pair_to_half2(lo[0], lo[1], sel, flip, bias),
+                     pair_to_half2(lo[2], lo[3], sel, flip, bias), pair_to_half2(lo[4], lo[5], sel, flip, bias),
+                     pair_to_half2(lo[6], lo[7], sel, flip, bias));
     }
 }
 
@@ -229,12 +232,12 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OS; ++s) {
-            ptx::mbar_init(bar_op_full + 8 * s, C::kRaw ? 4 : 1);
+            ptx::mbar_init(bar_op_full + 8 * s, C::kRaw ? C::kConvWarps : 1);
             ptx::mbar_init(bar_op_empty + 8 * s, 1);
         }
         for (int s = 0; s < RS; ++s) {
             ptx::mbar_init(bar_raw_full + 8 * s, 1);
-            ptx::mbar_init(bar_raw_empty + 8 * s, 4);
+            ptx::mbar_init(bar_raw_empty + 8 * s, C::kConvWarps);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(bar_acc_full + 8 * b, 1);
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         if (C::kSplit) ptx::prefetch_tensormap(&tmap_b);
     }
     if (warp == 1) {
-        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), kTmemCols);
+        ptx::tmem_alloc(ptx::smem_u32(tmem_slot), prm.tmem_cols);
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
@@ -269,7 +272,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             bool ok = true;
             for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
                 const int tile = (int)(item % prm.n_tiles);
-                const int64_t dc = item / prm.n_tiles;
+                const int64_t dg = item / prm.n_tiles;            // dump * n_groups + group
+                const int64_t dc = dg;                            // planes path: cpi == 1
                 int I, J;
                 tile_coords(tile, prm.nb, I, J);
                 const bool same = (I == J);
@@ -282,8 +286,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                     const uint32_t fb = bar_full + 8 * s;
                     if constexpr (C::kRaw) {
                         const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
-                        const int d = (int)(dc / prm.n_chan), c = (int)(dc % prm.n_chan);
-                        ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)C::kRawTileBytes);
+                        const int d = (int)(dg / prm.n_groups), c = (int)(dg % prm.n_groups) * prm.cpi;
+                        // one box covers cpi adjacent channels (cpi x 64 inputs per sample row)
+                        ptx::mbar_expect_tx(fb, (same ? (uint32_t)prm.cpi : 2u) * (uint32_t)C::kRawTileBytes);
                         tma_load_4d(st, &tmap_a, I * kBlockInputs * C::kBps, c, kb * kTimeBlock, d, fb);
                         if (!same)
                             tma_load_4d(st + C::kRawTileBytes, &tmap_a, J * kBlockInputs * C::kBps, c, kb * kTimeBlock,
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t d = tmem_base + (uint32_t)(abuf * 128);
+                    const uint32_t dset = tmem_base + (uint32_t)(abuf * prm.cpi * 128);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!ptx::mbar_wait_bounded(bar_op_full + 8 * s, ph, abort_flag, kWaitLimitNs)) {
                             record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
@@ -350,20 +355,24 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t a_hi = ptx::smem_u32(ring + s * prm.op_stage_bytes);
-                        const uint32_t b_hi = same ? a_hi : a_hi + (uint32_t)prm.b_offset;
+                        const uint32_t stage = ptx::smem_u32(ring + s * prm.op_stage_bytes);
+                        for (int ch = 0; ch < prm.cpi; ++ch) {
+                            const uint32_t d = dset + (uint32_t)(ch * 128);
+                            const uint32_t a_hi = stage + (uint32_t)(ch * kTileBytes);
+                            const uint32_t b_hi = same ? a_hi : a_hi + (uint32_t)prm.b_offset;
 #pragma unroll
-                        for (int k = 0; k < kTimeBlock / 16; ++k) {
-                            const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-                            const uint32_t ko = 32u * k;  // 16 elements = 32 bytes along the swizzled row
-                            const uint64_t da = ptx::sw128_kmajor_desc(a_hi + ko);
-                            const uint64_t db = ptx::sw128_kmajor_desc(b_hi + ko);
-                            ptx::mma_f16(d, da, db, idesc, acc);
-                            if constexpr (C::kSplit) {
-                                const uint32_t a_lo = a_hi + kTileBytes;
-                                const uint32_t b_lo = b_hi + kTileBytes;
-                                ptx::mma_f16(d, da, ptx::sw128_kmajor_desc(b_lo + ko), idesc, 1u);   // h_i l_j
-                                ptx::mma_f16(d, ptx::sw128_kmajor_desc(a_lo + ko), db, idesc, 1u);   // l_i h_j
+                            for (int k = 0; k < kTimeBlock / 16; ++k) {
+                                const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+                                const uint32_t ko = 32u * k;  // 16 elements = 32 bytes along the swizzled row
+                                const uint64_t da = ptx::sw128_kmajor_desc(a_hi + ko);
+                                const uint64_t db = ptx::sw128_kmajor_desc(b_hi + ko);
+                                ptx::mma_f16(d, da, db, idesc, acc);
+                                if constexpr (C::kSplit) {
+                                    const uint32_t a_lo = a_hi + kTileBytes;
+                                    const uint32_t b_lo = b_hi + kTileBytes;
+                                    ptx::mma_f16(d, da, ptx::sw128_kmajor_desc(b_lo + ko), idesc, 1u);   // h_i l_j
+                                    ptx::mma_f16(d, ptx::sw128_kmajor_desc(a_lo + ko), db, idesc, 1u);   // l_i h_j
+                                }
                             }
                         }
                         any = true;
@@ -403,12 +412,15 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         bool ok = true;
         for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
             const int tile = (int)(item % prm.n_tiles);
-            const int64_t dc = item / prm.n_tiles;
+            const int64_t dg = item / prm.n_tiles;
+            const int64_t d = dg / prm.n_groups;
+            const int c0 = (int)(dg % prm.n_groups) * prm.cpi;
             int I, J;
             tile_coords(tile, prm.nb, I, J);
             const int i = I * kBlockInputs + i_loc;
             const bool row_ok = i < prm.n_inputs;
-            const int64_t row_base = dc * P + (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 - i;  // + j
+            // baseline b(i, j) = row_off + j within one channel's [P] block
+            const int64_t row_off = (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 - i;
             for (int kb0 = 0; kb0 < nkb; kb0 += prm.chunk_kb) {
                 // every lane observes the phase; the warp decides as one
                 const bool got = ptx::mbar_wait_bounded(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
@@ -419,7 +431,11 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                 }
                 ptx::tc_fence_after();
                 const bool add = prm.accumulate || kb0 > 0;
-                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * 128);
+                for (int ch = 0; ch < prm.cpi; ++ch) {
+                const bool ch_ok = row_ok && (c0 + ch) < prm.n_chan;
+                const int64_t row_base = (d * prm.n_chan + c0 + ch) * P + row_off;
+                const uint32_t tbase =
+                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * prm.cpi * 128 + ch * 128);
 #pragma unroll 1
                 for (int m = 0; m < 4; ++m) {
                     uint32_t v[32];
@@ -442,15 +458,16 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int j = j0 + k;
-                        if (!row_ok || j < i || j >= prm.n_inputs) continue;
+                        if (!ch_ok || j < i || j >= prm.n_inputs) continue;
                         // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row
                         const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
                         const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
                         const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
                         const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
                         if constexpr (kIntOut) {
-                            longlong2 val = make_longlong2(__float2ll_rn(rr) + __float2ll_rn(ii),
-                                                           __float2ll_rn(ir) - __float2ll_rn(ri));
+                            // every D element is an integer of magnitude <= 2^24: exact in int32
+                            longlong2 val = make_longlong2((long long)__float2int_rn(rr) + __float2int_rn(ii),
+                                                           (long long)__float2int_rn(ir) - __float2int_rn(ri));
                             longlong2* dst = reinterpret_cast<longlong2*>(prm.vis) + row_base + j;
                             if (add) {
                                 const longlong2 old = *dst;
@@ -470,6 +487,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                         }
                     }
                 }
+                }  // channels of the item
                 // accumulator drained (the loads completed at tcgen05.wait::ld): hand the
                 // tensor-memory buffer back to the MMA warp
                 ptx::tc_fence_before();
@@ -482,8 +500,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             }
         }
     } else if constexpr (C::kRaw) {
-        // ---------------- converters (warps 6..9) ----------------
-        const int ct = threadIdx.x - 192;   // 0..127
+        // ---------------- converters (warps 6..13) ----------------
+        const int cwarp = warp - 6;         // 0..7
         int rs = 0, os = 0;
         uint32_t rph = 0, oph = 0;
         bool ok = true;
@@ -502,12 +520,19 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                 }
                 const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes);
                 const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
-                if constexpr (MODE == kRaw8) {
-                    convert_tile8(raw, dst, ct);
-                    if (!same) convert_tile8(raw + C::kRawTileBytes, dst + prm.b_offset, ct);
-                } else {
-                    convert_tile4(raw, dst, ct);
-                    if (!same) convert_tile4(raw + C::kRawTileBytes, dst + prm.b_offset, ct);
+                constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
+                // The stage holds n_tiles packed tiles: cpi channels side by side in each sample
+                // row (diagonal items), or blocks I and J (off-diagonal items).  Each tile splits
+                // into kSlices warp-sized slices; the 8 converter warps take slices round-robin.
+                const int n_tl = same ? prm.cpi : 2;
+                const uint32_t pitch = same ? kRow * (uint32_t)prm.cpi : kRow;
+                constexpr int kSlices = MODE == kRaw8 ? 8 : 4;
+                for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
+                    const int tl = sl / kSlices, part = sl % kSlices;
+                    const uint32_t src = same ? raw + tl * kRow : raw + tl * C::kRawTileBytes;
+                    const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
+                    if constexpr (MODE == kRaw8) convert_tile8(src, pitch, out, lane, part);
+                    else convert_tile4(src, pitch, out, lane, part);
                 }
                 fence_async_shared();   // generic-proxy writes -> visible to the tensor core
                 __syncwarp();
@@ -530,7 +555,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1) ptx::tmem_dealloc(tmem_base, kTmemCols);
+    if (warp == 1) ptx::tmem_dealloc(tmem_base, prm.tmem_cols);
 }
 
 // ---- host side --------------------------------------------------------------------
@@ -563,15 +588,17 @@ bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CU
     return r == CUDA_SUCCESS;
 }
 
-// 4-D map over packed bytes [dump][time][chan][input*bps]; box = 64 inputs x 1 chan x 64 samples.
+// 4-D map over packed bytes [dump][time][chan][input*bps]; box = 64 inputs x box_chans channels
+// x 64 samples.
 // Out-of-range inputs (ragged last block) and samples (ragged last block) read as zero.
-bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, int n_time, int n_dumps, int bps) {
+bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, int n_time, int n_dumps, int bps,
+                  int box_chans) {
     auto enc = get_encode();
     if (!enc) return false;
     const cuuint64_t row = (cuuint64_t)n_inputs * bps;
     cuuint64_t dims[4] = {row, (cuuint64_t)n_chan, (cuuint64_t)n_time, (cuuint64_t)n_dumps};
     cuuint64_t strides[3] = {row, row * n_chan, row * n_chan * n_time};
-    cuuint32_t box[4] = {(cuuint32_t)(kBlockInputs * bps), 1, (cuuint32_t)kTimeBlock, 1};
+    cuuint32_t box[4] = {(cuuint32_t)(kBlockInputs * bps), (cuuint32_t)box_chans, (cuuint32_t)kTimeBlock, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -589,7 +616,12 @@ cudaError_t launch_mode(const Plan& p, const CUtensorMap& ma, const CUtensorMap&
     prm.nb = p.nb;
     prm.kp = p.kp;
     prm.n_tiles = p.nb * (p.nb + 1) / 2;
-    prm.n_items = (int64_t)n_dumps * p.n_chan * prm.n_tiles;
+    // single-block arrays: a work item takes an adjacent channel pair, so each TMA row
+    // fetches 2 x 64 inputs of packed bytes contiguously (256-byte runs for 8-bit samples)
+    prm.cpi = (C::kRaw && p.nb == 1) ? 2 : 1;
+    prm.n_groups = (p.n_chan + prm.cpi - 1) / prm.cpi;
+    prm.n_items = (int64_t)n_dumps * prm.n_groups * prm.n_tiles;
+    prm.tmem_cols = prm.cpi == 2 ? 512u : 256u;
     // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
     prm.chunk_kb = C::kSplit ? (p.kp / kTimeBlock) : (p.sample_bits == 4 ? 2048 : 16);
     prm.accumulate = accumulate;
@@ -598,10 +630,10 @@ cudaError_t launch_mode(const Plan& p, const CUtensorMap& ma, const CUtensorMap&
     // shared-memory carve-up: a single input block means every tile is diagonal (B = A)
     const bool diag_only = p.nb == 1;
     const int operand_bytes = C::kTilesPerOperand * kTileBytes;
-    prm.op_stage_bytes = (diag_only ? 1 : 2) * operand_bytes;
+    prm.op_stage_bytes = (diag_only ? prm.cpi : 2) * operand_bytes;
     prm.b_offset = diag_only ? 0 : operand_bytes;
     if (C::kRaw) {
-        prm.raw_stage_bytes = (diag_only ? 1 : 2) * C::kRawTileBytes;
+        prm.raw_stage_bytes = (diag_only ? prm.cpi : 2) * C::kRawTileBytes;
         prm.op_stages = diag_only ? 4 : 3;
         const int raw_space = kSmemBudget - prm.op_stages * prm.op_stage_bytes;
         prm.raw_stages = raw_space / prm.raw_stage_bytes;
@@ -651,7 +683,9 @@ cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps,
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
     CUtensorMap m;
     const int bps = p.sample_bits == 8 ? 2 : 1;
-    if (!make_raw_map(&m, d_packed, p.n_inputs, p.n_chan, p.n_time, n_dumps, bps)) return cudaErrorInvalidValue;
+    const int box_chans = p.nb == 1 ? 2 : 1;   // matches the channels per work item
+    if (!make_raw_map(&m, d_packed, p.n_inputs, p.n_chan, p.n_time, n_dumps, bps, box_chans))
+        return cudaErrorInvalidValue;
     if (p.sample_bits == 8) return launch_mode<kRaw8>(p, m, m, n_dumps, d_vis, accumulate, s);
     return launch_mode<kRaw4>(p, m, m, n_dumps, d_vis, accumulate, s);
 }
