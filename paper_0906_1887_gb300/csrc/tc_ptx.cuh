@@ -47,6 +47,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait that lets the thread sleep (up to `hint_ns`) until the phase completes, so a
+// waiting warp does not take issue slots from the warps doing work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of `bar` with the given parity to complete.  Gives up after
 // `limit_ns` of wall time or when *abort becomes non-zero; returns false then.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort,
@@ -54,12 +68,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if ((it & 15u) == 0u) {
             if (*abort) return false;
             if (globaltimer() - t0 > limit_ns) return false;
         }
     }
+}
+
+// Warp-wide wait: lane 0 polls, the warp learns the outcome (and is ordered after the
+// observed phase) through __syncwarp and a broadcast.
+__device__ __forceinline__ bool mbar_wait_bounded_warp(uint32_t bar, uint32_t parity, volatile int* abort,
+                                                       uint64_t limit_ns) {
+    uint32_t ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity, abort, limit_ns) ? 1u : 0u;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // ---- TMA ------------------------------------------------------------------------
@@ -100,6 +124,22 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Same MMA with the two 64-bit smem descriptors given as (lo, hi) 32-bit halves.  A
+// descriptor's low word is (start address >> 4) | (leading byte offset << 16); operands
+// inside one tile advance by adding (byte offset >> 4) to it, so the issuing thread
+// spends one 32-bit add per operand instead of rebuilding the descriptor.
+__device__ __forceinline__ void mma_f16_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t desc_hi,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %3};\n\t"
+        "mov.b64 db, {%2, %3};\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -146,6 +186,10 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
     d |= static_cast<uint64_t>(2u) << 61;                      // SWIZZLE_128B
     return d;
 }
+
+// Low and high words of sw128_kmajor_desc(saddr).
+__device__ __forceinline__ uint32_t sw128_desc_lo(uint32_t saddr) { return ((saddr >> 4) & 0x3FFFu) | (1u << 16); }
+__host__ __device__ constexpr uint32_t sw128_desc_hi() { return (1024u >> 4) | (1u << 14) | (2u << 29); }
 
 // Instruction descriptor of kind::f16: fp32 accumulator, A/B fp16 (or bf16), both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16) {

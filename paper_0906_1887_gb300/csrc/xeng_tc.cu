@@ -147,7 +147,7 @@ __device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
 // Packed 8-bit tile [64 t][64 inputs][re, im] (t rows `pitch` bytes apart) -> interleaved fp16 operand tile.
 // Lane l of a converter warp takes inputs 2l, 2l+1 of sample group q (8 samples).
 // Byte lane k of a loaded word is re(2l), im(2l), re(2l+1), im(2l+1) = operand row 4l + k;
-// lanes start at different k so a quarter-warp's stores spread over the swizzle.
+// lanes start at different k so a quarter-warp's stores never share a bank.
 // `q` selects the group of 8 samples, so a tile is 8 groups x 32 threads.
 __device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t pitch, uint32_t dst, int l, int q) {
     const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
@@ -157,7 +157,9 @@ __device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t pitch, uint
     for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(raw + (uint32_t)(8 * q + e) * pitch + 4u * l);
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        const int k = (kk + l) & 3;
+        // rows 4l + k of a quarter-warp (l = 8a .. 8a+7) land in 8 distinct swizzle chunks
+        // when k = (kk + l/2) & 3: even l give (row & 7) in 0..3, odd l in 4..7
+        const int k = (kk + (l >> 1)) & 3;
         const uint32_t sel = lane_selector(k);
         st_shared_v4(dst + sw128_offset(4 * l + k, q), pair_to_half2(w[0], w[1], sel, flip, bias),
                      pair_to_half2(w[2], w[3], sel, flip, bias), pair_to_half2(w[4], w[5], sel, flip, bias),
@@ -328,6 +330,10 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_f16(128, 128, C::kSplit);
+            constexpr uint32_t desc_hi = ptx::sw128_desc_hi();
+            const uint32_t desc_lo_ring = ptx::sw128_desc_lo(ptx::smem_u32(ring));
+            const uint32_t stage16 = (uint32_t)prm.op_stage_bytes >> 4;
+            const uint32_t boff16 = (uint32_t)prm.b_offset >> 4;
             int s = 0;
             uint32_t ph = 0;
             int abuf = 0;
@@ -355,25 +361,34 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t stage = ptx::smem_u32(ring + s * prm.op_stage_bytes);
-                        for (int ch = 0; ch < prm.cpi; ++ch) {
-                            const uint32_t d = dset + (uint32_t)(ch * 128);
-                            const uint32_t a_hi = stage + (uint32_t)(ch * kTileBytes);
-                            const uint32_t b_hi = same ? a_hi : a_hi + (uint32_t)prm.b_offset;
+                        // descriptor low words, in 16-byte units: the stage, then +1024 per
+                        // 16 KB tile, +2 per 16-sample step along the swizzled rows
+                        const uint32_t a0 = desc_lo_ring + (uint32_t)s * stage16;
+                        const uint32_t acc0 = kb > kb0 ? 1u : 0u;
+                        if constexpr (C::kSplit) {
+                            const uint32_t b0 = same ? a0 : a0 + boff16;
 #pragma unroll
-                            for (int k = 0; k < kTimeBlock / 16; ++k) {
-                                const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-                                const uint32_t ko = 32u * k;  // 16 elements = 32 bytes along the swizzled row
-                                const uint64_t da = ptx::sw128_kmajor_desc(a_hi + ko);
-                                const uint64_t db = ptx::sw128_kmajor_desc(b_hi + ko);
-                                ptx::mma_f16(d, da, db, idesc, acc);
-                                if constexpr (C::kSplit) {
-                                    const uint32_t a_lo = a_hi + kTileBytes;
-                                    const uint32_t b_lo = b_hi + kTileBytes;
-                                    ptx::mma_f16(d, da, ptx::sw128_kmajor_desc(b_lo + ko), idesc, 1u);   // h_i l_j
-                                    ptx::mma_f16(d, ptx::sw128_kmajor_desc(a_lo + ko), db, idesc, 1u);   // l_i h_j
-                                }
+                            for (int k = 0; k < 4; ++k) {
+                                const uint32_t ak = a0 + 2u * k, bk = b0 + 2u * k;
+                                ptx::mma_f16_lo(dset, ak, bk, desc_hi, idesc, (k > 0) | acc0);
+                                ptx::mma_f16_lo(dset, ak, bk + 1024u, desc_hi, idesc, 1u);   // h_i l_j
+                                ptx::mma_f16_lo(dset, ak + 1024u, bk, desc_hi, idesc, 1u);   // l_i h_j
                             }
+                        } else if (prm.cpi == 2) {
+                            // two channels, each its own diagonal tile (B = A), accumulators
+                            // interleaved so consecutive MMAs are independent
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const uint32_t acc = (k > 0) | acc0;
+                                ptx::mma_f16_lo(dset, a0 + 2u * k, a0 + 2u * k, desc_hi, idesc, acc);
+                                ptx::mma_f16_lo(dset + 128u, a0 + 1024u + 2u * k, a0 + 1024u + 2u * k, desc_hi, idesc,
+                                                acc);
+                            }
+                        } else {
+                            const uint32_t b0 = same ? a0 : a0 + boff16;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                ptx::mma_f16_lo(dset, a0 + 2u * k, b0 + 2u * k, desc_hi, idesc, (k > 0) | acc0);
                         }
                         any = true;
                         ptx::mma_commit(bar_op_empty + 8 * s);
@@ -422,9 +437,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             // baseline b(i, j) = row_off + j within one channel's [P] block
             const int64_t row_off = (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 - i;
             for (int kb0 = 0; kb0 < nkb; kb0 += prm.chunk_kb) {
-                // every lane observes the phase; the warp decides as one
-                const bool got = ptx::mbar_wait_bounded(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
-                if (!__all_sync(0xffffffffu, got)) {
+                // lane 0 observes the phase; the warp decides as one
+                const bool got = ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
+                if (!got) {
                     if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutAccFull, kb0);
                     ok = false;
                     break;
@@ -511,9 +526,10 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             tile_coords(tile, prm.nb, I, J);
             const bool same = (I == J);
             for (int kb = 0; kb < nkb; ++kb) {
-                const bool got = ptx::mbar_wait_bounded(bar_raw_full + 8 * rs, rph, abort_flag, kWaitLimitNs) &&
-                                 ptx::mbar_wait_bounded(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, kWaitLimitNs);
-                if (!__all_sync(0xffffffffu, got)) {   // the warp decides as one
+                const bool got =
+                    ptx::mbar_wait_bounded_warp(bar_raw_full + 8 * rs, rph, abort_flag, kWaitLimitNs) &&
+                    ptx::mbar_wait_bounded_warp(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, kWaitLimitNs);
+                if (!got) {   // the warp decides as one
                     if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
                     ok = false;
                     break;
