@@ -176,6 +176,57 @@ corr_status corr_xengine_run_static(const void *d_packed, int n_inputs, int n_ch
 corr_status corr_plan_check(corr_plan plan, int *device_error);
 
 /*
+ * ---- Batched uneven jobs in one persistent launch --------------------------------
+ *
+ * Large batches per GPU call make launch overhead negligible (Sec. 4, Sec. 5).  A batch
+ * packs many correlation jobs -- arrays of different sizes, channel counts and dump
+ * lengths -- into one flat list of work items walked by one grid of persistent
+ * tensor-core CTAs (one launch per sample mode present, 64 jobs per launch at most).
+ * Every job here is one dump of 4/8-bit samples whose packed rows are TMA-addressable:
+ * n_inputs * bytes-per-sample must be a multiple of 16 (CORR_EUNSUPPORTED otherwise).
+ */
+typedef struct {
+    int n_inputs, n_chan, n_time, sample_bits;
+    const void *packed;   /* device: [n_time][n_chan][n_inputs] packed samples, 16-byte aligned */
+    void *vis;            /* device: [n_chan][P][2] int64, 16-byte aligned */
+} corr_job;
+
+typedef struct corr_batch_s *corr_batch;   /* opaque, owned by the library */
+
+enum {
+    CORR_BATCH_GRAPH = 1,       /* capture the launch(es) into a CUDA graph; corr_batch_run replays it */
+    CORR_BATCH_AUTOTUNE = 2,    /* time candidate launch shapes on the batch's buffers, keep the fastest */
+    CORR_BATCH_ACCUMULATE = 4   /* add into the jobs' visibilities instead of overwriting them */
+};
+
+typedef struct {
+    int n_jobs, n_launches, graph, tuned;
+    int64_t n_items;            /* work items of all launches */
+    double cmacs;               /* algorithmic CMACs of one run: sum of P * n_chan * n_time */
+    int op_stages, pair_cpi, order;   /* the launch shape in use (0: default) */
+    float tune_ms;              /* the tuner's best time, ms (0 if not tuned) */
+} corr_batch_stats;
+
+/*
+ * Build a batch over jobs[0..n_jobs) (the library copies the descriptors; the caller
+ * keeps the buffers alive).  flags: CORR_BATCH_* bits.  With CORR_BATCH_AUTOTUNE the
+ * library runs the batch several times on its own buffers (overwriting the
+ * visibilities) and keeps the fastest launch shape for this set of job sizes; with a
+ * non-NULL tune_cache path the choice is read from / appended to that JSON-lines file.
+ * AUTOTUNE with ACCUMULATE is rejected (tuning runs would add into the accumulators).
+ * With CORR_BATCH_GRAPH the launches are captured into a CUDA graph once.  Allocates a
+ * small device status block and a stream.
+ */
+corr_status corr_batch_create(corr_batch *out, const corr_job *jobs, int n_jobs, int flags,
+                              const char *tune_cache);
+/* Run the batch on `stream` (graph replay when captured).  Asynchronous. */
+corr_status corr_batch_run(corr_batch b, void *stream);
+corr_status corr_batch_info(corr_batch b, corr_batch_stats *stats);
+/* Synchronise and read/clear the batch's device status block (see corr_plan_check). */
+corr_status corr_batch_check(corr_batch b, int *device_error);
+corr_status corr_batch_destroy(corr_batch b);
+
+/*
  * Divide int64 visibilities by the number of accumulated dumps, on the host, in
  * float64 (Fig. 1: accumulators are divided by the number of times they were
  * updated).  n_values = 2 * P * n_chan * n_dumps.  No GPU work.

@@ -38,6 +38,11 @@ SIGNATURES = {
     "corr_xengine_run_planes": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_static": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
     "corr_plan_check": (_c_int, [_vp, _P(_c_int)]),
+    "corr_batch_create": (_c_int, [_P(_vp), _vp, _c_int, _c_int, ctypes.c_char_p]),
+    "corr_batch_run": (_c_int, [_vp, _vp]),
+    "corr_batch_info": (_c_int, [_vp, _vp]),
+    "corr_batch_check": (_c_int, [_vp, _P(_c_int)]),
+    "corr_batch_destroy": (_c_int, [_vp]),
     "corr_average_host": (_c_int, [_vp, _c_sz, _c_i64, _vp]),
 }
 
@@ -163,6 +168,64 @@ class Plan:
         import torch
         n = self.workspace_size(engine, n_dumps)
         return torch.empty(max(n, 16), dtype=torch.uint8, device=device) if n else None
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int), ("n_chan", ctypes.c_int), ("n_time", ctypes.c_int),
+                ("sample_bits", ctypes.c_int), ("packed", ctypes.c_void_p), ("vis", ctypes.c_void_p)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_int), ("n_launches", ctypes.c_int), ("graph", ctypes.c_int),
+                ("tuned", ctypes.c_int), ("n_items", ctypes.c_int64), ("cmacs", ctypes.c_double),
+                ("op_stages", ctypes.c_int), ("pair_cpi", ctypes.c_int), ("order", ctypes.c_int),
+                ("tune_ms", ctypes.c_float)]
+
+
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_ACCUMULATE = 1, 2, 4
+
+
+class Batch:
+    """Many uneven jobs in one persistent launch per sample mode (optionally tuned, graph-captured).
+
+    ``jobs``: sequence of (n_inputs, n_chan, n_time, sample_bits, packed_tensor, vis_tensor).
+    """
+
+    def __init__(self, jobs, flags: int = 0, tune_cache: str | None = None):
+        arr = (JobDesc * len(jobs))()
+        for k, (n, c, t, bits, packed, vis) in enumerate(jobs):
+            arr[k] = JobDesc(n, c, t, bits, _ptr(packed), _ptr(vis))
+        self._keep = list(jobs)
+        h = ctypes.c_void_p()
+        check(lib().corr_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(jobs), flags,
+                                      tune_cache.encode() if tune_cache else None), "corr_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        check(lib().corr_batch_run(self._h, _stream_handle(stream)), "corr_batch_run")
+
+    def info(self) -> dict:
+        st = BatchStats()
+        check(lib().corr_batch_info(self._h, ctypes.byref(st)), "corr_batch_info")
+        return {f: getattr(st, f) for f, _ in BatchStats._fields_}
+
+    def check_device(self) -> int:
+        code = ctypes.c_int(0)
+        st = lib().corr_batch_check(self._h, ctypes.byref(code))
+        if st not in (OK, ETIMEOUT):
+            check(st, "corr_batch_check")
+        return code.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().corr_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version() -> int:

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/corr.h"
@@ -13,6 +14,7 @@ constexpr int kBlockInputs = 64;      // inputs per operand block (rows 0..63 re
 constexpr int kBlockRows = 128;       // rows of one plane block
 constexpr int kTimeBlock = 64;        // samples per pipeline stage (one 128-byte fp16 row)
 constexpr int kMaxInputs = 8192;
+constexpr int kMaxJobsPerLaunch = 64;  // jobs one packed tensor-core launch carries
 
 // Device error codes written to the plan's status block.
 enum DeviceError : int {
@@ -59,7 +61,25 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
                            void* d_vis, int accumulate, cudaStream_t s);
 // Fused path: packed 4/8-bit samples straight into the tensor-core kernel (no planes).
 bool tc_raw_supported(const Plan& p);
+bool tc_raw_supported(int n_inputs, int sample_bits);
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s);
+
+// One job of a packed (multi-job) tensor-core launch.
+struct TcJobSpec {
+    int n_inputs, n_chan, n_time, n_dumps, sample_bits;
+    const void* data;   // packed samples [n_dumps][T][C][N] (device)
+    void* vis;          // [n_dumps][C][P][2] int64 (device)
+    int cpi;            // channels per work item: 1, or 2 for arrays of at most 64 inputs
+};
+// Launch-shape knobs the autotuner chooses (0 = default).
+struct TcTuning {
+    int op_stages;
+};
+int tc_default_cpi(int n_inputs);
+bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp);
+// All jobs of one launch share a sample mode (4 or 8 bits) and must be TMA-addressable.
+cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
+                                    int* status, int n_sm, const TcTuning& tune, cudaStream_t s);
 
 }  // namespace corr

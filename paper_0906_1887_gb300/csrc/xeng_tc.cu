@@ -47,6 +47,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <new>
 
 #include "corr_internal.h"
 #include "tc_ptx.cuh"
@@ -74,28 +75,51 @@ struct Cfg {
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
 };
 
-struct TcParams {
+constexpr int kMaxJobs = kMaxJobsPerLaunch;   // jobs one launch packs (kernel-parameter space holds their maps)
+
+// One correlation job of a launch: its TMA map (packed bytes, or fp16/bf16 hi planes),
+// sizes, output and the flat index of its first work item.
+struct TcJob {
+    CUtensorMap map;
+    void* vis;
+    int64_t item_begin;  // first flat item of this job
     int n_inputs;
     int n_chan;
-    int nb;
-    int kp;             // samples per dump rounded up to 64
-    int n_tiles;
-    int cpi;            // channels per work item (2: adjacent channel pair, single-block arrays)
-    int n_groups;       // channel groups per dump = ceil(n_chan / cpi)
-    int64_t n_items;    // n_dumps * n_groups * n_tiles
-    int chunk_kb;       // 64-sample blocks per exactly-flushed chunk
-    uint32_t tmem_cols; // 256 or 512 (two accumulator sets of cpi x 128 columns)
+    int nb;              // 64-input blocks
+    int kp;              // samples per dump rounded up to 64
+    int n_tiles;         // nb (nb + 1) / 2 upper-triangle blocks
+    int cpi;             // channels per work item (2: adjacent channel pair, single-block arrays)
+    int n_groups;        // channel groups per dump = ceil(n_chan / cpi)
+    int chunk_kb;        // 64-sample blocks per exactly-flushed chunk
+};
+
+template <int MAXJ>
+struct TcLaunch {
+    CUtensorMap map_lo;  // BF16x3 lo planes (single-job launches only)
+    int n_jobs;
+    int64_t n_items;     // sum over jobs of n_dumps * n_groups * n_tiles
     int accumulate;
-    void* vis;
     int* status;
+    uint32_t tmem_cols;  // 256 or 512 (two accumulator sets of up to 2 x 128 columns)
     // shared-memory carve-up (bytes; ring base is 1024-aligned)
     int op_stages;
-    int op_stage_bytes;  // operand tiles of one stage: A (+ B when I != J) (x2 for hi/lo)
+    int op_stage_bytes;  // operand tiles of one stage: A (+ B, or a second channel) (x2 for hi/lo)
     int b_offset;        // offset of the B tile(s) inside an op stage (0: B = A)
     int raw_stages;
     int raw_stage_bytes;
     int raw_offset;      // start of the raw ring
     int bar_offset;      // start of the barriers
+    TcJob jobs[MAXJ];
+};
+
+// Work-item coordinates.  Items are visited in increasing order by every role, so the job
+// index only moves forward.
+struct ItemCtx {
+    int j;
+    int I, J;
+    bool same;
+    int64_t d;           // dump within the job
+    int c0;              // first channel of the item
 };
 
 __device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
@@ -106,6 +130,20 @@ __device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
     }
     I = i;
     J = i + rem;
+}
+
+template <int MAXJ>
+__device__ __forceinline__ void decode_item(const TcLaunch<MAXJ>& L, int64_t item, int& j, ItemCtx& it) {
+    while (j + 1 < L.n_jobs && item >= L.jobs[j + 1].item_begin) ++j;
+    const TcJob& jb = L.jobs[j];
+    const int64_t local = item - jb.item_begin;
+    const int tile = (int)(local % jb.n_tiles);
+    const int64_t dg = local / jb.n_tiles;
+    it.j = j;
+    it.d = dg / jb.n_groups;
+    it.c0 = (int)(dg % jb.n_groups) * jb.cpi;
+    tile_coords(tile, jb.nb, it.I, it.J);
+    it.same = it.I == it.J;
 }
 
 __device__ __forceinline__ void record_error(int* status, volatile int* abort, int code, int detail) {
@@ -208,10 +246,8 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
-    xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-                   const TcParams prm) {
+template <int MODE, int MAXJ>
+__global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const __grid_constant__ TcLaunch<MAXJ> prm) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -248,8 +284,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         ptx::mbar_init(bar_drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
-        ptx::prefetch_tensormap(&tmap_a);
-        if (C::kSplit) ptx::prefetch_tensormap(&tmap_b);
+        for (int j = 0; j < prm.n_jobs; ++j) ptx::prefetch_tensormap(&prm.jobs[j].map);
+        if (C::kSplit) ptx::prefetch_tensormap(&prm.map_lo);
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(tmem_slot), prm.tmem_cols);
@@ -260,7 +296,6 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int nkb = prm.kp / kTimeBlock;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -272,13 +307,14 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             uint32_t ph = 0;
             int64_t n_issued = 0;
             bool ok = true;
+            int jc = 0;
             for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-                const int tile = (int)(item % prm.n_tiles);
-                const int64_t dg = item / prm.n_tiles;            // dump * n_groups + group
-                const int64_t dc = dg;                            // planes path: cpi == 1
-                int I, J;
-                tile_coords(tile, prm.nb, I, J);
-                const bool same = (I == J);
+                ItemCtx it;
+                decode_item(prm, item, jc, it);
+                const TcJob& jb = prm.jobs[it.j];
+                const int I = it.I, J = it.J;
+                const bool same = it.same;
+                const int nkb = jb.kp / kTimeBlock;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!ptx::mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, abort_flag, kWaitLimitNs)) {
                         record_error(prm.status, abort_flag, kDevTimeoutEmpty, kb);
@@ -288,24 +324,24 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                     const uint32_t fb = bar_full + 8 * s;
                     if constexpr (C::kRaw) {
                         const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
-                        const int d = (int)(dg / prm.n_groups), c = (int)(dg % prm.n_groups) * prm.cpi;
                         // one box covers cpi adjacent channels (cpi x 64 inputs per sample row)
-                        ptx::mbar_expect_tx(fb, (same ? (uint32_t)prm.cpi : 2u) * (uint32_t)C::kRawTileBytes);
-                        tma_load_4d(st, &tmap_a, I * kBlockInputs * C::kBps, c, kb * kTimeBlock, d, fb);
+                        ptx::mbar_expect_tx(fb, (same ? (uint32_t)jb.cpi : 2u) * (uint32_t)C::kRawTileBytes);
+                        tma_load_4d(st, &jb.map, I * kBlockInputs * C::kBps, it.c0, kb * kTimeBlock, (int)it.d, fb);
                         if (!same)
-                            tma_load_4d(st + C::kRawTileBytes, &tmap_a, J * kBlockInputs * C::kBps, c, kb * kTimeBlock,
-                                        d, fb);
+                            tma_load_4d(st + C::kRawTileBytes, &jb.map, J * kBlockInputs * C::kBps, it.c0,
+                                        kb * kTimeBlock, (int)it.d, fb);
                     } else {
                         const uint32_t st = ptx::smem_u32(ring + s * prm.op_stage_bytes);
-                        const int rowA = (int)((dc * prm.nb + I) * kBlockRows);
-                        const int rowB = (int)((dc * prm.nb + J) * kBlockRows);
+                        const int64_t dc = it.d * jb.n_chan + it.c0;   // planes: one channel per item
+                        const int rowA = (int)((dc * jb.nb + I) * kBlockRows);
+                        const int rowB = (int)((dc * jb.nb + J) * kBlockRows);
                         const uint32_t bo = (uint32_t)prm.b_offset;
                         ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)(C::kTilesPerOperand * kTileBytes));
-                        ptx::tma_load_2d(st, &tmap_a, kb * kTimeBlock, rowA, fb);
-                        if (!same) ptx::tma_load_2d(st + bo, &tmap_a, kb * kTimeBlock, rowB, fb);
+                        ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
+                        if (!same) ptx::tma_load_2d(st + bo, &jb.map, kb * kTimeBlock, rowB, fb);
                         if (C::kSplit) {
-                            ptx::tma_load_2d(st + kTileBytes, &tmap_b, kb * kTimeBlock, rowA, fb);
-                            if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &tmap_b, kb * kTimeBlock, rowB, fb);
+                            ptx::tma_load_2d(st + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowA, fb);
+                            if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowB, fb);
                         }
                     }
                     ++n_issued;
@@ -340,20 +376,22 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
             uint32_t aph = 0;
             bool ok = true;
             bool any = false;
+            int jc = 0;
             for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-                const int tile = (int)(item % prm.n_tiles);
-                int I, J;
-                tile_coords(tile, prm.nb, I, J);
-                const bool same = (I == J);
-                for (int kb0 = 0; ok && kb0 < nkb; kb0 += prm.chunk_kb) {
-                    const int kb1 = min(nkb, kb0 + prm.chunk_kb);
+                ItemCtx it;
+                decode_item(prm, item, jc, it);
+                const TcJob& jb = prm.jobs[it.j];
+                const bool same = it.same;
+                const int nkb = jb.kp / kTimeBlock;
+                for (int kb0 = 0; ok && kb0 < nkb; kb0 += jb.chunk_kb) {
+                    const int kb1 = min(nkb, kb0 + jb.chunk_kb);
                     if (!ptx::mbar_wait_bounded(bar_acc_empty + 8 * abuf, aph ^ 1u, abort_flag, kWaitLimitNs)) {
                         record_error(prm.status, abort_flag, kDevTimeoutAccEmpty, kb0);
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t dset = tmem_base + (uint32_t)(abuf * prm.cpi * 128);
+                    const uint32_t dset = tmem_base + (uint32_t)(abuf * (int)(prm.tmem_cols / 2));
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!ptx::mbar_wait_bounded(bar_op_full + 8 * s, ph, abort_flag, kWaitLimitNs)) {
                             record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
@@ -374,7 +412,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                                 ptx::mma_f16_lo(dset, ak, bk + 1024u, desc_hi, idesc, 1u);   // h_i l_j
                                 ptx::mma_f16_lo(dset, ak + 1024u, bk, desc_hi, idesc, 1u);   // l_i h_j
                             }
-                        } else if (prm.cpi == 2) {
+                        } else if (jb.cpi == 2) {
                             // two channels, each its own diagonal tile (B = A), accumulators
                             // interleaved so consecutive MMAs are independent
 #pragma unroll
@@ -420,23 +458,24 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         const int q = warp & 3;
         const int i_loc = 16 * q + (lane >> 1);
         const bool odd = lane & 1;
-        const int64_t P = (int64_t)prm.n_inputs * (prm.n_inputs + 1) / 2;
         constexpr bool kIntOut = !C::kSplit;
         int abuf = 0;
         uint32_t aph = 0;
         bool ok = true;
+        int jc = 0;
         for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-            const int tile = (int)(item % prm.n_tiles);
-            const int64_t dg = item / prm.n_tiles;
-            const int64_t d = dg / prm.n_groups;
-            const int c0 = (int)(dg % prm.n_groups) * prm.cpi;
-            int I, J;
-            tile_coords(tile, prm.nb, I, J);
+            ItemCtx it;
+            decode_item(prm, item, jc, it);
+            const TcJob& jb = prm.jobs[it.j];
+            const int n_in = jb.n_inputs;
+            const int64_t P = (int64_t)n_in * (n_in + 1) / 2;
+            const int I = it.I, J = it.J;
+            const int nkb = jb.kp / kTimeBlock;
             const int i = I * kBlockInputs + i_loc;
-            const bool row_ok = i < prm.n_inputs;
+            const bool row_ok = i < n_in;
             // baseline b(i, j) = row_off + j within one channel's [P] block
-            const int64_t row_off = (int64_t)i * prm.n_inputs - (int64_t)i * (i - 1) / 2 - i;
-            for (int kb0 = 0; kb0 < nkb; kb0 += prm.chunk_kb) {
+            const int64_t row_off = (int64_t)i * n_in - (int64_t)i * (i - 1) / 2 - i;
+            for (int kb0 = 0; kb0 < nkb; kb0 += jb.chunk_kb) {
                 // lane 0 observes the phase; the warp decides as one
                 const bool got = ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
                 if (!got) {
@@ -446,11 +485,11 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                 }
                 ptx::tc_fence_after();
                 const bool add = prm.accumulate || kb0 > 0;
-                for (int ch = 0; ch < prm.cpi; ++ch) {
-                const bool ch_ok = row_ok && (c0 + ch) < prm.n_chan;
-                const int64_t row_base = (d * prm.n_chan + c0 + ch) * P + row_off;
-                const uint32_t tbase =
-                    tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * prm.cpi * 128 + ch * 128);
+                for (int ch = 0; ch < jb.cpi; ++ch) {
+                const bool ch_ok = row_ok && (it.c0 + ch) < jb.n_chan;
+                const int64_t row_base = (it.d * jb.n_chan + it.c0 + ch) * P + row_off;
+                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) +
+                                       (uint32_t)(abuf * (int)(prm.tmem_cols / 2) + ch * 128);
 #pragma unroll 1
                 for (int m = 0; m < 4; ++m) {
                     uint32_t v[32];
@@ -473,7 +512,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int j = j0 + k;
-                        if (!ch_ok || j < i || j >= prm.n_inputs) continue;
+                        if (!ch_ok || j < i || j >= n_in) continue;
                         // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row
                         const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
                         const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
@@ -483,7 +522,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                             // every D element is an integer of magnitude <= 2^24: exact in int32
                             longlong2 val = make_longlong2((long long)__float2int_rn(rr) + __float2int_rn(ii),
                                                            (long long)__float2int_rn(ir) - __float2int_rn(ri));
-                            longlong2* dst = reinterpret_cast<longlong2*>(prm.vis) + row_base + j;
+                            longlong2* dst = reinterpret_cast<longlong2*>(jb.vis) + row_base + j;
                             if (add) {
                                 const longlong2 old = *dst;
                                 val.x += old.x;
@@ -492,7 +531,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                             *dst = val;
                         } else {
                             float2 val = make_float2(rr + ii, ir - ri);
-                            float2* dst = reinterpret_cast<float2*>(prm.vis) + row_base + j;
+                            float2* dst = reinterpret_cast<float2*>(jb.vis) + row_base + j;
                             if (add) {
                                 const float2 old = *dst;
                                 val.x += old.x;
@@ -520,11 +559,13 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
         int rs = 0, os = 0;
         uint32_t rph = 0, oph = 0;
         bool ok = true;
+        int jc = 0;
         for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
-            const int tile = (int)(item % prm.n_tiles);
-            int I, J;
-            tile_coords(tile, prm.nb, I, J);
-            const bool same = (I == J);
+            ItemCtx it;
+            decode_item(prm, item, jc, it);
+            const int cpi = prm.jobs[it.j].cpi;
+            const bool same = it.same;
+            const int nkb = prm.jobs[it.j].kp / kTimeBlock;
             for (int kb = 0; kb < nkb; ++kb) {
                 const bool got =
                     ptx::mbar_wait_bounded_warp(bar_raw_full + 8 * rs, rph, abort_flag, kWaitLimitNs) &&
@@ -540,8 +581,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1)
                 // The stage holds n_tiles packed tiles: cpi channels side by side in each sample
                 // row (diagonal items), or blocks I and J (off-diagonal items).  Each tile splits
                 // into kSlices warp-sized slices; the 8 converter warps take slices round-robin.
-                const int n_tl = same ? prm.cpi : 2;
-                const uint32_t pitch = same ? kRow * (uint32_t)prm.cpi : kRow;
+                const int n_tl = same ? cpi : 2;
+                const uint32_t pitch = same ? kRow * (uint32_t)cpi : kRow;
                 constexpr int kSlices = MODE == kRaw8 ? 8 : 4;
                 for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
                     const int tl = sl / kSlices, part = sl % kSlices;
@@ -622,52 +663,80 @@ bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, 
     return r == CUDA_SUCCESS;
 }
 
-template <int MODE>
-cudaError_t launch_mode(const Plan& p, const CUtensorMap& ma, const CUtensorMap& mb, int n_dumps, void* vis,
-                        int accumulate, cudaStream_t s) {
+template <int MODE, int MAXJ>
+cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* maps, const CUtensorMap* map_lo,
+                        int accumulate, int* status, int n_sm, const TcTuning& tune, cudaStream_t s) {
     using C = Cfg<MODE>;
-    TcParams prm;
-    prm.n_inputs = p.n_inputs;
-    prm.n_chan = p.n_chan;
-    prm.nb = p.nb;
-    prm.kp = p.kp;
-    prm.n_tiles = p.nb * (p.nb + 1) / 2;
-    // single-block arrays: a work item takes an adjacent channel pair, so each TMA row
-    // fetches 2 x 64 inputs of packed bytes contiguously (256-byte runs for 8-bit samples)
-    prm.cpi = (C::kRaw && p.nb == 1) ? 2 : 1;
-    prm.n_groups = (p.n_chan + prm.cpi - 1) / prm.cpi;
-    prm.n_items = (int64_t)n_dumps * prm.n_groups * prm.n_tiles;
-    prm.tmem_cols = prm.cpi == 2 ? 512u : 256u;
-    // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
-    prm.chunk_kb = C::kSplit ? (p.kp / kTimeBlock) : (p.sample_bits == 4 ? 2048 : 16);
-    prm.accumulate = accumulate;
-    prm.vis = vis;
-    prm.status = p.d_status;
-    // shared-memory carve-up: a single input block means every tile is diagonal (B = A)
-    const bool diag_only = p.nb == 1;
-    const int operand_bytes = C::kTilesPerOperand * kTileBytes;
-    prm.op_stage_bytes = (diag_only ? prm.cpi : 2) * operand_bytes;
-    prm.b_offset = diag_only ? 0 : operand_bytes;
-    if (C::kRaw) {
-        prm.raw_stage_bytes = (diag_only ? prm.cpi : 2) * C::kRawTileBytes;
-        prm.op_stages = diag_only ? 4 : 3;
-        const int raw_space = kSmemBudget - prm.op_stages * prm.op_stage_bytes;
-        prm.raw_stages = raw_space / prm.raw_stage_bytes;
-        if (prm.raw_stages > kMaxRawStages) prm.raw_stages = kMaxRawStages;
-    } else {
-        prm.raw_stage_bytes = 0;
-        prm.raw_stages = 0;
-        prm.op_stages = kSmemBudget / prm.op_stage_bytes;
-        if (prm.op_stages > kMaxOpStages) prm.op_stages = kMaxOpStages;
+    if (n_jobs < 1 || n_jobs > MAXJ) return cudaErrorInvalidValue;
+    static_assert(sizeof(TcLaunch<MAXJ>) <= 32000, "kernel parameters exceed the launch limit");
+    auto* prm = new (std::nothrow) TcLaunch<MAXJ>();
+    if (!prm) return cudaErrorMemoryAllocation;
+    prm->n_jobs = n_jobs;
+    prm->accumulate = accumulate;
+    prm->status = status;
+    if (map_lo) prm->map_lo = *map_lo;
+    int64_t items = 0;
+    int op_tiles = 1, raw_tiles = 1;
+    bool any_pair = false;
+    for (int j = 0; j < n_jobs; ++j) {
+        const TcJobSpec& sp = specs[j];
+        TcJob& jb = prm->jobs[j];
+        jb.map = maps[j];
+        jb.vis = sp.vis;
+        jb.n_inputs = sp.n_inputs;
+        jb.n_chan = sp.n_chan;
+        jb.nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
+        jb.kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+        jb.n_tiles = jb.nb * (jb.nb + 1) / 2;
+        jb.cpi = sp.cpi;
+        jb.n_groups = (sp.n_chan + jb.cpi - 1) / jb.cpi;
+        // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
+        jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock) : (sp.sample_bits == 4 ? 2048 : 16);
+        jb.item_begin = items;
+        items += (int64_t)sp.n_dumps * jb.n_groups * jb.n_tiles;
+        const int tiles = jb.nb == 1 ? jb.cpi : 2;    // operand tiles one stage needs
+        op_tiles = tiles > op_tiles ? tiles : op_tiles;
+        raw_tiles = tiles > raw_tiles ? tiles : raw_tiles;
+        any_pair = any_pair || jb.cpi == 2;
     }
-    prm.raw_offset = prm.op_stages * prm.op_stage_bytes;
-    prm.bar_offset = prm.raw_offset + prm.raw_stages * prm.raw_stage_bytes;
-    const int smem_bytes = prm.bar_offset + kBarBytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(xeng_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-    const int grid = (int)(prm.n_items < p.n_sm ? prm.n_items : p.n_sm);
-    xeng_tc_kernel<MODE><<<grid, C::kThreads, smem_bytes, s>>>(ma, mb, prm);
-    return cudaGetLastError();
+    prm->n_items = items;
+    prm->tmem_cols = any_pair ? 512u : 256u;
+    // shared-memory carve-up
+    const int operand_bytes = C::kTilesPerOperand * kTileBytes;
+    prm->op_stage_bytes = op_tiles * operand_bytes;
+    prm->b_offset = operand_bytes;
+    if (C::kRaw) {
+        prm->raw_stage_bytes = raw_tiles * C::kRawTileBytes;
+        prm->op_stages = tune.op_stages > 0 ? tune.op_stages : (op_tiles == 2 ? 4 : 4);
+        int raw_space = kSmemBudget - prm->op_stages * prm->op_stage_bytes;
+        prm->raw_stages = raw_space / prm->raw_stage_bytes;
+        if (prm->raw_stages > kMaxRawStages) prm->raw_stages = kMaxRawStages;
+        if (prm->raw_stages < 2) {
+            delete prm;
+            return cudaErrorInvalidValue;
+        }
+    } else {
+        prm->raw_stage_bytes = 0;
+        prm->raw_stages = 0;
+        prm->op_stages = kSmemBudget / prm->op_stage_bytes;
+        if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
+    }
+    if (prm->op_stages < 2 || prm->op_stages > kMaxOpStages) {
+        delete prm;
+        return cudaErrorInvalidValue;
+    }
+    prm->raw_offset = prm->op_stages * prm->op_stage_bytes;
+    prm->bar_offset = prm->raw_offset + prm->raw_stages * prm->raw_stage_bytes;
+    const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
+    cudaError_t e =
+        cudaFuncSetAttribute(xeng_tc_kernel<MODE, MAXJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess && items > 0) {
+        const int grid = (int)(items < n_sm ? items : n_sm);
+        xeng_tc_kernel<MODE, MAXJ><<<grid, C::kThreads, smem_bytes, s>>>(*prm);
+        e = cudaGetLastError();
+    }
+    delete prm;
+    return e;
 }
 
 }  // namespace
@@ -677,33 +746,58 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
     const int64_t rows = (int64_t)n_dumps * p.n_chan * p.nb * kBlockRows;
     if (rows >= (int64_t)1 << 31) return cudaErrorInvalidValue;   // TMA row coordinates are int32
     CUtensorMap mh, ml;
+    TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_planes, d_vis, 1};
+    TcTuning tune{};
     if (d_planes_lo) {
         if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) ||
             !make_plane_map(&ml, d_planes_lo, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16))
             return cudaErrorInvalidValue;
-        return launch_mode<kPlanesBF16x3>(p, mh, ml, n_dumps, d_vis, accumulate, s);
+        return launch_jobs<kPlanesBF16x3, 1>(&sp, 1, &mh, &ml, accumulate, p.d_status, p.n_sm, tune, s);
     }
     if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16)) return cudaErrorInvalidValue;
-    return launch_mode<kPlanesF16>(p, mh, mh, n_dumps, d_vis, accumulate, s);
+    return launch_jobs<kPlanesF16, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s);
 }
 
-bool tc_raw_supported(const Plan& p) {
+bool tc_raw_supported(int n_inputs, int sample_bits) {
     // TMA needs every global stride (the packed row of N samples) to be a multiple of 16 bytes
-    if (p.sample_bits != 4 && p.sample_bits != 8) return false;
-    const int64_t row = (int64_t)p.n_inputs * (p.sample_bits == 8 ? 2 : 1);
+    if (sample_bits != 4 && sample_bits != 8) return false;
+    const int64_t row = (int64_t)n_inputs * (sample_bits == 8 ? 2 : 1);
     return row % 16 == 0;
+}
+
+bool tc_raw_supported(const Plan& p) { return tc_raw_supported(p.n_inputs, p.sample_bits); }
+
+int tc_default_cpi(int n_inputs) { return n_inputs <= kBlockInputs ? 2 : 1; }
+
+bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp) {
+    const int bps = sp.sample_bits == 8 ? 2 : 1;
+    return make_raw_map(map, sp.data, sp.n_inputs, sp.n_chan, sp.n_time, sp.n_dumps, bps, sp.cpi);
+}
+
+cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
+                                    int* status, int n_sm, const TcTuning& tune, cudaStream_t s) {
+    if (n_jobs < 1) return cudaErrorInvalidValue;
+    const int bits = specs[0].sample_bits;
+    for (int j = 0; j < n_jobs; ++j)
+        if (specs[j].sample_bits != bits || !tc_raw_supported(specs[j].n_inputs, bits) ||
+            (specs[j].cpi != 1 && specs[j].cpi != 2) || (specs[j].cpi == 2 && specs[j].n_inputs > kBlockInputs))
+            return cudaErrorInvalidValue;
+    if (n_jobs == 1) {
+        if (bits == 8) return launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        return launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+    }
+    if (n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+    if (bits == 8) return launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+    return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
 }
 
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s) {
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
+    TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_packed, d_vis, tc_default_cpi(p.n_inputs)};
     CUtensorMap m;
-    const int bps = p.sample_bits == 8 ? 2 : 1;
-    const int box_chans = p.nb == 1 ? 2 : 1;   // matches the channels per work item
-    if (!make_raw_map(&m, d_packed, p.n_inputs, p.n_chan, p.n_time, n_dumps, bps, box_chans))
-        return cudaErrorInvalidValue;
-    if (p.sample_bits == 8) return launch_mode<kRaw8>(p, m, m, n_dumps, d_vis, accumulate, s);
-    return launch_mode<kRaw4>(p, m, m, n_dumps, d_vis, accumulate, s);
+    if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
+    return launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, TcTuning{}, s);
 }
 
 }  // namespace corr
