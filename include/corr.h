@@ -227,6 +227,70 @@ corr_status corr_batch_check(corr_batch b, int *device_error);
 corr_status corr_batch_destroy(corr_batch b);
 
 /*
+ * ---- Real-time serving loop ------------------------------------------------------
+ *
+ * The prototype stages the next batch in host memory while the GPU correlates the
+ * previous one (Sec. 5, Table 3 notes).  A server takes correlation jobs from any number
+ * of host threads (the mailbox), admits them in arrival order by device footprint into
+ * an HBM arena allocated once (packed samples + visibilities + any workspace), and runs
+ * each on one of n_streams CUDA streams: host-to-device copy, X stage, status readback
+ * and, when host_vis is given, device-to-host copy of the visibilities -- so the copies
+ * of some jobs overlap the kernels of others.  A job that can never fit the budget is
+ * rejected at submission (CORR_EBUSY); one that fits waits until enough space is free.
+ * Engines: the tensor-core X stage for 4/8-bit samples, BF16x3 for float samples.
+ */
+typedef struct corr_server_s *corr_server;   /* opaque, owned by the library */
+
+typedef struct {
+    int n_inputs, n_chan, n_time, sample_bits;
+    const void *host_packed;  /* host: [n_time][n_chan][n_inputs] packed samples (pinned memory
+                                 from corr_host_alloc makes the copy asynchronous) */
+    void *host_vis;           /* host: [n_chan][P][2] output, or NULL to keep the result in the
+                                 arena (corr_job_result.d_vis) until corr_release */
+    int stream_tag;           /* caller's label of the input stream the job came from */
+} corr_job_desc;
+
+typedef struct {
+    int status;               /* CORR_PENDING, CORR_OK, CORR_ETIMEOUT (a device wait gave up),
+                                 CORR_ECUDA, or CORR_EBUSY (cancelled at shutdown) */
+    double t_submit, t_start, t_done;   /* host monotonic seconds */
+    float gpu_ms;             /* stream time from the job's first copy to its last */
+    void *d_vis;              /* device result while the job keeps it (host_vis == NULL) */
+} corr_job_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, rejected, cancelled, queued, running;
+    size_t arena_bytes, bytes_in_use, peak_bytes;
+} corr_server_stats;
+
+enum { CORR_SERVER_START_PAUSED = 1 };   /* admit nothing until corr_server_resume */
+
+/* Allocates the arena (hbm_budget_bytes of device memory), n_streams streams and two host
+ * threads (dispatcher, completion). */
+corr_status corr_server_create(corr_server *out, size_t hbm_budget_bytes, int n_streams, int flags);
+/* Queue a job (thread-safe, non-blocking).  The host buffers must stay valid until the
+ * job finishes.  CORR_EBUSY if the job can never fit the budget, CORR_EINVAL on bad sizes. */
+corr_status corr_submit(corr_server s, const corr_job_desc *job, uint64_t *job_id);
+/* Non-blocking: returns CORR_PENDING while the job is queued or running, else its final
+ * status; *res gets the timestamps. */
+corr_status corr_poll(corr_server s, uint64_t job_id, corr_job_result *res);
+/* Bounded wait for a job: CORR_ETIMEOUT if not finished within timeout_s seconds. */
+corr_status corr_wait(corr_server s, uint64_t job_id, double timeout_s, corr_job_result *res);
+/* Copy a finished job's device-resident visibilities (host_vis was NULL) to host memory
+ * (synchronous).  Do not call concurrently with corr_release of the same job. */
+corr_status corr_fetch(corr_server s, uint64_t job_id, void *host_vis);
+/* Forget a finished job; frees its device result if it kept one. */
+corr_status corr_release(corr_server s, uint64_t job_id);
+corr_status corr_server_resume(corr_server s);
+corr_status corr_server_get_stats(corr_server s, corr_server_stats *st);
+/* Cancel queued jobs, wait up to drain_timeout_s for running ones (CORR_ETIMEOUT if some
+ * are still running; the streams are then synchronised before memory is freed). */
+corr_status corr_server_destroy(corr_server s, double drain_timeout_s);
+/* Page-locked host memory for job buffers (cudaMallocHost). */
+corr_status corr_host_alloc(void **ptr, size_t bytes);
+corr_status corr_host_free(void *ptr);
+
+/*
  * Divide int64 visibilities by the number of accumulated dumps, on the host, in
  * float64 (Fig. 1: accumulators are divided by the number of times they were
  * updated).  n_values = 2 * P * n_chan * n_dumps.  No GPU work.

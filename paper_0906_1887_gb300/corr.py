@@ -43,6 +43,17 @@ SIGNATURES = {
     "corr_batch_info": (_c_int, [_vp, _vp]),
     "corr_batch_check": (_c_int, [_vp, _P(_c_int)]),
     "corr_batch_destroy": (_c_int, [_vp]),
+    "corr_server_create": (_c_int, [_P(_vp), _c_sz, _c_int, _c_int]),
+    "corr_submit": (_c_int, [_vp, _vp, _P(ctypes.c_uint64)]),
+    "corr_poll": (_c_int, [_vp, ctypes.c_uint64, _vp]),
+    "corr_wait": (_c_int, [_vp, ctypes.c_uint64, ctypes.c_double, _vp]),
+    "corr_release": (_c_int, [_vp, ctypes.c_uint64]),
+    "corr_fetch": (_c_int, [_vp, ctypes.c_uint64, _vp]),
+    "corr_server_resume": (_c_int, [_vp]),
+    "corr_server_get_stats": (_c_int, [_vp, _vp]),
+    "corr_server_destroy": (_c_int, [_vp, ctypes.c_double]),
+    "corr_host_alloc": (_c_int, [_P(_vp), _c_sz]),
+    "corr_host_free": (_c_int, [_vp]),
     "corr_average_host": (_c_int, [_vp, _c_sz, _c_i64, _vp]),
 }
 
@@ -220,6 +231,85 @@ class Batch:
         if self._h is not None and self._h.value:
             lib().corr_batch_destroy(self._h)
         self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServerJob(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int), ("n_chan", ctypes.c_int), ("n_time", ctypes.c_int),
+                ("sample_bits", ctypes.c_int), ("host_packed", ctypes.c_void_p), ("host_vis", ctypes.c_void_p),
+                ("stream_tag", ctypes.c_int)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_float), ("d_vis", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t)]
+
+
+SERVER_START_PAUSED = 1
+
+
+class Server:
+    """Real-time serving loop: submit jobs (host buffers), poll or wait by id."""
+
+    def __init__(self, hbm_budget_bytes: int, n_streams: int = 8, flags: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().corr_server_create(ctypes.byref(h), int(hbm_budget_bytes), n_streams, flags),
+              "corr_server_create")
+        self._h = h
+
+    def submit(self, n_inputs, n_chan, n_time, sample_bits, host_packed, host_vis=None, stream_tag=0) -> int:
+        d = ServerJob(n_inputs, n_chan, n_time, sample_bits, _ptr(host_packed), _ptr(host_vis), stream_tag)
+        jid = ctypes.c_uint64(0)
+        check(lib().corr_submit(self._h, ctypes.byref(d), ctypes.byref(jid)), "corr_submit")
+        return jid.value
+
+    def poll(self, job_id: int):
+        r = JobResult()
+        st = lib().corr_poll(self._h, job_id, ctypes.byref(r))
+        if st == EINVAL:
+            check(st, "corr_poll")
+        return st, r
+
+    def wait(self, job_id: int, timeout_s: float):
+        r = JobResult()
+        st = lib().corr_wait(self._h, job_id, float(timeout_s), ctypes.byref(r))
+        if st == EINVAL:
+            check(st, "corr_wait")
+        return st, r
+
+    def release(self, job_id: int):
+        check(lib().corr_release(self._h, job_id), "corr_release")
+
+    def fetch(self, job_id: int, host_vis):
+        """Copy a device-resident result (job submitted without host_vis) into host memory."""
+        check(lib().corr_fetch(self._h, job_id, _ptr(host_vis)), "corr_fetch")
+
+    def resume(self):
+        check(lib().corr_server_resume(self._h), "corr_server_resume")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().corr_server_get_stats(self._h, ctypes.byref(st)), "corr_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self, drain_timeout_s: float = 30.0) -> int:
+        st = OK
+        if self._h is not None and self._h.value:
+            st = lib().corr_server_destroy(self._h, float(drain_timeout_s))
+        self._h = None
+        return st
 
     def __del__(self):
         try:
