@@ -15,6 +15,15 @@ Printed on rank 0 as one JSON line:
   cpu_baseline the CPU oracle on a bounded sample of the same workload
 Options: --gpus N (torchrun, one rank per GPU, weak scaling: every rank runs the whole
 job on its own GPU), --steps K, --warmup W, --impl reference (the CPU oracle arm).
+
+Other workloads (--workload; each prints its own JSON line):
+  large   1024 inputs (512 dual-pol antennas) x 1536 channels x 256 samples, 20 dumps
+          per step, 8-bit Gaussian sigma 8; one launch per dump into a 2-dump output ring
+  batch   40 uneven jobs (8 each of 16/32/64/128/256 dual-pol antennas, 64..1024
+          channels, 128..2048 samples) in one persistent launch, autotuned, CUDA graph
+  serve   Poisson arrivals (mean 200 jobs/s) tagged over 8 streams, each job a random
+          array of 32..512 dual-pol antennas, 128..1536 channels, 256..1024 samples, 4 or
+          8 bits; p50/p99 latency, real-time factor, TeraCMAC/s
 """
 from __future__ import annotations
 
@@ -26,6 +35,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -153,6 +164,218 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- secondary workloads (--workload large | batch | serve) ----
+
+def run_large(args):
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    n, c, t, d = 1024, 1536, 256, 20
+    dev = torch.device("cuda", 0)
+    plan = corr.Plan(n, c, t, 8)
+    P = plan.n_baselines
+    packed = synth.torch_correlated_gaussian_packed8(d, t, c, n, 8.0, 0.0, 3000, dev)   # 16.1 GB
+    per_dump = t * c * n * 2
+    vis = [plan.empty_vis(1, dev) for _ in range(2)]                                  # 2 x 12.9 GB ring
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for k in range(d):
+            plan.run(packed[k], vis[k & 1], None, engine=corr.ENGINE_TC, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    cm = P * c * t * d
+    # one-dump launch times for the roofline
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run(packed[0], vis[0], None, engine=corr.ENGINE_TC, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = e0.elapsed_time(e1)
+    # FP32 engine on one dump
+    ws = plan.empty_workspace(corr.ENGINE_FP32, 1, dev)
+    plan.run(packed[0], vis[1], ws, engine=corr.ENGINE_FP32, stream=stream)
+    e0.record(stream)
+    plan.run(packed[0], vis[1], ws, engine=corr.ENGINE_FP32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    hbm, bf16, src = _peaks()
+    out_bytes = P * c * 16
+    bytes_launch = per_dump + out_bytes
+    gbs = bytes_launch / (ms_one / 1e3) / 1e9
+    line = {"metric": "X-engine TeraCMAC/s", "value": cm / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s",
+            "workload": "large1024_8bit: 1024 inputs x 1536 channels x 256 samples/dump x 20 dumps, sigma 8",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "real_time_factor": (t * d / CHANNEL_RATE_HZ) / (ms / 1e3),
+            "fp32_path": {"value": P * c * t / (ms32 / 1e3) / 1e12, "ms_per_dump": ms32,
+                          "speedup_tc_over_fp32": ms32 / ms_one},
+            "roofline": {"bound": "hbm", "kernel": "xeng_tc_kernel<raw8>", "achieved": gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes_per_launch": bytes_launch,
+                         "kernel_ms": ms_one, "tensor_tflops_algorithmic": 8.0 * P * c * t / (ms_one / 1e3) / 1e12,
+                         "peak_source": src},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def _batch_jobs(rng):
+    sizes = []
+    for ant in (16, 32, 64, 128, 256):
+        for _ in range(8):
+            sizes.append((2 * ant, 64 * int(rng.integers(1, 17)), 128 * int(rng.integers(1, 17))))
+    return sizes
+
+
+def run_batch(args):
+    import os
+    import tempfile
+
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    rng = np.random.default_rng(4000)
+    sizes = _batch_jobs(rng)
+    dev = torch.device("cuda", 0)
+    jobs, descs = [], []
+    for k, (n, c, t) in enumerate(sizes):
+        x = synth.torch_correlated_gaussian_packed8(1, t, c, n, 16.0, 0.0, 4000 + k, dev).reshape(-1)
+        v = torch.empty((c, n * (n + 1) // 2, 2), dtype=torch.int64, device=dev)
+        jobs.append((x, v))
+        descs.append((n, c, t, 8, x, v))
+    cm = sum(n * (n + 1) // 2 * c * t for n, c, t in sizes)
+    cache = os.path.join(tempfile.gettempdir(), "corr_batch_tune.jsonl")
+    t0 = time.time()
+    b = corr.Batch(descs, flags=corr.BATCH_GRAPH | corr.BATCH_AUTOTUNE, tune_cache=cache)
+    tune_s = time.time() - t0
+    info = b.info()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        b.run(stream)
+    torch.cuda.synchronize()
+    assert b.check_device() == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same jobs, one launch each
+    plans = [corr.Plan(n, c, t, 8) for n, c, t in sizes]
+    for p, (x, v) in zip(plans, jobs):
+        p.run(x, v, None, engine=corr.ENGINE_TC, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for p, (x, v) in zip(plans, jobs):
+            p.run(x, v, None, engine=corr.ENGINE_TC, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_each = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "X-engine TeraCMAC/s", "value": cm / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s",
+            "workload": "batch40: 8 each of 16/32/64/128/256 dual-pol antennas, 64..1024 channels, "
+                        "128..2048 samples, 8-bit Gaussian sigma 16, seed 4000",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "one_launch_per_job": {"ms_per_step": ms_each, "value": cm / (ms_each / 1e3) / 1e12},
+            "batch": info, "autotune_seconds": tune_s, "cmacs_per_step": cm}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+def run_serve(args):
+    import torch
+
+    from paper_0906_1887_gb300 import corr
+    rng = np.random.default_rng(5000)
+    max_in = 1024 * 1536 * 1024 * 2
+    # one pinned pool of random bytes serves every job's samples (any byte is a valid sample)
+    pool = torch.empty(max_in, dtype=torch.uint8).pin_memory()
+    chunk = torch.randint(0, 256, (1 << 26,), dtype=torch.uint8, generator=torch.Generator().manual_seed(5000))
+    for off in range(0, max_in, chunk.numel()):
+        m = min(chunk.numel(), max_in - off)
+        pool[off:off + m].copy_(chunk[:m])
+    srv = corr.Server(160 << 30, n_streams=8)
+    rate = 200.0
+    records = []
+    lock = threading.Lock()
+    pending = []
+    done_evt = threading.Event()
+
+    def waiter():
+        while not (done_evt.is_set() and not pending):
+            with lock:
+                item = pending.pop(0) if pending else None
+            if item is None:
+                time.sleep(0.0005)
+                continue
+            jid, n, c, t, bits = item
+            st, r = srv.wait(jid, 60.0)
+            with lock:
+                records.append((st, r.t_submit, r.t_start, r.t_done, n, c, t, bits, r.gpu_ms))
+            srv.release(jid)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    # warm-up: one job of each mode
+    for bits in (4, 8):
+        jid = srv.submit(64, 128, 256, bits, pool, None)
+        srv.wait(jid, 60.0)
+        srv.release(jid)
+    t_start = time.time()
+    t_next = t_start
+    n_sub = 0
+    while True:
+        now = time.time()
+        if now - t_start > args.serve_seconds:
+            break
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.002))
+            continue
+        t_next += rng.exponential(1.0 / rate)
+        a = 8 * int(rng.integers(4, 65))            # 32..512 antennas (multiples of 8)
+        n, c, t = 2 * a, int(rng.integers(128, 1537)), int(rng.integers(256, 1025))
+        bits = 4 if rng.random() < 0.5 else 8
+        jid = srv.submit(n, c, t, bits, pool, None, stream_tag=n_sub % 8)
+        n_sub += 1
+        with lock:
+            pending.append((jid, n, c, t, bits))
+    done_evt.set()
+    th.join(timeout=300)
+    wall = time.time() - t_start
+    srv.close()
+    ok = [r for r in records if r[0] == 0]
+    lat = np.array([r[3] - r[1] for r in ok]) * 1e3
+    tdump = np.array([r[6] / CHANNEL_RATE_HZ for r in ok]) * 1e3
+    cm = sum(r[4] * (r[4] + 1) // 2 * r[5] * r[6] for r in ok)
+    line = {"metric": "serving p99 latency / real-time factor / TeraCMAC/s", "unit": "ms",
+            "workload": "serve: Poisson 200 jobs/s over 8 stream tags, 32..512 dual-pol antennas, "
+                        "128..1536 channels, 256..1024 samples, 4/8-bit",
+            "value": float(np.percentile(lat, 99)) if len(lat) else None,
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "frac_within_dump_interval": float(np.mean(lat < tdump)) if len(lat) else None,
+            "jobs_submitted": n_sub, "jobs_ok": len(ok), "jobs_failed": len(records) - len(ok),
+            "wall_s": wall, "jobs_per_s": len(ok) / wall,
+            "real_time_factor": float(tdump.sum() / 1e3 / wall) if len(lat) else None,
+            "tera_cmac_per_s": cm / wall / 1e12,
+            "result": "visibilities left in HBM (device-resident), released after completion"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global N_DUMPS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -164,10 +387,15 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--dumps", type=int, default=N_DUMPS,
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
+    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
 
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload != "stream":
+        {"large": run_large, "batch": run_batch, "serve": run_serve}[args.workload](args)
         return
 
     import torch
