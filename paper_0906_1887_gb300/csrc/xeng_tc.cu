@@ -61,6 +61,10 @@ constexpr int kMaxOpStages = 16;
 constexpr int kMaxRawStages = 32;
 constexpr int kBarBytes = 8 * (2 * kMaxOpStages + 2 * kMaxRawStages + 5) + 16;
 constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after barriers and alignment
+// Staged epilogue: a warp's 16 rows of 64 baselines (16 bytes each), row pitch 65 x 16 B so
+// that the 16-byte stores of a quarter-warp fall in 8 distinct bank groups.
+constexpr int kStageRowBytes = 65 * 16;
+constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 
 enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
 
@@ -109,6 +113,8 @@ struct TcLaunch {
     int raw_stage_bytes;
     int raw_offset;      // start of the raw ring
     int bar_offset;      // start of the barriers
+    int staged;          // 1: epilogue stages rows in shared memory and bulk-copies them out
+    int staging_offset;  // start of the staging area (4 warps x 16 rows x kStageRowBytes)
     TcJob jobs[MAXJ];
 };
 
@@ -176,6 +182,10 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+__device__ __forceinline__ void st_shared_v2_u64(uint32_t addr, uint64_t a, uint64_t b) {
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -232,6 +242,21 @@ __device__ __forceinline__ void convert_tile4(uint32_t raw, uint32_t pitch, uint
                      pair_to_half2(lo[6], lo[7], sel, flip, bias));
     }
 }
+
+__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_add_u64(void* gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -459,6 +484,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         const int i_loc = 16 * q + (lane >> 1);
         const bool odd = lane & 1;
         constexpr bool kIntOut = !C::kSplit;
+        const uint32_t staging_q = ptx::smem_u32(smem + prm.staging_offset) + (uint32_t)(q * 16 * kStageRowBytes);
         int abuf = 0;
         uint32_t aph = 0;
         bool ok = true;
@@ -487,9 +513,15 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 const bool add = prm.accumulate || kb0 > 0;
                 for (int ch = 0; ch < jb.cpi; ++ch) {
                 const bool ch_ok = row_ok && (it.c0 + ch) < jb.n_chan;
-                const int64_t row_base = (it.d * jb.n_chan + it.c0 + ch) * P + row_off;
+                const int64_t chan_base = (it.d * jb.n_chan + it.c0 + ch) * P;
+                const int64_t row_base = chan_base + row_off;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) +
                                        (uint32_t)(abuf * (int)(prm.tmem_cols / 2) + ch * 128);
+                if (kIntOut && prm.staged) {
+                    // the bulk copies of the previous channel must have read the staging rows
+                    if (lane < 16) bulk_wait_read();
+                    __syncwarp();
+                }
 #pragma unroll 1
                 for (int m = 0; m < 4; ++m) {
                     uint32_t v[32];
@@ -509,27 +541,56 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         own1[k] = odd ? v[2 * k + 17] : v[2 * k + 1];
                     }
                     const int j0 = J * kBlockInputs + 16 * m + (odd ? 8 : 0);
+                    if constexpr (kIntOut) {
+                        // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row;
+                        // every D element is an integer of magnitude <= 2^24: exact in int32
+                        long long re[8], imv[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int j = j0 + k;
-                        if (!ch_ok || j < i || j >= n_in) continue;
-                        // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row
-                        const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
-                        const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
-                        const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
-                        const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
-                        if constexpr (kIntOut) {
-                            // every D element is an integer of magnitude <= 2^24: exact in int32
-                            longlong2 val = make_longlong2((long long)__float2int_rn(rr) + __float2int_rn(ii),
-                                                           (long long)__float2int_rn(ir) - __float2int_rn(ri));
-                            longlong2* dst = reinterpret_cast<longlong2*>(jb.vis) + row_base + j;
-                            if (add) {
-                                const longlong2 old = *dst;
-                                val.x += old.x;
-                                val.y += old.y;
+                        for (int k = 0; k < 8; ++k) {
+                            const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                            const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                            const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                            const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
+                            re[k] = (long long)__float2int_rn(rr) + __float2int_rn(ii);
+                            imv[k] = (long long)__float2int_rn(ir) - __float2int_rn(ri);
+                        }
+                        if (prm.staged) {
+                            // row lane/2 of this warp's staging rows, slots j - J0; odd lanes
+                            // write their slots rotated by 4 so a quarter-warp never shares banks
+                            const uint32_t rowp = staging_q + (uint32_t)(lane >> 1) * kStageRowBytes +
+                                                  (uint32_t)(j0 - J * kBlockInputs) * 16u;
+#pragma unroll
+                            for (int kk = 0; kk < 8; ++kk) {
+                                const int k_even = kk, k_odd = (kk + 4) & 7;
+                                const long long xr = odd ? re[k_odd] : re[k_even];
+                                const long long xi = odd ? imv[k_odd] : imv[k_even];
+                                const int k = odd ? k_odd : k_even;
+                                st_shared_v2_u64(rowp + 16u * (uint32_t)k, (uint64_t)xr, (uint64_t)xi);
                             }
-                            *dst = val;
                         } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int j = j0 + k;
+                                if (!ch_ok || j < i || j >= n_in) continue;
+                                longlong2 val = make_longlong2(re[k], imv[k]);
+                                longlong2* dst = reinterpret_cast<longlong2*>(jb.vis) + row_base + j;
+                                if (add) {
+                                    const longlong2 old = *dst;
+                                    val.x += old.x;
+                                    val.y += old.y;
+                                }
+                                *dst = val;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int j = j0 + k;
+                            if (!ch_ok || j < i || j >= n_in) continue;
+                            const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                            const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                            const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                            const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
                             float2 val = make_float2(rr + ii, ir - ri);
                             float2* dst = reinterpret_cast<float2*>(jb.vis) + row_base + j;
                             if (add) {
@@ -539,6 +600,28 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             }
                             *dst = val;
                         }
+                    }
+                }
+                if (kIntOut && prm.staged) {
+                    // make the staged rows visible to the bulk-copy engine, then lane r (< 16)
+                    // copies row r's valid run of baselines [max(J0, i_r), min(J0 + 64, N))
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane < 16) {
+                        const int ir_ = I * kBlockInputs + 16 * q + lane;
+                        const int j_lo = max(J * kBlockInputs, ir_);
+                        const int j_hi = min(J * kBlockInputs + kBlockInputs, n_in);
+                        if (ir_ < n_in && j_lo < j_hi && (it.c0 + ch) < jb.n_chan) {
+                            const int64_t b0 = chan_base + (int64_t)ir_ * n_in - (int64_t)ir_ * (ir_ - 1) / 2 +
+                                               (j_lo - ir_);
+                            const uint32_t src = staging_q + (uint32_t)lane * kStageRowBytes +
+                                                 (uint32_t)(j_lo - J * kBlockInputs) * 16u;
+                            void* dst = reinterpret_cast<longlong2*>(jb.vis) + b0;
+                            const uint32_t bytes = (uint32_t)(j_hi - j_lo) * 16u;
+                            if (add) bulk_add_u64(dst, src, bytes);
+                            else bulk_store(dst, src, bytes);
+                        }
+                        bulk_commit();
                     }
                 }
                 }  // channels of the item
@@ -553,6 +636,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 }
             }
         }
+        // every bulk copy of ours must have completed before the CTA exits
+        if (kIntOut && prm.staged && lane < 16) bulk_wait_all();
     } else if constexpr (C::kRaw) {
         // ---------------- converters (warps 6..13) ----------------
         const int cwarp = warp - 6;         // 0..7
@@ -701,14 +786,22 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     }
     prm->n_items = items;
     prm->tmem_cols = any_pair ? 512u : 256u;
-    // shared-memory carve-up
+    // shared-memory carve-up; multi-block arrays (output-heavy tiles) stage their epilogue rows
+    bool any_multi = false;
+    for (int j = 0; j < n_jobs; ++j) any_multi = any_multi || prm->jobs[j].nb > 1;
+    prm->staged = (!C::kSplit && any_multi) ? 1 : 0;
+    const int stage_space = prm->staged ? kStageBytes : 0;
     const int operand_bytes = C::kTilesPerOperand * kTileBytes;
     prm->op_stage_bytes = op_tiles * operand_bytes;
     prm->b_offset = operand_bytes;
     if (C::kRaw) {
         prm->raw_stage_bytes = raw_tiles * C::kRawTileBytes;
-        prm->op_stages = tune.op_stages > 0 ? tune.op_stages : (op_tiles == 2 ? 4 : 4);
-        int raw_space = kSmemBudget - prm->op_stages * prm->op_stage_bytes;
+        prm->op_stages = tune.op_stages > 0 ? tune.op_stages : (prm->staged ? 3 : 4);
+        // a requested depth that leaves fewer than 3 raw stages is reduced to what fits
+        while (prm->op_stages > 2 &&
+               kSmemBudget - stage_space - prm->op_stages * prm->op_stage_bytes < 3 * prm->raw_stage_bytes)
+            --prm->op_stages;
+        int raw_space = kSmemBudget - stage_space - prm->op_stages * prm->op_stage_bytes;
         prm->raw_stages = raw_space / prm->raw_stage_bytes;
         if (prm->raw_stages > kMaxRawStages) prm->raw_stages = kMaxRawStages;
         if (prm->raw_stages < 2) {
@@ -718,7 +811,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     } else {
         prm->raw_stage_bytes = 0;
         prm->raw_stages = 0;
-        prm->op_stages = kSmemBudget / prm->op_stage_bytes;
+        prm->op_stages = (kSmemBudget - stage_space) / prm->op_stage_bytes;
         if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
     }
     if (prm->op_stages < 2 || prm->op_stages > kMaxOpStages) {
@@ -726,7 +819,8 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         return cudaErrorInvalidValue;
     }
     prm->raw_offset = prm->op_stages * prm->op_stage_bytes;
-    prm->bar_offset = prm->raw_offset + prm->raw_stages * prm->raw_stage_bytes;
+    prm->staging_offset = prm->raw_offset + prm->raw_stages * prm->raw_stage_bytes;
+    prm->bar_offset = prm->staging_offset + stage_space;
     const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
     cudaError_t e =
         cudaFuncSetAttribute(xeng_tc_kernel<MODE, MAXJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
