@@ -169,6 +169,20 @@ corr_status corr_xengine_run_static(const void *d_packed, int n_inputs, int n_ch
                                     int sample_bits, void *d_vis, int accumulate, void *stream);
 
 /*
+ * The X stage of n_dumps dumps held in HOST memory, end to end: the prototype streams
+ * samples to the GPU in large batches and overlaps staging with the CMAC (Sec. 5).  The
+ * call splits the dumps into chunks of dumps_per_chunk (<= 0: about 256 MB of samples
+ * per chunk) and pipelines, on three internal streams, the host-to-device copy of chunk
+ * k+1, the X stage of chunk k and the device-to-host copy of chunk k-1, with double
+ * buffers in device memory that the plan allocates on first use (and keeps, growing it
+ * when a larger chunk needs it; freed by corr_plan_destroy).  host_packed: n_dumps x
+ * [T][C][N] packed samples; host_vis: n_dumps x [C][P][2].  Page-locked host memory
+ * (corr_host_alloc) lets the copies overlap.  Returns when host_vis holds every result.
+ */
+corr_status corr_xengine_run_host(corr_plan plan, const void *host_packed, int n_dumps, void *host_vis,
+                                  int dumps_per_chunk, int engine);
+
+/*
  * Read and clear the plan's device status block (synchronises with the device).
  * *device_error receives 0, or the code a kernel recorded when one of its bounded
  * waits gave up.  Returns CORR_ETIMEOUT in that case, else CORR_OK / CORR_ECUDA.

@@ -37,6 +37,7 @@ SIGNATURES = {
     "corr_xengine_run_batch": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_planes": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_static": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
+    "corr_xengine_run_host": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int]),
     "corr_plan_check": (_c_int, [_vp, _P(_c_int)]),
     "corr_batch_create": (_c_int, [_P(_vp), _vp, _c_int, _c_int, ctypes.c_char_p]),
     "corr_batch_run": (_c_int, [_vp, _vp]),
@@ -158,6 +159,12 @@ class Plan:
                    stream=None):
         check(lib().corr_xengine_run_planes(self._h, _ptr(planes), n_dumps, _ptr(vis), 1 if accumulate else 0,
                                             engine, _stream_handle(stream)), "corr_xengine_run_planes")
+
+    def run_host(self, host_packed, host_vis, n_dumps: int = 1, dumps_per_chunk: int = 0,
+                 engine: int = ENGINE_TC):
+        """End to end from host buffers: pipelined copy in / X stage / copy out (returns when done)."""
+        check(lib().corr_xengine_run_host(self._h, _ptr(host_packed), n_dumps, _ptr(host_vis), dumps_per_chunk,
+                                          engine), "corr_xengine_run_host")
 
     def check_device(self) -> int:
         code = ctypes.c_int(0)

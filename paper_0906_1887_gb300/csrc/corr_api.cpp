@@ -95,6 +95,11 @@ corr_status corr_plan_create(corr_plan* out, int n_inputs, int n_chan, int n_tim
 corr_status corr_plan_destroy(corr_plan plan) {
     if (!plan) return set_error(CORR_EINVAL, "corr_plan_destroy: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);
+    for (auto& st : p->pipe_stream)
+        if (st) cudaStreamDestroy(st);
+    for (auto& ev : p->pipe_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (p->pipe_dev) cudaFree(p->pipe_dev);
     if (p->d_status) cudaFree(p->d_status);
     delete p;
     return CORR_OK;
@@ -210,6 +215,76 @@ corr_status corr_xengine_run_planes(corr_plan plan, const void* d_planes, int n_
 corr_status corr_xengine_run(corr_plan plan, const void* d_packed, void* d_vis, void* d_workspace, int accumulate,
                              int engine, void* stream) {
     return corr_xengine_run_batch(plan, d_packed, 1, d_vis, d_workspace, accumulate, engine, stream);
+}
+
+corr_status corr_xengine_run_host(corr_plan plan, const void* host_packed, int n_dumps, void* host_vis,
+                                  int dumps_per_chunk, int engine) {
+    if (!plan || !host_packed || !host_vis) return set_error(CORR_EINVAL, "corr_xengine_run_host: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    const size_t in1 = packed_bytes_one(*p), out1 = vis_bytes_one(*p);
+    int chunk = dumps_per_chunk;
+    if (chunk <= 0) {   // default: about 256 MB of samples per chunk
+        chunk = (int)((size_t)256 << 20) / (int)(in1 > 0 ? in1 : 1);
+        if (chunk < 1) chunk = 1;
+    }
+    if (chunk > n_dumps) chunk = n_dumps;
+    size_t ws = 0;
+    corr_status st = corr_workspace_size(plan, engine, chunk, &ws);
+    if (st != CORR_OK) return st;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t in_c = up(in1 * chunk), out_c = up(out1 * chunk);
+    const size_t need = 2 * in_c + 2 * out_c + up(ws);
+    cudaError_t e = cudaSuccess;
+    if (need > p->pipe_bytes) {
+        if (p->pipe_dev) cudaFree(p->pipe_dev);
+        p->pipe_dev = nullptr;
+        p->pipe_bytes = 0;
+        e = cudaMalloc((void**)&p->pipe_dev, need);
+        if (e != cudaSuccess) return set_error(CORR_ENOMEM, "cudaMalloc(%zu) for the host pipeline failed", need);
+        p->pipe_bytes = need;
+    }
+    for (auto& s : p->pipe_stream)
+        if (!s && e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (auto& ev : p->pipe_ev)
+        if (!ev && e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "host pipeline set-up");
+    cudaStream_t s_in = p->pipe_stream[0], s_x = p->pipe_stream[1], s_out = p->pipe_stream[2];
+    // events per buffer b: in_ready[b] = pipe_ev[b], x_done[b] = pipe_ev[2 + b], out_free[b] = pipe_ev[4 + b]
+    char* in_buf[2] = {p->pipe_dev, p->pipe_dev + in_c};
+    char* out_buf[2] = {p->pipe_dev + 2 * in_c, p->pipe_dev + 2 * in_c + out_c};
+    char* wsp = ws ? p->pipe_dev + 2 * in_c + 2 * out_c : nullptr;
+    const int n_chunks = (n_dumps + chunk - 1) / chunk;
+    for (int k = 0; k < n_chunks && st == CORR_OK; ++k) {
+        const int b = k & 1;
+        const int nd = (k == n_chunks - 1) ? n_dumps - k * chunk : chunk;
+        // copy in: the buffer is free once the X stage of chunk k - 2 finished with it
+        if (k >= 2) e = cudaStreamWaitEvent(s_in, p->pipe_ev[2 + b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(in_buf[b], static_cast<const char*>(host_packed) + (size_t)k * chunk * in1, in1 * nd,
+                                cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(p->pipe_ev[b], s_in);
+        // X stage: needs the samples and a drained output buffer
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_x, p->pipe_ev[b], 0);
+        if (e == cudaSuccess && k >= 2) e = cudaStreamWaitEvent(s_x, p->pipe_ev[4 + b], 0);
+        if (e != cudaSuccess) break;
+        st = corr_xengine_run_batch(plan, in_buf[b], nd, out_buf[b], wsp, 0, engine, s_x);
+        if (st != CORR_OK) break;
+        e = cudaEventRecord(p->pipe_ev[2 + b], s_x);
+        // copy out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, p->pipe_ev[2 + b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char*>(host_vis) + (size_t)k * chunk * out1, out_buf[b], out1 * nd,
+                                cudaMemcpyDeviceToHost, s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(p->pipe_ev[4 + b], s_out);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s_out);
+    cudaError_t e3 = cudaStreamSynchronize(s_x);
+    cudaError_t e4 = cudaStreamSynchronize(s_in);
+    if (st != CORR_OK) return st;
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
+    if (e != cudaSuccess) return cuda_error(e, "host pipeline");
+    return CORR_OK;
 }
 
 corr_status corr_plan_check(corr_plan plan, int* device_error) {

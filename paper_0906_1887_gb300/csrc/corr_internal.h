@@ -37,6 +37,11 @@ struct Plan {
     int device = 0;
     int n_sm = 0;
     int* d_status = nullptr; // [4] device status words
+    // host-buffer pipeline (corr_xengine_run_host), created on first use
+    char* pipe_dev = nullptr;   // 2 x (chunk inputs) + 2 x (chunk outputs) + workspace
+    size_t pipe_bytes = 0;
+    cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};   // copy in, compute, copy out
+    cudaEvent_t pipe_ev[8] = {};
 };
 
 inline int64_t n_baselines(int64_t n) { return n * (n + 1) / 2; }

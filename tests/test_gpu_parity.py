@@ -110,6 +110,24 @@ def test_plane_path_tc_and_fp32(n, c, t, bits):
     plan.close()
 
 
+@pytest.mark.parametrize("n,bits,chunk", [(64, 8, 2), (40, 8, 3), (128, 4, 0)])
+def test_host_pipeline_end_to_end(n, bits, chunk):
+    # host buffers in, host buffers out: pipelined copies and X stage over chunks of dumps
+    from paper_0906_1887_gb300 import corr
+    c, t, d = 6, 300, 7
+    packs = [int_case(700 + k + n, n, c, t, bits) for k in range(d)]
+    host_in = torch.from_numpy(np.concatenate([x.reshape(-1) for x in packs])).pin_memory()
+    P = n * (n + 1) // 2
+    host_out = torch.full((d, c, P, 2), -1, dtype=torch.int64).pin_memory()
+    plan = corr.Plan(n, c, t, bits)
+    plan.run_host(host_in, host_out, n_dumps=d, dumps_per_chunk=chunk)
+    assert plan.check_device() == 0
+    out = host_out.numpy()
+    for k in range(d):
+        assert np.array_equal(out[k], oracle.xcorr_int(packs[k], n, c, t, bits)), k
+    plan.close()
+
+
 def test_unpack_planes_match_oracle_unpack():
     from paper_0906_1887_gb300 import corr
     for bits in (4, 8):
