@@ -45,6 +45,10 @@ N_INPUTS, N_CHAN, N_TIME, N_DUMPS, BITS = 64, 768, 1000, 200, 8
 SIGMA, RHO, SEED = 16.0, 0.1, 2000
 CHANNEL_RATE_HZ = 1.28e6 / 128.0
 WORKLOAD = "stream64_8bit: 64 inputs x 768 channels x 1000 samples/dump x 200 dumps, 8-bit complex Gaussian sigma=16 rho=0.1"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per dump of the fused kernel on this
+# workload, from one ncu capture of an 8-dump launch (786.7 MB read + 177.4 MB written), scaled
+# by dumps; set to None whenever the kernel changes until it is captured again.
+DRAM_BYTES_PER_DUMP = (786.671104e6 + 177.364736e6) / 8
 
 
 def _peaks():
@@ -516,7 +520,8 @@ def main():
     x_gbs = x_bytes / (ms_x / 1e3) / 1e9
     flops = 8.0 * cm_step
     roofline = {"bound": "hbm", "kernel": "xeng_tc_kernel<raw8>", "achieved": x_gbs, "peak": hbm_peak,
-                "unit": "GB/s", "frac": x_gbs / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": x_gbs / hbm_peak,
+                "traffic": DRAM_BYTES_PER_DUMP * N_DUMPS if DRAM_BYTES_PER_DUMP else None,
                 "peak_source": ("measured: MEASURED_PEAKS.json hbm_gbs" if peak_src == "measured" else peak_src),
                 "algorithmic_bytes_per_launch": x_bytes, "kernel_ms": ms_x,
                 "tensor_tflops_algorithmic": flops / (ms_x / 1e3) / 1e12,
