@@ -305,6 +305,18 @@ corr_status corr_host_alloc(void **ptr, size_t bytes);
 corr_status corr_host_free(void *ptr);
 
 /*
+ * Self-test of failure detection, with no GPU fault: runs the packed-sample tensor-core X
+ * stage of one dump with its mbarrier waits bounded by wait_limit_ms, while the producer
+ * withholds the first stage of work item `stall_item`, so the waiting role gives up,
+ * records its code in the plan's status block and every role of that CTA exits cleanly
+ * (in-flight copies and MMAs are drained first).  Synchronises; *device_error receives
+ * the recorded code (0 if nothing timed out; 1 = a loaded stage never arrived) and the
+ * call returns CORR_ETIMEOUT when one was recorded.  The plan stays usable afterwards.
+ */
+corr_status corr_selftest_stall(corr_plan plan, const void *d_packed, void *d_vis, int stall_item,
+                                int wait_limit_ms, int *device_error);
+
+/*
  * Divide int64 visibilities by the number of accumulated dumps, on the host, in
  * float64 (Fig. 1: accumulators are divided by the number of times they were
  * updated).  n_values = 2 * P * n_chan * n_dumps.  No GPU work.

@@ -39,6 +39,7 @@ SIGNATURES = {
     "corr_xengine_run_static": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
     "corr_xengine_run_host": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int]),
     "corr_plan_check": (_c_int, [_vp, _P(_c_int)]),
+    "corr_selftest_stall": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _P(_c_int)]),
     "corr_batch_create": (_c_int, [_P(_vp), _vp, _c_int, _c_int, ctypes.c_char_p]),
     "corr_batch_run": (_c_int, [_vp, _vp]),
     "corr_batch_info": (_c_int, [_vp, _vp]),
@@ -172,6 +173,13 @@ class Plan:
         if st not in (OK, ETIMEOUT):
             check(st, "corr_plan_check")
         return code.value
+
+    def selftest_stall(self, packed, vis, stall_item: int, wait_limit_ms: int = 100):
+        """Make one bounded device wait run out on purpose; returns (status, device_error)."""
+        code = ctypes.c_int(0)
+        st = lib().corr_selftest_stall(self._h, _ptr(packed), _ptr(vis), stall_item, wait_limit_ms,
+                                       ctypes.byref(code))
+        return st, code.value
 
     # ---- torch conveniences (allocation only) ----
     def vis_dtype(self):

@@ -287,6 +287,21 @@ corr_status corr_xengine_run_host(corr_plan plan, const void* host_packed, int n
     return CORR_OK;
 }
 
+corr_status corr_selftest_stall(corr_plan plan, const void* d_packed, void* d_vis, int stall_item, int wait_limit_ms,
+                                int* device_error) {
+    if (!plan || !d_packed || !d_vis || !device_error) return set_error(CORR_EINVAL, "corr_selftest_stall: NULL argument");
+    if (wait_limit_ms < 1 || wait_limit_ms > 10000) return set_error(CORR_EINVAL, "wait_limit_ms outside [1, 10000]");
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (!tc_raw_supported(*p))
+        return set_error(CORR_EUNSUPPORTED, "the self-test runs the packed-sample tensor-core kernel");
+    TcTuning tune;
+    tune.wait_limit_ns = (uint64_t)wait_limit_ms * 1000000ull;
+    tune.stall_item = stall_item;
+    cudaError_t e = launch_xeng_tc_raw(*p, d_packed, 1, d_vis, 0, nullptr, &tune);
+    if (e != cudaSuccess) return cuda_error(e, "self-test launch");
+    return corr_plan_check(plan, device_error);
+}
+
 corr_status corr_plan_check(corr_plan plan, int* device_error) {
     if (!plan) return set_error(CORR_EINVAL, "corr_plan_check: plan is NULL");
     Plan* p = reinterpret_cast<Plan*>(plan);

@@ -67,8 +67,9 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
 // Fused path: packed 4/8-bit samples straight into the tensor-core kernel (no planes).
 bool tc_raw_supported(const Plan& p);
 bool tc_raw_supported(int n_inputs, int sample_bits);
+struct TcTuning;
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
-                               cudaStream_t s);
+                               cudaStream_t s, const TcTuning* tune = nullptr);
 
 // One job of a packed (multi-job) tensor-core launch.
 struct TcJobSpec {
@@ -79,7 +80,9 @@ struct TcJobSpec {
 };
 // Launch-shape knobs the autotuner chooses (0 = default).
 struct TcTuning {
-    int op_stages;
+    int op_stages = 0;
+    uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
+    int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };
 int tc_default_cpi(int n_inputs);
 bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp);

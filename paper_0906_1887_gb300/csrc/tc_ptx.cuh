@@ -76,6 +76,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     }
 }
 
+// Wait bounded by time only (the abort flag is ignored): used when a role that gave up
+// must still see its own in-flight copies or MMAs complete before shared or tensor memory
+// is released.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 0u && globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
 // Warp-wide wait: lane 0 polls, the warp learns the outcome (and is ordered after the
 // observed phase) through __syncwarp and a broadcast.
 __device__ __forceinline__ bool mbar_wait_bounded_warp(uint32_t bar, uint32_t parity, volatile int* abort,

@@ -57,6 +57,7 @@ namespace {
 
 constexpr int kTileBytes = kBlockRows * kTimeBlock * 2;     // 16 KB: 128 rows x 64 fp16
 constexpr uint64_t kWaitLimitNs = 2000000000ull;            // 2 s per wait
+constexpr uint64_t kDrainLimitNs = 200000000ull;            // 0.2 s for in-flight work at exit
 constexpr int kMaxOpStages = 16;
 constexpr int kMaxRawStages = 32;
 constexpr int kBarBytes = 8 * (2 * kMaxOpStages + 2 * kMaxRawStages + 5) + 16;
@@ -113,6 +114,8 @@ struct TcLaunch {
     int raw_stage_bytes;
     int raw_offset;      // start of the raw ring
     int bar_offset;      // start of the barriers
+    uint64_t wait_limit_ns;  // bound of every mbarrier wait
+    int64_t stall_item;  // self-test: the producer withholds the first stage of this item (-1: none)
     int staged;          // 1: epilogue stages rows in shared memory and bulk-copies them out
     int staging_offset;  // start of the staging area (4 warps x 16 rows x kStageRowBytes)
     TcJob jobs[MAXJ];
@@ -330,7 +333,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             const uint32_t bar_empty = C::kRaw ? bar_raw_empty : bar_op_empty;
             int s = 0;
             uint32_t ph = 0;
-            int64_t n_issued = 0;
+            int64_t n_slots = 0;       // ring slots used so far (issued or withheld)
+            int64_t withheld = -1;     // the slot the self-test withheld
             bool ok = true;
             int jc = 0;
             for (int64_t item = blockIdx.x; ok && item < prm.n_items; item += gridDim.x) {
@@ -341,12 +345,21 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 const bool same = it.same;
                 const int nkb = jb.kp / kTimeBlock;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!ptx::mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, abort_flag, kWaitLimitNs)) {
+                    if (!ptx::mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, abort_flag, prm.wait_limit_ns)) {
                         record_error(prm.status, abort_flag, kDevTimeoutEmpty, kb);
                         ok = false;
                         break;
                     }
                     const uint32_t fb = bar_full + 8 * s;
+                    if (item == prm.stall_item && kb == 0) {
+                        // self-test of the bounded waits: nothing will complete this stage
+                        withheld = n_slots++;
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                        continue;
+                    }
                     if constexpr (C::kRaw) {
                         const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
                         // one box covers cpi adjacent channels (cpi x 64 inputs per sample row)
@@ -369,7 +382,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowB, fb);
                         }
                     }
-                    ++n_issued;
+                    ++n_slots;
                     if (++s == S) {
                         s = 0;
                         ph ^= 1u;
@@ -377,13 +390,16 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 }
             }
             // no copy of ours may still be landing in shared memory when the CTA exits:
-            // wait for the last phase issued on each stage
-            const int64_t n_last = n_issued < S ? n_issued : S;
-            for (int64_t k = 0; k < n_last; ++k) {
-                const int64_t idx = n_issued - 1 - k;           // k-th most recent issue
-                const int st = (int)(idx % S);
-                const uint32_t par = (uint32_t)((idx / S) & 1);
-                ptx::mbar_wait_bounded(bar_full + 8 * st, par, abort_flag, kWaitLimitNs);
+            // wait for the last phase issued on each stage (even after an abort)
+            if (!ok || *abort_flag) {
+                const int64_t n_last = n_slots < S ? n_slots : S;
+                for (int64_t k = 0; k < n_last; ++k) {
+                    const int64_t idx = n_slots - 1 - k;        // k-th most recent slot
+                    if (idx == withheld) continue;              // nothing was issued there
+                    const int st = (int)(idx % S);
+                    const uint32_t par = (uint32_t)((idx / S) & 1);
+                    ptx::mbar_wait_drain(bar_full + 8 * st, par, kDrainLimitNs);
+                }
             }
         }
         __syncwarp();
@@ -410,7 +426,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 const int nkb = jb.kp / kTimeBlock;
                 for (int kb0 = 0; ok && kb0 < nkb; kb0 += jb.chunk_kb) {
                     const int kb1 = min(nkb, kb0 + jb.chunk_kb);
-                    if (!ptx::mbar_wait_bounded(bar_acc_empty + 8 * abuf, aph ^ 1u, abort_flag, kWaitLimitNs)) {
+                    if (!ptx::mbar_wait_bounded(bar_acc_empty + 8 * abuf, aph ^ 1u, abort_flag, prm.wait_limit_ns)) {
                         record_error(prm.status, abort_flag, kDevTimeoutAccEmpty, kb0);
                         ok = false;
                         break;
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     ptx::tc_fence_after();
                     const uint32_t dset = tmem_base + (uint32_t)(abuf * (int)(prm.tmem_cols / 2));
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!ptx::mbar_wait_bounded(bar_op_full + 8 * s, ph, abort_flag, kWaitLimitNs)) {
+                        if (!ptx::mbar_wait_bounded(bar_op_full + 8 * s, ph, abort_flag, prm.wait_limit_ns)) {
                             record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
                             ok = false;
                             break;
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             // every MMA of ours must be complete before tensor memory is released
             if (any) {
                 ptx::mma_commit(bar_drain);
-                ptx::mbar_wait_bounded(bar_drain, 0, abort_flag, kWaitLimitNs);
+                ptx::mbar_wait_drain(bar_drain, 0, kDrainLimitNs);
             }
         }
         __syncwarp();
@@ -503,7 +519,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             const int64_t row_off = (int64_t)i * n_in - (int64_t)i * (i - 1) / 2 - i;
             for (int kb0 = 0; kb0 < nkb; kb0 += jb.chunk_kb) {
                 // lane 0 observes the phase; the warp decides as one
-                const bool got = ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, kWaitLimitNs);
+                const bool got = ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, prm.wait_limit_ns);
                 if (!got) {
                     if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutAccFull, kb0);
                     ok = false;
@@ -653,8 +669,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             const int nkb = prm.jobs[it.j].kp / kTimeBlock;
             for (int kb = 0; kb < nkb; ++kb) {
                 const bool got =
-                    ptx::mbar_wait_bounded_warp(bar_raw_full + 8 * rs, rph, abort_flag, kWaitLimitNs) &&
-                    ptx::mbar_wait_bounded_warp(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, kWaitLimitNs);
+                    ptx::mbar_wait_bounded_warp(bar_raw_full + 8 * rs, rph, abort_flag, prm.wait_limit_ns) &&
+                    ptx::mbar_wait_bounded_warp(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, prm.wait_limit_ns);
                 if (!got) {   // the warp decides as one
                     if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutFull, kb);
                     ok = false;
@@ -759,6 +775,8 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->n_jobs = n_jobs;
     prm->accumulate = accumulate;
     prm->status = status;
+    prm->wait_limit_ns = tune.wait_limit_ns ? tune.wait_limit_ns : kWaitLimitNs;
+    prm->stall_item = tune.stall_item;
     if (map_lo) prm->map_lo = *map_lo;
     int64_t items = 0;
     int op_tiles = 1, raw_tiles = 1;
@@ -886,12 +904,12 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
 }
 
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
-                               cudaStream_t s) {
+                               cudaStream_t s, const TcTuning* tune) {
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
     TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_packed, d_vis, tc_default_cpi(p.n_inputs)};
     CUtensorMap m;
     if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
-    return launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, TcTuning{}, s);
+    return launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, tune ? *tune : TcTuning{}, s);
 }
 
 }  // namespace corr

@@ -170,6 +170,28 @@ def test_float_engines_ragged(n, c, t):
     assert normwise_error(run_engine(x, n, c, t, 32, BF16X3)[0], ref, n) <= 1e-2
 
 
+def test_bounded_wait_gives_up_and_context_survives():
+    # Failure detection without a GPU fault: the producer withholds one stage, the waiting
+    # role's bounded wait (100 ms) runs out, the kernel records a status and returns.
+    import time
+    from paper_0906_1887_gb300 import corr
+    n, c, t = 64, 16, 256
+    p = int_case(31, n, c, t, 8)
+    plan = corr.Plan(n, c, t, 8)
+    x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
+    vis = plan.empty_vis(1, "cuda")
+    t0 = time.time()
+    st, code = plan.selftest_stall(x, vis, stall_item=3, wait_limit_ms=100)
+    assert st == corr.ETIMEOUT and code == 1
+    assert time.time() - t0 < 10
+    # the context and the plan are intact: a normal run is bit-exact
+    plan.run(x, vis, None, engine=TC)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    assert np.array_equal(vis.cpu().numpy()[0], oracle.xcorr_int(p, n, c, t, 8))
+    plan.close()
+
+
 def test_invalid_arguments_rejected():
     from paper_0906_1887_gb300 import corr
     with pytest.raises(corr.CorrError):
