@@ -195,52 +195,93 @@ __device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
     return v;
 }
 
-// Packed 8-bit tile [64 t][64 inputs][re, im] (t rows `pitch` bytes apart) -> interleaved fp16 operand tile.
-// Lane l of a converter warp takes inputs 2l, 2l+1 of sample group q (8 samples).
-// Byte lane k of a loaded word is re(2l), im(2l), re(2l+1), im(2l+1) = operand row 4l + k;
-// lanes start at different k so a quarter-warp's stores never share a bank.
-// `q` selects the group of 8 samples, so a tile is 8 groups x 32 threads.
-__device__ __forceinline__ void convert_tile8(uint32_t raw, uint32_t pitch, uint32_t dst, int l, int q) {
-    const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
-    const uint32_t flip = 0x64806480u;   // exponent bytes 0x64, sign bit of each sample byte flipped
-    uint32_t w[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(raw + (uint32_t)(8 * q + e) * pitch + 4u * l);
+// Per-thread constants of the converters: for each of the 4 output rows a lane writes, the
+// byte-lane selector, the row's swizzle-atom offset and (row & 7) << 4.  They depend only on
+// the lane, so they are computed once per kernel.
+struct ConvLane {
+    uint32_t sel[4];
+    uint32_t rowoff[4];
+    uint32_t r7x16[4];
+};
+
+// 8-bit: lane l takes inputs 2l, 2l+1; byte lane k of a loaded word is re(2l), im(2l),
+// re(2l+1), im(2l+1) = operand row 4l + k.  At step kk the lane writes k = (kk + l/2) & 3,
+// so the rows of a quarter-warp (l = 8a .. 8a+7) fall in 8 distinct swizzle chunks: even l
+// give (row & 7) in 0..3, odd l in 4..7, and the 16-byte stores never share a bank.
+__device__ __forceinline__ ConvLane conv_lane8(int l) {
+    ConvLane c;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        // rows 4l + k of a quarter-warp (l = 8a .. 8a+7) land in 8 distinct swizzle chunks
-        // when k = (kk + l/2) & 3: even l give (row & 7) in 0..3, odd l in 4..7
         const int k = (kk + (l >> 1)) & 3;
-        const uint32_t sel = lane_selector(k);
-        st_shared_v4(dst + sw128_offset(4 * l + k, q), pair_to_half2(w[0], w[1], sel, flip, bias),
+        const int row = 4 * l + k;
+        c.sel[kk] = lane_selector(k);
+        c.rowoff[kk] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
+        c.r7x16[kk] = (uint32_t)((row & 7) << 4);
+    }
+    return c;
+}
+
+// 4-bit: lane l takes inputs 4m .. 4m+3 (m = l & 15); at step kk input 4m + k with
+// k = (kk + m) & 3, rows 2(4m + k) (re) and 2(4m + k) + 1 (im).
+__device__ __forceinline__ ConvLane conv_lane4(int l) {
+    ConvLane c;
+    const int m = l & 15;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = (kk + m) & 3;
+        const int row = 2 * (4 * m + k);
+        c.sel[kk] = lane_selector(k);
+        c.rowoff[kk] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
+        c.r7x16[kk] = (uint32_t)((row & 7) << 4);
+    }
+    return c;
+}
+
+// Packed 8-bit tile [64 t][64 inputs][re, im] (t rows PITCH bytes apart) -> interleaved fp16
+// operand tile, one warp-sized slice: the 8 samples of group q.  raw_lane = raw + 4l.
+template <uint32_t PITCH>
+__device__ __forceinline__ void convert_slice8(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
+    const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
+    const uint32_t flip = 0x64806480u;   // exponent bytes 0x64, sign bit of each sample byte flipped
+    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
+    uint32_t w[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
+    const uint32_t q16 = (uint32_t)q << 4;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t sel = cl.sel[kk];
+        st_shared_v4(dst + cl.rowoff[kk] + (q16 ^ cl.r7x16[kk]), pair_to_half2(w[0], w[1], sel, flip, bias),
                      pair_to_half2(w[2], w[3], sel, flip, bias), pair_to_half2(w[4], w[5], sel, flip, bias),
                      pair_to_half2(w[6], w[7], sel, flip, bias));
     }
 }
 
-// Packed 4-bit tile [64 t][64 inputs] (rows `pitch` apart; high nibble re, low nibble im) ->
-// interleaved fp16 operand tile, in 4 slices of 32 lanes: lane l of slice s takes inputs
-// 4m .. 4m+3 (m = l & 15) of sample group q = 2s + (l >> 4).
-__device__ __forceinline__ void convert_tile4(uint32_t raw, uint32_t pitch, uint32_t dst, int l, int slice) {
-    const int m = l & 15, q = 2 * slice + (l >> 4);
+// Packed 4-bit tile [64 t][64 inputs] (rows PITCH apart; high nibble re, low nibble im) ->
+// interleaved fp16 operand tile, one of 4 slices: lane l of slice s takes inputs 4m .. 4m+3
+// (m = l & 15) of sample group q = 2s + (l >> 4).  raw_lane = raw + 4m.
+template <uint32_t PITCH>
+__device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
     const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
     const uint32_t flip = 0x64086408u;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
+    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const uint32_t w = ld_shared_u32(raw + (uint32_t)(8 * q + e) * pitch + 4u * m);
+        const uint32_t w = ld_shared_u32(src + (uint32_t)e * PITCH);
         hi[e] = (w >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
         lo[e] = w & 0x0F0F0F0Fu;         // im nibble per byte
     }
+    const uint32_t q16 = (uint32_t)q << 4;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        const int k = (kk + m) & 3;
-        const uint32_t sel = lane_selector(k);
-        const int row = 2 * (4 * m + k);
-        st_shared_v4(dst + sw128_offset(row, q), pair_to_half2(hi[0], hi[1], sel, flip, bias),
+        const uint32_t sel = cl.sel[kk];
+        const uint32_t at = dst + cl.rowoff[kk];
+        st_shared_v4(at + (q16 ^ cl.r7x16[kk]), pair_to_half2(hi[0], hi[1], sel, flip, bias),
                      pair_to_half2(hi[2], hi[3], sel, flip, bias), pair_to_half2(hi[4], hi[5], sel, flip, bias),
                      pair_to_half2(hi[6], hi[7], sel, flip, bias));
-        st_shared_v4(dst + sw128_offset(row + 1, q), pair_to_half2(lo[0], lo[1], sel, flip, bias),
+        // the im row is the next row: +128 bytes, (row & 7) one higher
+        st_shared_v4(at + 128u + (q16 ^ (cl.r7x16[kk] + 16u)), pair_to_half2(lo[0], lo[1], sel, flip, bias),
                      pair_to_half2(lo[2], lo[3], sel, flip, bias), pair_to_half2(lo[4], lo[5], sel, flip, bias),
                      pair_to_half2(lo[6], lo[7], sel, flip, bias));
     }
@@ -657,6 +698,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
     } else if constexpr (C::kRaw) {
         // ---------------- converters (warps 6..13) ----------------
         const int cwarp = warp - 6;         // 0..7
+        const ConvLane cl = MODE == kRaw8 ? conv_lane8(lane) : conv_lane4(lane);
+        constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
+        const uint32_t lane_byte = MODE == kRaw8 ? 4u * lane : 4u * (lane & 15);
         int rs = 0, os = 0;
         uint32_t rph = 0, oph = 0;
         bool ok = true;
@@ -667,6 +711,13 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             const int cpi = prm.jobs[it.j].cpi;
             const bool same = it.same;
             const int nkb = prm.jobs[it.j].kp / kTimeBlock;
+            // The stage holds n_tl packed tiles: cpi channels side by side in each sample row
+            // (diagonal items, row pitch cpi x kRow), or blocks I and J (off-diagonal items,
+            // pitch kRow).  Each tile splits into warp-sized slices (8 for 8-bit, 4 for 4-bit);
+            // the converter warps take slices round-robin.
+            constexpr int kSlices = MODE == kRaw8 ? 8 : 4;
+            const int n_tl = same ? cpi : 2;
+            const bool pair_pitch = same && cpi == 2;
             for (int kb = 0; kb < nkb; ++kb) {
                 const bool got =
                     ptx::mbar_wait_bounded_warp(bar_raw_full + 8 * rs, rph, abort_flag, prm.wait_limit_ns) &&
@@ -676,21 +727,20 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     ok = false;
                     break;
                 }
-                const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes);
+                const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes) + lane_byte;
                 const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
-                constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
-                // The stage holds n_tiles packed tiles: cpi channels side by side in each sample
-                // row (diagonal items), or blocks I and J (off-diagonal items).  Each tile splits
-                // into kSlices warp-sized slices; the 8 converter warps take slices round-robin.
-                const int n_tl = same ? cpi : 2;
-                const uint32_t pitch = same ? kRow * (uint32_t)cpi : kRow;
-                constexpr int kSlices = MODE == kRaw8 ? 8 : 4;
                 for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
                     const int tl = sl / kSlices, part = sl % kSlices;
                     const uint32_t src = same ? raw + tl * kRow : raw + tl * C::kRawTileBytes;
                     const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
-                    if constexpr (MODE == kRaw8) convert_tile8(src, pitch, out, lane, part);
-                    else convert_tile4(src, pitch, out, lane, part);
+                    if constexpr (MODE == kRaw8) {
+                        if (pair_pitch) convert_slice8<2 * kRow>(src, out, part, cl);
+                        else convert_slice8<kRow>(src, out, part, cl);
+                    } else {
+                        const int q = 2 * part + (lane >> 4);
+                        if (pair_pitch) convert_slice4<2 * kRow>(src, out, q, cl);
+                        else convert_slice4<kRow>(src, out, q, cl);
+                    }
                 }
                 fence_async_shared();   // generic-proxy writes -> visible to the tensor core
                 __syncwarp();
