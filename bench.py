@@ -51,6 +51,22 @@ WORKLOAD = "stream64_8bit: 64 inputs x 768 channels x 1000 samples/dump x 200 du
 DRAM_BYTES_PER_DUMP = (786.671104e6 + 177.364736e6) / 8
 
 
+def rank_max(x: float, dist, device) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_tera_cmac(cmac_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank runs its own job (weak scaling); the slowest rank's
+    time counts for all."""
+    return cmac_per_rank * world / (ms_max / 1e3) / 1e12
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -427,11 +443,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, dist, dev)
 
     corr.lib()
     plan = corr.Plan(N_INPUTS, N_CHAN, N_TIME, BITS)
@@ -471,7 +483,7 @@ def main():
 
     ms_step = max_over_ranks(ms_total / args.steps)
     cm_step = P * N_CHAN * N_TIME * N_DUMPS
-    value = cm_step * world / (ms_step / 1e3) / 1e12
+    value = aggregate_tera_cmac(cm_step, world, ms_step)
     rtf = (N_TIME * N_DUMPS / CHANNEL_RATE_HZ) / (ms_step / 1e3)
 
     # FP32 CUDA-core engine on the same job (unpack to fp16 planes + CUDA-core cross-multiply)
