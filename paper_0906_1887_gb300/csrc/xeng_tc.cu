@@ -60,6 +60,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;            // 2 s per wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;            // 0.2 s for in-flight work at exit
 constexpr int kMaxOpStages = 16;
 constexpr int kMaxRawStages = 32;
+constexpr int kDefaultL2Lead = 8;                           // stages the L2 prefetch runs ahead
 constexpr int kBarBytes = 8 * (2 * kMaxOpStages + 2 * kMaxRawStages + 5) + 16;
 constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after barriers and alignment
 // Staged epilogue: a warp's 16 rows of 64 baselines (16 bytes each), row pitch 65 x 16 B so
@@ -67,15 +68,20 @@ constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after 
 constexpr int kStageRowBytes = 65 * 16;
 constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 
-enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
+// Raw modes come in two feeds: kRaw8/kRaw4 stage the packed bytes in a shared-memory ring
+// by TMA; kRaw8G/kRaw4G have the converters load them from global memory into registers
+// (L2 prefetched ahead by TMA), so shared memory only carries the operand tiles.
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRaw8G = 4, kRaw4G = 5 };
 
 template <int MODE>
 struct Cfg {
-    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4);
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || MODE == kRaw8G || MODE == kRaw4G);
+    static constexpr bool kGlobal = (MODE == kRaw8G || MODE == kRaw4G);   // no raw ring
+    static constexpr bool kBits8 = (MODE == kRaw8 || MODE == kRaw8G);
     static constexpr bool kSplit = (MODE == kPlanesBF16x3);
     static constexpr int kConvWarps = 8;
     static constexpr int kThreads = kRaw ? 192 + 32 * kConvWarps : 192;
-    static constexpr int kBps = MODE == kRaw8 ? 2 : 1;                    // packed bytes per sample
+    static constexpr int kBps = kBits8 ? 2 : 1;                           // packed bytes per sample
     static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
 };
@@ -96,6 +102,19 @@ struct TcJob {
     int cpi;             // channels per work item (2: adjacent channel pair, single-block arrays)
     int n_groups;        // channel groups per dump = ceil(n_chan / cpi)
     int chunk_kb;        // 64-sample blocks per exactly-flushed chunk
+    // division by n_tiles and n_groups as q = (umulhi(n, m) + n) >> s (n < 2^31; Granlund and
+    // Montgomery, division by invariant integers using multiplication)
+    uint32_t tiles_m, groups_m;
+    int tiles_s, groups_s;
+    // 1: every D element of a chunk is at most 2^23 in magnitude, so rr + ii and ir - ri are
+    // exact in fp32 and each needs one conversion (4-bit samples; 8-bit with <= 512 samples)
+    int f32_combine;
+    // packed samples [n_dumps][n_time][n_chan][row_bytes] for the global-load feed
+    const uint8_t* raw;
+    int64_t t_stride;    // bytes per time sample (n_chan x row_bytes)
+    int64_t d_stride;    // bytes per dump
+    int n_time;
+    int row_bytes;       // n_inputs x packed bytes per sample
 };
 
 template <int MAXJ>
@@ -118,6 +137,7 @@ struct TcLaunch {
     int64_t stall_item;  // self-test: the producer withholds the first stage of this item (-1: none)
     int staged;          // 1: epilogue stages rows in shared memory and bulk-copies them out
     int staging_offset;  // start of the staging area (4 warps x 16 rows x kStageRowBytes)
+    int l2_lead;         // global-load feed: stages between the L2 prefetch and the conversion
     TcJob jobs[MAXJ];
 };
 
@@ -131,26 +151,33 @@ struct ItemCtx {
     int c0;              // first channel of the item
 };
 
+// Tiles are numbered row by row over I <= J: row I starts at off(I) = I nb - I (I - 1) / 2.
+// The row is the larger root bound of off(I) <= tile, taken in float and corrected exactly.
 __device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
-    int i = 0, rem = tile;
-    while (rem >= nb - i) {
-        rem -= nb - i;
-        ++i;
-    }
+    const int b = 2 * nb + 1;
+    int i = (int)(((float)b - sqrtf((float)(b * b - 8 * tile))) * 0.5f);
+    i = max(0, min(i, nb - 1));
+    while (i > 0 && i * nb - i * (i - 1) / 2 > tile) --i;
+    while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= tile) ++i;
     I = i;
-    J = i + rem;
+    J = i + (tile - (i * nb - i * (i - 1) / 2));
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t m, int s) {
+    return (uint32_t)(((uint64_t)__umulhi(n, m) + n) >> s);
 }
 
 template <int MAXJ>
 __device__ __forceinline__ void decode_item(const TcLaunch<MAXJ>& L, int64_t item, int& j, ItemCtx& it) {
     while (j + 1 < L.n_jobs && item >= L.jobs[j + 1].item_begin) ++j;
     const TcJob& jb = L.jobs[j];
-    const int64_t local = item - jb.item_begin;
-    const int tile = (int)(local % jb.n_tiles);
-    const int64_t dg = local / jb.n_tiles;
+    const uint32_t local = (uint32_t)(item - jb.item_begin);   // < 2^31 per job (host-checked)
+    const uint32_t dg = fast_div(local, jb.tiles_m, jb.tiles_s);
+    const int tile = (int)(local - dg * (uint32_t)jb.n_tiles);
+    const uint32_t d = fast_div(dg, jb.groups_m, jb.groups_s);
     it.j = j;
-    it.d = dg / jb.n_groups;
-    it.c0 = (int)(dg % jb.n_groups) * jb.cpi;
+    it.d = d;
+    it.c0 = (int)(dg - d * (uint32_t)jb.n_groups) * jb.cpi;
     tile_coords(tile, jb.nb, it.I, it.J);
     it.same = it.I == it.J;
 }
@@ -158,11 +185,6 @@ __device__ __forceinline__ void decode_item(const TcLaunch<MAXJ>& L, int64_t ite
 __device__ __forceinline__ void record_error(int* status, volatile int* abort, int code, int detail) {
     *abort = 1;
     if (atomicCAS(status, 0, code) == 0) status[1] = detail;
-}
-
-// byte offset of 16-byte chunk q (0..7) of row r in a 128-byte-swizzled K-major tile
-__device__ __forceinline__ uint32_t sw128_offset(int r, int q) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
 }
 
 // Two samples (t, t+1) taken from byte lane `sel` of words a, b -> half2 of the signed
@@ -237,16 +259,12 @@ __device__ __forceinline__ ConvLane conv_lane4(int l) {
     return c;
 }
 
-// Packed 8-bit tile [64 t][64 inputs][re, im] (t rows PITCH bytes apart) -> interleaved fp16
-// operand tile, one warp-sized slice: the 8 samples of group q.  raw_lane = raw + 4l.
-template <uint32_t PITCH>
-__device__ __forceinline__ void convert_slice8(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
+// One warp-sized slice of a packed 8-bit tile -> interleaved fp16 operand tile.  Lane l holds
+// w[e] = bytes 4l .. 4l+3 (re, im of inputs 2l, 2l+1) of sample 8q + e; the slice is the 8
+// samples of group q, written as four 16-byte swizzled row chunks.
+__device__ __forceinline__ void convert_words8(const uint32_t (&w)[8], uint32_t dst, int q, const ConvLane& cl) {
     const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
     const uint32_t flip = 0x64806480u;   // exponent bytes 0x64, sign bit of each sample byte flipped
-    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
-    uint32_t w[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
     const uint32_t q16 = (uint32_t)q << 4;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
@@ -257,20 +275,16 @@ __device__ __forceinline__ void convert_slice8(uint32_t raw_lane, uint32_t dst, 
     }
 }
 
-// Packed 4-bit tile [64 t][64 inputs] (rows PITCH apart; high nibble re, low nibble im) ->
-// interleaved fp16 operand tile, one of 4 slices: lane l of slice s takes inputs 4m .. 4m+3
-// (m = l & 15) of sample group q = 2s + (l >> 4).  raw_lane = raw + 4m.
-template <uint32_t PITCH>
-__device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
+// Packed 4-bit words (high nibble re, low nibble im): lane l holds w[e] = inputs 4m .. 4m+3
+// (m = l & 15) of sample 8q + e, q = 2s + (l >> 4) for slice s.
+__device__ __forceinline__ void convert_words4(const uint32_t (&w)[8], uint32_t dst, int q, const ConvLane& cl) {
     const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
     const uint32_t flip = 0x64086408u;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
-    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const uint32_t w = ld_shared_u32(src + (uint32_t)e * PITCH);
-        hi[e] = (w >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
-        lo[e] = w & 0x0F0F0F0Fu;         // im nibble per byte
+        hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
+        lo[e] = w[e] & 0x0F0F0F0Fu;         // im nibble per byte
     }
     const uint32_t q16 = (uint32_t)q << 4;
 #pragma unroll
@@ -284,6 +298,101 @@ __device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, 
         st_shared_v4(at + 128u + (q16 ^ (cl.r7x16[kk] + 16u)), pair_to_half2(lo[0], lo[1], sel, flip, bias),
                      pair_to_half2(lo[2], lo[3], sel, flip, bias), pair_to_half2(lo[4], lo[5], sel, flip, bias),
                      pair_to_half2(lo[6], lo[7], sel, flip, bias));
+    }
+}
+
+// Raw ring feed: packed tile [64 t][64 inputs] staged in shared memory (t rows PITCH bytes
+// apart), raw_lane = raw + the lane's byte offset.
+template <uint32_t PITCH>
+__device__ __forceinline__ void convert_slice8(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
+    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
+    uint32_t w[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
+    convert_words8(w, dst, q, cl);
+}
+
+template <uint32_t PITCH>
+__device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
+    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
+    uint32_t w[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
+    convert_words4(w, dst, q, cl);
+}
+
+// Global-load feed: a read-only word that no later access of this kernel reuses.
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint8_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// L2 prefetch of one box of a tensor map (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int x, int y, int z, int w) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+
+// A position in this CTA's sequence of stages: (item, 64-sample block kb), items strided by
+// the grid.  Every role walks the same sequence.
+struct StageCursor {
+    int64_t item;
+    int kb;
+    int nkb;
+    int jc;
+    ItemCtx it;
+};
+
+template <int MAXJ>
+__device__ __forceinline__ bool cursor_start(const TcLaunch<MAXJ>& L, StageCursor& c) {
+    c.item = blockIdx.x;
+    c.kb = 0;
+    c.jc = 0;
+    c.nkb = 0;
+    if (c.item >= L.n_items) return false;
+    decode_item(L, c.item, c.jc, c.it);
+    c.nkb = L.jobs[c.it.j].kp / kTimeBlock;
+    return true;
+}
+
+template <int MAXJ>
+__device__ __forceinline__ bool cursor_next(const TcLaunch<MAXJ>& L, StageCursor& c) {
+    if (++c.kb < c.nkb) return true;
+    c.kb = 0;
+    c.item += gridDim.x;
+    if (c.item >= L.n_items) return false;
+    decode_item(L, c.item, c.jc, c.it);
+    c.nkb = L.jobs[c.it.j].kp / kTimeBlock;
+    return true;
+}
+
+// The words converter warp `cw` needs for stage c: its slices cw and cw + 8 of the stage
+// (8-bit: 8 slices per tile; 4-bit: 4), 8 samples each, zero outside the problem
+// (t >= n_time, channel >= n_chan, input >= n_inputs) as the TMA box fill would give.
+template <bool BITS8, int SLOTS, int MAXJ>
+__device__ __forceinline__ void load_stage_words(const TcLaunch<MAXJ>& L, const StageCursor& c, int cw, int lane,
+                                                 uint32_t lane_byte, uint32_t (&w)[SLOTS][8]) {
+    constexpr int kSlices = BITS8 ? 8 : 4;
+    constexpr int kBps = BITS8 ? 2 : 1;
+    const TcJob& jb = L.jobs[c.it.j];
+    const int n_tl = c.it.same ? jb.cpi : 2;
+#pragma unroll
+    for (int u = 0; u < SLOTS; ++u) {
+        const int sl = cw + 8 * u;
+        const int tl = sl / kSlices, part = sl % kSlices;
+        const int q = BITS8 ? part : 2 * part + (lane >> 4);
+        const int chan = c.it.c0 + (c.it.same ? tl : 0);
+        const int blk = c.it.same ? c.it.I : (tl ? c.it.J : c.it.I);
+        const int byte = blk * kBlockInputs * kBps + (int)lane_byte;
+        const bool ok = sl < n_tl * kSlices && chan < jb.n_chan && byte < jb.row_bytes;
+        const int t0 = c.kb * kTimeBlock + 8 * q;
+        const uint8_t* p = jb.raw + c.it.d * jb.d_stride + (int64_t)t0 * jb.t_stride + (int64_t)chan * jb.row_bytes + byte;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            w[u][e] = (ok && t0 + e < jb.n_time) ? ld_stream_u32(p + (int64_t)e * jb.t_stride) : 0u;
     }
 }
 
@@ -367,8 +476,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
 
 
     if (warp == 0) {
-        // ---------------- TMA producer ----------------
-        if (lane == 0) {
+        // ---------------- TMA producer (idle with the global-load feed) ----------------
+        if (!C::kGlobal && lane == 0) {
             const int S = C::kRaw ? RS : OS;
             const uint32_t bar_full = C::kRaw ? bar_raw_full : bar_op_full;
             const uint32_t bar_empty = C::kRaw ? bar_raw_empty : bar_op_empty;
@@ -602,14 +711,26 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row;
                         // every D element is an integer of magnitude <= 2^24: exact in int32
                         long long re[8], imv[8];
+                        if (jb.f32_combine) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
-                            const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
-                            const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
-                            const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
-                            re[k] = (long long)__float2int_rn(rr) + __float2int_rn(ii);
-                            imv[k] = (long long)__float2int_rn(ir) - __float2int_rn(ri);
+                            for (int k = 0; k < 8; ++k) {
+                                const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                                const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                                const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                                const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
+                                re[k] = __float2int_rn(rr + ii);
+                                imv[k] = __float2int_rn(ir - ri);
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                                const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                                const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                                const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
+                                re[k] = (long long)__float2int_rn(rr) + __float2int_rn(ii);
+                                imv[k] = (long long)__float2int_rn(ir) - __float2int_rn(ri);
+                            }
                         }
                         if (prm.staged) {
                             // row lane/2 of this warp's staging rows, slots j - J0; odd lanes
@@ -695,12 +816,101 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         }
         // every bulk copy of ours must have completed before the CTA exits
         if (kIntOut && prm.staged && lane < 16) bulk_wait_all();
+    } else if constexpr (C::kGlobal) {
+        // ---------------- converters, global-load feed (warps 6..13) ----------------
+        // The packed words of a stage go straight from global memory to registers, issued
+        // two stages before they are converted; one lane keeps an L2 prefetch l2_lead stages
+        // ahead of the conversion, so those loads hit L2.  Shared memory carries only the
+        // fp16 operand tiles.
+        constexpr int kSlots = C::kBits8 ? 2 : 1;   // slices per warp per stage (at most)
+        constexpr int kSlices = C::kBits8 ? 8 : 4;
+        const int cwarp = warp - 6;
+        const ConvLane cl = C::kBits8 ? conv_lane8(lane) : conv_lane4(lane);
+        const uint32_t lane_byte = C::kBits8 ? 4u * lane : 4u * (lane & 15);
+        const bool pf_lane = cwarp == 0 && lane == 0;
+        StageCursor cur, ld, pf;
+        bool cur_ok = cursor_start(prm, cur);
+        ld = cur;
+        pf = cur;
+        bool ld_ok = cur_ok, pf_ok = cur_ok;
+        if (pf_lane) {
+            for (int k = 0; pf_ok && k < prm.l2_lead; ++k) {
+                const TcJob& jb = prm.jobs[pf.it.j];
+                tma_prefetch_4d(&jb.map, pf.it.I * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock, (int)pf.it.d);
+                if (!pf.it.same)
+                    tma_prefetch_4d(&jb.map, pf.it.J * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
+                                    (int)pf.it.d);
+                pf_ok = cursor_next(prm, pf);
+            }
+        }
+        uint32_t buf[3][kSlots][8];
+        if (ld_ok) {
+            load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[0]);
+            ld_ok = cursor_next(prm, ld);
+        }
+        if (ld_ok) {
+            load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[1]);
+            ld_ok = cursor_next(prm, ld);
+        }
+        int os = 0;
+        uint32_t oph = 0;
+        bool ok = true;
+        while (ok && cur_ok) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                if (!ok || !cur_ok) break;
+                // buf[u] holds this stage, buf[u + 1] the next; refill the third
+                if (ld_ok) {
+                    load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[(u + 2) % 3]);
+                    ld_ok = cursor_next(prm, ld);
+                }
+                if (pf_lane && pf_ok) {
+                    const TcJob& jb = prm.jobs[pf.it.j];
+                    tma_prefetch_4d(&jb.map, pf.it.I * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
+                                    (int)pf.it.d);
+                    if (!pf.it.same)
+                        tma_prefetch_4d(&jb.map, pf.it.J * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
+                                        (int)pf.it.d);
+                    pf_ok = cursor_next(prm, pf);
+                }
+                if (!ptx::mbar_wait_bounded_warp(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, prm.wait_limit_ns)) {
+                    if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutFull, cur.kb);
+                    ok = false;
+                    break;
+                }
+                const TcJob& jb = prm.jobs[cur.it.j];
+                const bool same = cur.it.same;
+                const int n_tl = same ? jb.cpi : 2;
+                const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
+#pragma unroll
+                for (int v = 0; v < kSlots; ++v) {
+                    const int sl = cwarp + 8 * v;
+                    if (sl < n_tl * kSlices) {
+                        const int tl = sl / kSlices, part = sl % kSlices;
+                        const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
+                        if constexpr (C::kBits8) convert_words8(buf[u][v], out, part, cl);
+                        else convert_words4(buf[u][v], out, 2 * part + (lane >> 4), cl);
+                    }
+                }
+                fence_async_shared();   // generic-proxy writes -> visible to the tensor core
+                __syncwarp();
+                // self-test of the bounded waits: warp 0 withholds its arrival on one stage,
+                // so the MMA issuer's wait for it runs out
+                const bool withhold = cwarp == 0 && cur.item == prm.stall_item && cur.kb == 0;
+                if (lane == 0 && !withhold) ptx::mbar_arrive(bar_op_full + 8 * os);
+                if (++os == OS) {
+                    os = 0;
+                    oph ^= 1u;
+                }
+                cur_ok = cursor_next(prm, cur);
+            }
+        }
     } else if constexpr (C::kRaw) {
-        // ---------------- converters (warps 6..13) ----------------
+        // ---------------- converters, raw ring feed (warps 6..13) ----------------
         const int cwarp = warp - 6;         // 0..7
-        const ConvLane cl = MODE == kRaw8 ? conv_lane8(lane) : conv_lane4(lane);
+        const ConvLane cl = C::kBits8 ? conv_lane8(lane) : conv_lane4(lane);
         constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
-        const uint32_t lane_byte = MODE == kRaw8 ? 4u * lane : 4u * (lane & 15);
+        const uint32_t lane_byte = C::kBits8 ? 4u * lane : 4u * (lane & 15);
         int rs = 0, os = 0;
         uint32_t rph = 0, oph = 0;
         bool ok = true;
@@ -715,7 +925,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             // (diagonal items, row pitch cpi x kRow), or blocks I and J (off-diagonal items,
             // pitch kRow).  Each tile splits into warp-sized slices (8 for 8-bit, 4 for 4-bit);
             // the converter warps take slices round-robin.
-            constexpr int kSlices = MODE == kRaw8 ? 8 : 4;
+            constexpr int kSlices = C::kBits8 ? 8 : 4;
             const int n_tl = same ? cpi : 2;
             const bool pair_pitch = same && cpi == 2;
             for (int kb = 0; kb < nkb; ++kb) {
@@ -729,17 +939,31 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 }
                 const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes) + lane_byte;
                 const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
-                for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
-                    const int tl = sl / kSlices, part = sl % kSlices;
-                    const uint32_t src = same ? raw + tl * kRow : raw + tl * C::kRawTileBytes;
-                    const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
-                    if constexpr (MODE == kRaw8) {
-                        if (pair_pitch) convert_slice8<2 * kRow>(src, out, part, cl);
-                        else convert_slice8<kRow>(src, out, part, cl);
-                    } else {
-                        const int q = 2 * part + (lane >> 4);
-                        if (pair_pitch) convert_slice4<2 * kRow>(src, out, q, cl);
-                        else convert_slice4<kRow>(src, out, q, cl);
+                const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
+                // all loads of the warp's slices (slices cwarp and cwarp + 8) are issued before
+                // the first conversion, so their shared-memory latencies overlap
+                constexpr int kSlots = C::kBits8 ? 2 : 1;
+                uint32_t w[kSlots][8];
+#pragma unroll
+                for (int v = 0; v < kSlots; ++v) {
+                    const int sl = cwarp + C::kConvWarps * v;
+                    if (sl < n_tl * kSlices) {
+                        const int tl = sl / kSlices, part = sl % kSlices;
+                        const int q = C::kBits8 ? part : 2 * part + (lane >> 4);
+                        const uint32_t src = (same ? raw + tl * kRow : raw + tl * C::kRawTileBytes) +
+                                             (uint32_t)q * 8u * pitch;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) w[v][e] = ld_shared_u32(src + (uint32_t)e * pitch);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < kSlots; ++v) {
+                    const int sl = cwarp + C::kConvWarps * v;
+                    if (sl < n_tl * kSlices) {
+                        const int tl = sl / kSlices, part = sl % kSlices;
+                        const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
+                        if constexpr (C::kBits8) convert_words8(w[v], out, part, cl);
+                        else convert_words4(w[v], out, 2 * part + (lane >> 4), cl);
                     }
                 }
                 fence_async_shared();   // generic-proxy writes -> visible to the tensor core
@@ -814,6 +1038,14 @@ bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, 
     return r == CUDA_SUCCESS;
 }
 
+// constants of fast_div for the divisor d (1 <= d <= 2^31)
+void fast_div_make(uint32_t d, uint32_t& m, int& s) {
+    int l = 0;
+    while ((uint64_t{1} << l) < d) ++l;
+    m = (uint32_t)(((uint64_t{1} << 32) * ((uint64_t{1} << l) - d)) / d + 1);
+    s = l;
+}
+
 template <int MODE, int MAXJ>
 cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* maps, const CUtensorMap* map_lo,
                         int accumulate, int* status, int n_sm, const TcTuning& tune, cudaStream_t s) {
@@ -827,6 +1059,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->status = status;
     prm->wait_limit_ns = tune.wait_limit_ns ? tune.wait_limit_ns : kWaitLimitNs;
     prm->stall_item = tune.stall_item;
+    prm->l2_lead = tune.l2_lead > 0 ? tune.l2_lead : kDefaultL2Lead;
     if (map_lo) prm->map_lo = *map_lo;
     int64_t items = 0;
     int op_tiles = 1, raw_tiles = 1;
@@ -845,8 +1078,22 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         jb.n_groups = (sp.n_chan + jb.cpi - 1) / jb.cpi;
         // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
         jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock) : (sp.sample_bits == 4 ? 2048 : 16);
+        // |D| <= chunk samples x max |x_a x_b|: 4-bit 2^17 x 2^6 = 2^23, 8-bit 512 x 2^14 = 2^23
+        jb.f32_combine = !C::kSplit && (sp.sample_bits == 4 || jb.kp <= 512) ? 1 : 0;
+        jb.raw = static_cast<const uint8_t*>(sp.data);
+        jb.row_bytes = sp.n_inputs * C::kBps;
+        jb.t_stride = (int64_t)jb.row_bytes * sp.n_chan;
+        jb.d_stride = jb.t_stride * sp.n_time;
+        jb.n_time = sp.n_time;
         jb.item_begin = items;
-        items += (int64_t)sp.n_dumps * jb.n_groups * jb.n_tiles;
+        const int64_t job_items = (int64_t)sp.n_dumps * jb.n_groups * jb.n_tiles;
+        if (job_items >= (int64_t{1} << 31)) {   // decode_item divides 32-bit item indices
+            delete prm;
+            return cudaErrorInvalidValue;
+        }
+        fast_div_make((uint32_t)jb.n_tiles, jb.tiles_m, jb.tiles_s);
+        fast_div_make((uint32_t)jb.n_groups, jb.groups_m, jb.groups_s);
+        items += job_items;
         const int tiles = jb.nb == 1 ? jb.cpi : 2;    // operand tiles one stage needs
         op_tiles = tiles > op_tiles ? tiles : op_tiles;
         raw_tiles = tiles > raw_tiles ? tiles : raw_tiles;
@@ -862,7 +1109,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     const int operand_bytes = C::kTilesPerOperand * kTileBytes;
     prm->op_stage_bytes = op_tiles * operand_bytes;
     prm->b_offset = operand_bytes;
-    if (C::kRaw) {
+    if (C::kRaw && !C::kGlobal) {
         prm->raw_stage_bytes = raw_tiles * C::kRawTileBytes;
         prm->op_stages = tune.op_stages > 0 ? tune.op_stages : (prm->staged ? 3 : 4);
         // a requested depth that leaves fewer than 3 raw stages is reduced to what fits
@@ -881,6 +1128,8 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         prm->raw_stages = 0;
         prm->op_stages = (kSmemBudget - stage_space) / prm->op_stage_bytes;
         if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
+        // the global-load feed may ask for a shallower operand ring
+        if (C::kGlobal && tune.op_stages > 1 && tune.op_stages < prm->op_stages) prm->op_stages = tune.op_stages;
     }
     if (prm->op_stages < 2 || prm->op_stages > kMaxOpStages) {
         delete prm;
@@ -944,22 +1193,49 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
         if (specs[j].sample_bits != bits || !tc_raw_supported(specs[j].n_inputs, bits) ||
             (specs[j].cpi != 1 && specs[j].cpi != 2) || (specs[j].cpi == 2 && specs[j].n_inputs > kBlockInputs))
             return cudaErrorInvalidValue;
+    const bool ring = tune.feed != kFeedGlobal;
     if (n_jobs == 1) {
-        if (bits == 8) return launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
-        return launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        if (bits == 8)
+            return ring ? launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s)
+                        : launch_jobs<kRaw8G, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        return ring ? launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s)
+                    : launch_jobs<kRaw4G, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
     }
     if (n_jobs > kMaxJobs) return cudaErrorInvalidValue;
-    if (bits == 8) return launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
-    return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+    if (bits == 8)
+        return ring ? launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s)
+                    : launch_jobs<kRaw8G, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+    return ring ? launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s)
+                : launch_jobs<kRaw4G, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
 }
 
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s, const TcTuning* tune) {
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
-    TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_packed, d_vis, tc_default_cpi(p.n_inputs)};
-    CUtensorMap m;
-    if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
-    return launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, tune ? *tune : TcTuning{}, s);
+    TcTuning plan_tune;
+    plan_tune.feed = p.tc_feed;
+    plan_tune.op_stages = p.tc_op_stages;
+    plan_tune.l2_lead = p.tc_l2_lead;
+    const int cpi = tc_default_cpi(p.n_inputs);
+    // one launch covers fewer than 2^31 work items (the kernel decodes 32-bit item indices)
+    const int64_t items_per_dump = (int64_t)((p.n_chan + cpi - 1) / cpi) * (p.nb * (p.nb + 1) / 2);
+    const int64_t max_dumps = ((int64_t{1} << 31) - 1) / items_per_dump;
+    if (max_dumps < 1) return cudaErrorInvalidValue;
+    const size_t packed_dump = (size_t)p.n_time * p.n_chan * p.n_inputs * (p.sample_bits == 8 ? 2 : 1);
+    const size_t vis_dump = (size_t)p.n_chan * (size_t)p.n_baselines * 16;
+    for (int d0 = 0; d0 < n_dumps;) {
+        const int nd = (int)((n_dumps - d0) < max_dumps ? (n_dumps - d0) : max_dumps);
+        TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, nd, p.sample_bits,
+                     static_cast<const uint8_t*>(d_packed) + (size_t)d0 * packed_dump,
+                     static_cast<uint8_t*>(d_vis) + (size_t)d0 * vis_dump, cpi};
+        CUtensorMap m;
+        if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
+        const cudaError_t e =
+            launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, tune ? *tune : plan_tune, s);
+        if (e != cudaSuccess) return e;
+        d0 += nd;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace corr

@@ -52,6 +52,32 @@ def test_small_ragged_bit_exact(engine, n, c, t, bits):
     assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
 
 
+# the fused kernel's two feeds of packed samples (TMA ring / global loads), with ring depths
+# and L2 prefetch leads away from the defaults: every setting must give the same bits
+FEED_CASES = [(8, 2, 100, 8), (16, 3, 64, 4), (32, 3, 1000, 8), (64, 5, 1100, 8), (96, 1, 77, 4),
+              (128, 2, 256, 4), (136, 3, 130, 8), (192, 1, 65, 8), (48, 2, 300, 4), (64, 1, 1, 8)]
+TUNINGS = [(1, 0, 0), (2, 0, 0), (2, 2, 1), (2, 3, 32), (1, 3, 0)]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+@pytest.mark.parametrize("n,c,t,bits", FEED_CASES)
+def test_fused_feeds_bit_exact(tuning, n, c, t, bits):
+    p = int_case(5000 + n + 3 * c + t, n, c, t, bits)
+    v = run_engine(p, n, c, t, bits, TC, tuning=tuning)[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
+
+
+@pytest.mark.parametrize("feed", [1, 2])
+def test_fused_feeds_dumps_and_accumulate(feed):
+    n, c, t, bits, d = 64, 3, 200, 8, 3
+    p = np.concatenate([int_case(77 + k, n, c, t, bits) for k in range(d)])
+    ref = np.stack([oracle.xcorr_int(p[k * t:(k + 1) * t], n, c, t, bits) for k in range(d)])
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=d, tuning=(feed, 0, 0))
+    assert np.array_equal(v, ref)
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=d, accumulate=True, vis_init=ref, tuning=(feed, 0, 0))
+    assert np.array_equal(v, 2 * ref)
+
+
 @pytest.mark.parametrize("engine", [TC, FP32])
 @pytest.mark.parametrize("t", [1023, 1024, 1025, 2048, 3000])
 def test_extreme_magnitudes_chunk_flush(engine, t):
@@ -63,6 +89,23 @@ def test_extreme_magnitudes_chunk_flush(engine, t):
     p = synth.pack(re, im, 8)
     v = run_engine(p, n, 1, t, 8, engine)[0]
     assert np.array_equal(v, oracle.xcorr_int(p, n, 1, t, 8))
+
+
+@pytest.mark.parametrize("n,t,bits,lo", [(66, 512, 8, -128), (64, 512, 8, -128), (136, 512, 8, -128),
+                                         (66, 511, 8, -128), (64, 513, 8, -128),
+                                         (16, 131072, 4, -8), (16, 131072 + 64, 4, -8)])
+def test_fp32_combined_epilogue_edges(n, t, bits, lo):
+    # chunks whose D elements reach 2^23 (rr + ii = 2^24, still exact in fp32): 512 samples
+    # of -128 (8-bit) and a full 131072-sample chunk of -8 (4-bit), and one past each edge
+    re = np.full((t, 1, n), lo, np.int16)
+    im = np.full((t, 1, n), lo, np.int16)
+    im[:, 0, 3] = -lo - 1
+    re[::3, 0, 7] = -lo - 1
+    p = synth.pack(re, im, bits)
+    v = run_engine(p, n, 1, t, bits, TC)[0]
+    ref = oracle.xcorr_int(p, n, 1, t, bits)
+    assert np.array_equal(v, ref)
+    assert int(ref[0, 0, 0]) == 2 * t * lo * lo
 
 
 @pytest.mark.parametrize("engine", [TC, FP32])
@@ -170,14 +213,17 @@ def test_float_engines_ragged(n, c, t):
     assert normwise_error(run_engine(x, n, c, t, 32, BF16X3)[0], ref, n) <= 1e-2
 
 
-def test_bounded_wait_gives_up_and_context_survives():
-    # Failure detection without a GPU fault: the producer withholds one stage, the waiting
-    # role's bounded wait (100 ms) runs out, the kernel records a status and returns.
+@pytest.mark.parametrize("feed", [1, 2])
+def test_bounded_wait_gives_up_and_context_survives(feed):
+    # Failure detection without a GPU fault: one stage is withheld (by the TMA producer with
+    # the ring feed, by a converter warp with the global feed), the MMA issuer's bounded
+    # wait (100 ms) runs out, the kernel records a status and returns.
     import time
     from paper_0906_1887_gb300 import corr
     n, c, t = 64, 16, 256
     p = int_case(31, n, c, t, 8)
     plan = corr.Plan(n, c, t, 8)
+    plan.set_tuning(feed, 0, 0)
     x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
     vis = plan.empty_vis(1, "cuda")
     t0 = time.time()
