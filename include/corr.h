@@ -106,20 +106,13 @@ corr_status corr_plan_destroy(corr_plan plan);
 corr_status corr_plan_info(corr_plan plan, int64_t *n_baselines, size_t *packed_bytes, size_t *vis_bytes);
 
 /*
- * Launch knobs of the packed-sample tensor-core kernel for this plan (no counterpart in
- * the paper: they choose how the fused unpack is fed, not what it computes).
- *   feed       CORR_FEED_DEFAULT (= RING), CORR_FEED_RING: TMA copies the packed bytes
- *              into a shared-memory ring that the converter warps read, or
- *              CORR_FEED_GLOBAL: the converter warps load them from global memory into
- *              registers, an L2 prefetch running l2_lead stages ahead
- *   op_stages  depth of the fp16 operand ring (0 = the deepest that fits)
- *   l2_lead    stages of L2 prefetch lead for the global feed (0 = default 8; <= 64)
- * Results are identical for every setting.  CORR_EINVAL for values out of range.
+ * Launch knob of the packed-sample tensor-core kernel for this plan (no counterpart in the
+ * paper: it shapes the pipeline, not what it computes): op_stages = depth of the fp16
+ * operand ring in shared memory, 0 = the default; a depth that leaves fewer than 3 stages
+ * for the packed-sample ring is reduced to what fits.  Results are identical for every
+ * setting.  CORR_EINVAL outside [0, 16].
  */
-#define CORR_FEED_DEFAULT 0
-#define CORR_FEED_RING 1
-#define CORR_FEED_GLOBAL 2
-corr_status corr_plan_set_tuning(corr_plan plan, int feed, int op_stages, int l2_lead);
+corr_status corr_plan_set_tuning(corr_plan plan, int op_stages);
 
 /* Device workspace (bytes) corr_xengine_run_batch needs for `engine` and n_dumps
  * dumps.  0 means the engine needs none (d_workspace may be NULL). */
@@ -323,8 +316,7 @@ corr_status corr_host_free(void *ptr);
 /*
  * Self-test of failure detection, with no GPU fault: runs the packed-sample tensor-core X
  * stage of one dump with its mbarrier waits bounded by wait_limit_ms, while the producer
- * (ring feed) or the first converter warp (global feed, the plan's corr_plan_set_tuning
- * choice) withholds the first stage of work item `stall_item`, so the waiting role gives up,
+ * withholds the first stage of work item `stall_item`, so the waiting role gives up,
  * records its code in the plan's status block and every role of that CTA exits cleanly
  * (in-flight copies and MMAs are drained first).  Synchronises; *device_error receives
  * the recorded code (0 if nothing timed out; 1 = a loaded stage never arrived) and the

@@ -15,7 +15,6 @@ LIB_PATH = os.path.join(HERE, "libcorr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, PENDING, EUNSUPPORTED = range(8)
 ENGINE_TC, ENGINE_FP32, ENGINE_BF16X3 = 0, 1, 2
-FEED_DEFAULT, FEED_RING, FEED_GLOBAL = 0, 1, 2
 STATUS_NAMES = {OK: "CORR_OK", EINVAL: "CORR_EINVAL", ENOMEM: "CORR_ENOMEM", ECUDA: "CORR_ECUDA",
                 EBUSY: "CORR_EBUSY", ETIMEOUT: "CORR_ETIMEOUT", PENDING: "CORR_PENDING",
                 EUNSUPPORTED: "CORR_EUNSUPPORTED"}
@@ -32,7 +31,7 @@ SIGNATURES = {
     "corr_plan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int, _c_int]),
     "corr_plan_destroy": (_c_int, [_vp]),
     "corr_plan_info": (_c_int, [_vp, _P(_c_i64), _P(_c_sz), _P(_c_sz)]),
-    "corr_plan_set_tuning": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "corr_plan_set_tuning": (_c_int, [_vp, _c_int]),
     "corr_workspace_size": (_c_int, [_vp, _c_int, _c_int, _P(_c_sz)]),
     "corr_unpack": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
     "corr_xengine_run": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
@@ -144,9 +143,9 @@ class Plan:
     def n_baselines(self) -> int:
         return self.info()[0]
 
-    def set_tuning(self, feed: int = FEED_DEFAULT, op_stages: int = 0, l2_lead: int = 0):
-        """Launch knobs of the packed-sample tensor-core kernel (results do not depend on them)."""
-        check(lib().corr_plan_set_tuning(self._h, feed, op_stages, l2_lead), "corr_plan_set_tuning")
+    def set_tuning(self, op_stages: int = 0):
+        """Operand ring depth of the packed-sample tensor-core kernel (results do not depend on it)."""
+        check(lib().corr_plan_set_tuning(self._h, op_stages), "corr_plan_set_tuning")
 
     def workspace_size(self, engine: int, n_dumps: int = 1) -> int:
         b = ctypes.c_size_t()

@@ -114,15 +114,10 @@ corr_status corr_plan_info(corr_plan plan, int64_t* n_bl, size_t* packed_bytes, 
     return CORR_OK;
 }
 
-corr_status corr_plan_set_tuning(corr_plan plan, int feed, int op_stages, int l2_lead) {
+corr_status corr_plan_set_tuning(corr_plan plan, int op_stages) {
     if (!plan) return set_error(CORR_EINVAL, "corr_plan_set_tuning: plan is NULL");
-    if (feed < CORR_FEED_DEFAULT || feed > CORR_FEED_GLOBAL) return set_error(CORR_EINVAL, "feed=%d unknown", feed);
     if (op_stages < 0 || op_stages > 16) return set_error(CORR_EINVAL, "op_stages=%d outside [0, 16]", op_stages);
-    if (l2_lead < 0 || l2_lead > 64) return set_error(CORR_EINVAL, "l2_lead=%d outside [0, 64]", l2_lead);
-    Plan* p = reinterpret_cast<Plan*>(plan);
-    p->tc_feed = feed == CORR_FEED_RING ? kFeedRing : feed == CORR_FEED_GLOBAL ? kFeedGlobal : kFeedDefault;
-    p->tc_op_stages = op_stages;
-    p->tc_l2_lead = l2_lead;
+    reinterpret_cast<Plan*>(plan)->tc_op_stages = op_stages;
     return CORR_OK;
 }
 
@@ -307,9 +302,7 @@ corr_status corr_selftest_stall(corr_plan plan, const void* d_packed, void* d_vi
     if (!tc_raw_supported(*p))
         return set_error(CORR_EUNSUPPORTED, "the self-test runs the packed-sample tensor-core kernel");
     TcTuning tune;
-    tune.feed = p->tc_feed;
     tune.op_stages = p->tc_op_stages;
-    tune.l2_lead = p->tc_l2_lead;
     tune.wait_limit_ns = (uint64_t)wait_limit_ms * 1000000ull;
     tune.stall_item = stall_item;
     cudaError_t e = launch_xeng_tc_raw(*p, d_packed, 1, d_vis, 0, nullptr, &tune);

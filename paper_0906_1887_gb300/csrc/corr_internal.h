@@ -37,10 +37,7 @@ struct Plan {
     int device = 0;
     int n_sm = 0;
     int* d_status = nullptr; // [4] device status words
-    // launch knobs of the packed-sample tensor-core kernel (corr_plan_set_tuning)
-    int tc_feed = 0;
-    int tc_op_stages = 0;
-    int tc_l2_lead = 0;
+    int tc_op_stages = 0;     // operand ring depth of the packed-sample kernel (0: default)
     // host-buffer pipeline (corr_xengine_run_host), created on first use
     char* pipe_dev = nullptr;   // 2 x (chunk inputs) + 2 x (chunk outputs) + workspace
     size_t pipe_bytes = 0;
@@ -83,13 +80,8 @@ struct TcJobSpec {
     int cpi;            // channels per work item: 1, or 2 for arrays of at most 64 inputs
 };
 // Launch-shape knobs the autotuner chooses (0 = default).
-constexpr int kFeedDefault = 0;   // the packed-sample feed of the fused kernel: the TMA ring
-constexpr int kFeedRing = 1;      // TMA-staged raw ring in shared memory
-constexpr int kFeedGlobal = 2;    // global loads into registers, L2 prefetched ahead
 struct TcTuning {
     int op_stages = 0;
-    int feed = kFeedDefault;
-    int l2_lead = 0;              // global-load feed: stages of L2 prefetch lead (0: default)
     uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };

@@ -34,8 +34,9 @@
 // CTA roles (one CTA per SM, persistent over work items = (dump, channel, I, J)):
 //   warp 0       TMA producer
 //   warp 1       tensor-memory allocator and single-thread MMA issuer
-//   warps 2..5   epilogue: tensor memory -> registers -> lane-pair combine -> int64 ->
-//                baseline order, stored straight from registers
+//   warps 2..5   epilogue, one warp per tensor-memory lane quarter: tensor memory ->
+//                registers -> lane-pair combine -> int64 -> baseline order, stored from
+//                registers (single-block arrays) or staged in shared memory and bulk-copied
 //   warps 6..13  (raw only) converters: packed bytes -> fp16 K-major swizzled tiles
 // Shared memory is carved at launch: when the array has a single 64-input block every
 // item is a diagonal tile (B = A), so stages hold one tile and the rings get deeper.
@@ -60,7 +61,6 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;            // 2 s per wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;            // 0.2 s for in-flight work at exit
 constexpr int kMaxOpStages = 16;
 constexpr int kMaxRawStages = 32;
-constexpr int kDefaultL2Lead = 8;                           // stages the L2 prefetch runs ahead
 constexpr int kBarBytes = 8 * (2 * kMaxOpStages + 2 * kMaxRawStages + 5) + 16;
 constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after barriers and alignment
 // Staged epilogue: a warp's 16 rows of 64 baselines (16 bytes each), row pitch 65 x 16 B so
@@ -68,19 +68,16 @@ constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after 
 constexpr int kStageRowBytes = 65 * 16;
 constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 
-// Raw modes come in two feeds: kRaw8/kRaw4 stage the packed bytes in a shared-memory ring
-// by TMA; kRaw8G/kRaw4G have the converters load them from global memory into registers
-// (L2 prefetched ahead by TMA), so shared memory only carries the operand tiles.
-enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRaw8G = 4, kRaw4G = 5 };
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
 
 template <int MODE>
 struct Cfg {
-    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || MODE == kRaw8G || MODE == kRaw4G);
-    static constexpr bool kGlobal = (MODE == kRaw8G || MODE == kRaw4G);   // no raw ring
-    static constexpr bool kBits8 = (MODE == kRaw8 || MODE == kRaw8G);
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4);
+    static constexpr bool kBits8 = MODE == kRaw8;
     static constexpr bool kSplit = (MODE == kPlanesBF16x3);
+    static constexpr int kEpiWarps = 4;     // one per tensor-memory lane quarter
     static constexpr int kConvWarps = 8;
-    static constexpr int kThreads = kRaw ? 192 + 32 * kConvWarps : 192;
+    static constexpr int kThreads = 64 + 32 * kEpiWarps + (kRaw ? 32 * kConvWarps : 0);
     static constexpr int kBps = kBits8 ? 2 : 1;                           // packed bytes per sample
     static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
@@ -109,12 +106,6 @@ struct TcJob {
     // 1: every D element of a chunk is at most 2^23 in magnitude, so rr + ii and ir - ri are
     // exact in fp32 and each needs one conversion (4-bit samples; 8-bit with <= 512 samples)
     int f32_combine;
-    // packed samples [n_dumps][n_time][n_chan][row_bytes] for the global-load feed
-    const uint8_t* raw;
-    int64_t t_stride;    // bytes per time sample (n_chan x row_bytes)
-    int64_t d_stride;    // bytes per dump
-    int n_time;
-    int row_bytes;       // n_inputs x packed bytes per sample
 };
 
 template <int MAXJ>
@@ -137,7 +128,6 @@ struct TcLaunch {
     int64_t stall_item;  // self-test: the producer withholds the first stage of this item (-1: none)
     int staged;          // 1: epilogue stages rows in shared memory and bulk-copies them out
     int staging_offset;  // start of the staging area (4 warps x 16 rows x kStageRowBytes)
-    int l2_lead;         // global-load feed: stages between the L2 prefetch and the conversion
     TcJob jobs[MAXJ];
 };
 
@@ -321,81 +311,6 @@ __device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, 
     convert_words4(w, dst, q, cl);
 }
 
-// Global-load feed: a read-only word that no later access of this kernel reuses.
-__device__ __forceinline__ uint32_t ld_stream_u32(const uint8_t* p) {
-    uint32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-
-// L2 prefetch of one box of a tensor map (no shared memory, no completion to wait for).
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int x, int y, int z, int w) {
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(z), "r"(w)
-                 : "memory");
-}
-
-// A position in this CTA's sequence of stages: (item, 64-sample block kb), items strided by
-// the grid.  Every role walks the same sequence.
-struct StageCursor {
-    int64_t item;
-    int kb;
-    int nkb;
-    int jc;
-    ItemCtx it;
-};
-
-template <int MAXJ>
-__device__ __forceinline__ bool cursor_start(const TcLaunch<MAXJ>& L, StageCursor& c) {
-    c.item = blockIdx.x;
-    c.kb = 0;
-    c.jc = 0;
-    c.nkb = 0;
-    if (c.item >= L.n_items) return false;
-    decode_item(L, c.item, c.jc, c.it);
-    c.nkb = L.jobs[c.it.j].kp / kTimeBlock;
-    return true;
-}
-
-template <int MAXJ>
-__device__ __forceinline__ bool cursor_next(const TcLaunch<MAXJ>& L, StageCursor& c) {
-    if (++c.kb < c.nkb) return true;
-    c.kb = 0;
-    c.item += gridDim.x;
-    if (c.item >= L.n_items) return false;
-    decode_item(L, c.item, c.jc, c.it);
-    c.nkb = L.jobs[c.it.j].kp / kTimeBlock;
-    return true;
-}
-
-// The words converter warp `cw` needs for stage c: its slices cw and cw + 8 of the stage
-// (8-bit: 8 slices per tile; 4-bit: 4), 8 samples each, zero outside the problem
-// (t >= n_time, channel >= n_chan, input >= n_inputs) as the TMA box fill would give.
-template <bool BITS8, int SLOTS, int MAXJ>
-__device__ __forceinline__ void load_stage_words(const TcLaunch<MAXJ>& L, const StageCursor& c, int cw, int lane,
-                                                 uint32_t lane_byte, uint32_t (&w)[SLOTS][8]) {
-    constexpr int kSlices = BITS8 ? 8 : 4;
-    constexpr int kBps = BITS8 ? 2 : 1;
-    const TcJob& jb = L.jobs[c.it.j];
-    const int n_tl = c.it.same ? jb.cpi : 2;
-#pragma unroll
-    for (int u = 0; u < SLOTS; ++u) {
-        const int sl = cw + 8 * u;
-        const int tl = sl / kSlices, part = sl % kSlices;
-        const int q = BITS8 ? part : 2 * part + (lane >> 4);
-        const int chan = c.it.c0 + (c.it.same ? tl : 0);
-        const int blk = c.it.same ? c.it.I : (tl ? c.it.J : c.it.I);
-        const int byte = blk * kBlockInputs * kBps + (int)lane_byte;
-        const bool ok = sl < n_tl * kSlices && chan < jb.n_chan && byte < jb.row_bytes;
-        const int t0 = c.kb * kTimeBlock + 8 * q;
-        const uint8_t* p = jb.raw + c.it.d * jb.d_stride + (int64_t)t0 * jb.t_stride + (int64_t)chan * jb.row_bytes + byte;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-            w[u][e] = (ok && t0 + e < jb.n_time) ? ld_stream_u32(p + (int64_t)e * jb.t_stride) : 0u;
-    }
-}
-
 __device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                  : "memory");
@@ -457,7 +372,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(bar_acc_full + 8 * b, 1);
-            ptx::mbar_init(bar_acc_empty + 8 * b, 4);
+            ptx::mbar_init(bar_acc_empty + 8 * b, C::kEpiWarps);
         }
         ptx::mbar_init(bar_drain, 1);
         *abort_flag = 0;
@@ -476,8 +391,8 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
 
 
     if (warp == 0) {
-        // ---------------- TMA producer (idle with the global-load feed) ----------------
-        if (!C::kGlobal && lane == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
             const int S = C::kRaw ? RS : OS;
             const uint32_t bar_full = C::kRaw ? bar_raw_full : bar_op_full;
             const uint32_t bar_empty = C::kRaw ? bar_raw_empty : bar_op_empty;
@@ -641,7 +556,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             }
         }
         __syncwarp();
-    } else if (warp < 6) {
+    } else if (warp < 2 + C::kEpiWarps) {
         // ---------------- epilogue (warps 2..5) ----------------
         // Lane L of quadrant q holds operand row 32q + L: input i_loc = 16q + L/2, real part
         // for even L, imaginary part for odd L.  Per 32 columns (16 inputs j, re/im each)
@@ -668,8 +583,11 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             // baseline b(i, j) = row_off + j within one channel's [P] block
             const int64_t row_off = (int64_t)i * n_in - (int64_t)i * (i - 1) / 2 - i;
             for (int kb0 = 0; kb0 < nkb; kb0 += jb.chunk_kb) {
-                // lane 0 observes the phase; the warp decides as one
-                const bool got = ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, prm.wait_limit_ns);
+                // lane 0 observes the phase; the warp decides as one.  An accumulator spans a
+                // whole chunk of stages, so this wait gets twice the bound: a stage that never
+                // arrives is reported by the role waiting for that stage
+                const bool got =
+                    ptx::mbar_wait_bounded_warp(bar_acc_full + 8 * abuf, aph, abort_flag, 2 * prm.wait_limit_ns);
                 if (!got) {
                     if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutAccFull, kb0);
                     ok = false;
@@ -816,98 +734,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         }
         // every bulk copy of ours must have completed before the CTA exits
         if (kIntOut && prm.staged && lane < 16) bulk_wait_all();
-    } else if constexpr (C::kGlobal) {
-        // ---------------- converters, global-load feed (warps 6..13) ----------------
-        // The packed words of a stage go straight from global memory to registers, issued
-        // two stages before they are converted; one lane keeps an L2 prefetch l2_lead stages
-        // ahead of the conversion, so those loads hit L2.  Shared memory carries only the
-        // fp16 operand tiles.
-        constexpr int kSlots = C::kBits8 ? 2 : 1;   // slices per warp per stage (at most)
-        constexpr int kSlices = C::kBits8 ? 8 : 4;
-        const int cwarp = warp - 6;
-        const ConvLane cl = C::kBits8 ? conv_lane8(lane) : conv_lane4(lane);
-        const uint32_t lane_byte = C::kBits8 ? 4u * lane : 4u * (lane & 15);
-        const bool pf_lane = cwarp == 0 && lane == 0;
-        StageCursor cur, ld, pf;
-        bool cur_ok = cursor_start(prm, cur);
-        ld = cur;
-        pf = cur;
-        bool ld_ok = cur_ok, pf_ok = cur_ok;
-        if (pf_lane) {
-            for (int k = 0; pf_ok && k < prm.l2_lead; ++k) {
-                const TcJob& jb = prm.jobs[pf.it.j];
-                tma_prefetch_4d(&jb.map, pf.it.I * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock, (int)pf.it.d);
-                if (!pf.it.same)
-                    tma_prefetch_4d(&jb.map, pf.it.J * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
-                                    (int)pf.it.d);
-                pf_ok = cursor_next(prm, pf);
-            }
-        }
-        uint32_t buf[3][kSlots][8];
-        if (ld_ok) {
-            load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[0]);
-            ld_ok = cursor_next(prm, ld);
-        }
-        if (ld_ok) {
-            load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[1]);
-            ld_ok = cursor_next(prm, ld);
-        }
-        int os = 0;
-        uint32_t oph = 0;
-        bool ok = true;
-        while (ok && cur_ok) {
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                if (!ok || !cur_ok) break;
-                // buf[u] holds this stage, buf[u + 1] the next; refill the third
-                if (ld_ok) {
-                    load_stage_words<C::kBits8>(prm, ld, cwarp, lane, lane_byte, buf[(u + 2) % 3]);
-                    ld_ok = cursor_next(prm, ld);
-                }
-                if (pf_lane && pf_ok) {
-                    const TcJob& jb = prm.jobs[pf.it.j];
-                    tma_prefetch_4d(&jb.map, pf.it.I * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
-                                    (int)pf.it.d);
-                    if (!pf.it.same)
-                        tma_prefetch_4d(&jb.map, pf.it.J * kBlockInputs * C::kBps, pf.it.c0, pf.kb * kTimeBlock,
-                                        (int)pf.it.d);
-                    pf_ok = cursor_next(prm, pf);
-                }
-                if (!ptx::mbar_wait_bounded_warp(bar_op_empty + 8 * os, oph ^ 1u, abort_flag, prm.wait_limit_ns)) {
-                    if (lane == 0) record_error(prm.status, abort_flag, kDevTimeoutFull, cur.kb);
-                    ok = false;
-                    break;
-                }
-                const TcJob& jb = prm.jobs[cur.it.j];
-                const bool same = cur.it.same;
-                const int n_tl = same ? jb.cpi : 2;
-                const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
-#pragma unroll
-                for (int v = 0; v < kSlots; ++v) {
-                    const int sl = cwarp + 8 * v;
-                    if (sl < n_tl * kSlices) {
-                        const int tl = sl / kSlices, part = sl % kSlices;
-                        const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
-                        if constexpr (C::kBits8) convert_words8(buf[u][v], out, part, cl);
-                        else convert_words4(buf[u][v], out, 2 * part + (lane >> 4), cl);
-                    }
-                }
-                fence_async_shared();   // generic-proxy writes -> visible to the tensor core
-                __syncwarp();
-                // self-test of the bounded waits: warp 0 withholds its arrival on one stage,
-                // so the MMA issuer's wait for it runs out
-                const bool withhold = cwarp == 0 && cur.item == prm.stall_item && cur.kb == 0;
-                if (lane == 0 && !withhold) ptx::mbar_arrive(bar_op_full + 8 * os);
-                if (++os == OS) {
-                    os = 0;
-                    oph ^= 1u;
-                }
-                cur_ok = cursor_next(prm, cur);
-            }
-        }
     } else if constexpr (C::kRaw) {
-        // ---------------- converters, raw ring feed (warps 6..13) ----------------
-        const int cwarp = warp - 6;         // 0..7
+        // ---------------- converters (the last kConvWarps warps) ----------------
+        const int cwarp = warp - 2 - C::kEpiWarps;   // 0 .. kConvWarps - 1
         const ConvLane cl = C::kBits8 ? conv_lane8(lane) : conv_lane4(lane);
         constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
         const uint32_t lane_byte = C::kBits8 ? 4u * lane : 4u * (lane & 15);
@@ -942,7 +771,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
                 // all loads of the warp's slices (slices cwarp and cwarp + 8) are issued before
                 // the first conversion, so their shared-memory latencies overlap
-                constexpr int kSlots = C::kBits8 ? 2 : 1;
+                constexpr int kSlots = (2 * kSlices + C::kConvWarps - 1) / C::kConvWarps;
                 uint32_t w[kSlots][8];
 #pragma unroll
                 for (int v = 0; v < kSlots; ++v) {
@@ -1059,7 +888,6 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->status = status;
     prm->wait_limit_ns = tune.wait_limit_ns ? tune.wait_limit_ns : kWaitLimitNs;
     prm->stall_item = tune.stall_item;
-    prm->l2_lead = tune.l2_lead > 0 ? tune.l2_lead : kDefaultL2Lead;
     if (map_lo) prm->map_lo = *map_lo;
     int64_t items = 0;
     int op_tiles = 1, raw_tiles = 1;
@@ -1080,11 +908,6 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock) : (sp.sample_bits == 4 ? 2048 : 16);
         // |D| <= chunk samples x max |x_a x_b|: 4-bit 2^17 x 2^6 = 2^23, 8-bit 512 x 2^14 = 2^23
         jb.f32_combine = !C::kSplit && (sp.sample_bits == 4 || jb.kp <= 512) ? 1 : 0;
-        jb.raw = static_cast<const uint8_t*>(sp.data);
-        jb.row_bytes = sp.n_inputs * C::kBps;
-        jb.t_stride = (int64_t)jb.row_bytes * sp.n_chan;
-        jb.d_stride = jb.t_stride * sp.n_time;
-        jb.n_time = sp.n_time;
         jb.item_begin = items;
         const int64_t job_items = (int64_t)sp.n_dumps * jb.n_groups * jb.n_tiles;
         if (job_items >= (int64_t{1} << 31)) {   // decode_item divides 32-bit item indices
@@ -1109,7 +932,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     const int operand_bytes = C::kTilesPerOperand * kTileBytes;
     prm->op_stage_bytes = op_tiles * operand_bytes;
     prm->b_offset = operand_bytes;
-    if (C::kRaw && !C::kGlobal) {
+    if (C::kRaw) {
         prm->raw_stage_bytes = raw_tiles * C::kRawTileBytes;
         prm->op_stages = tune.op_stages > 0 ? tune.op_stages : (prm->staged ? 3 : 4);
         // a requested depth that leaves fewer than 3 raw stages is reduced to what fits
@@ -1128,8 +951,6 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         prm->raw_stages = 0;
         prm->op_stages = (kSmemBudget - stage_space) / prm->op_stage_bytes;
         if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
-        // the global-load feed may ask for a shallower operand ring
-        if (C::kGlobal && tune.op_stages > 1 && tune.op_stages < prm->op_stages) prm->op_stages = tune.op_stages;
     }
     if (prm->op_stages < 2 || prm->op_stages > kMaxOpStages) {
         delete prm;
@@ -1193,29 +1014,20 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
         if (specs[j].sample_bits != bits || !tc_raw_supported(specs[j].n_inputs, bits) ||
             (specs[j].cpi != 1 && specs[j].cpi != 2) || (specs[j].cpi == 2 && specs[j].n_inputs > kBlockInputs))
             return cudaErrorInvalidValue;
-    const bool ring = tune.feed != kFeedGlobal;
     if (n_jobs == 1) {
-        if (bits == 8)
-            return ring ? launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s)
-                        : launch_jobs<kRaw8G, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
-        return ring ? launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s)
-                    : launch_jobs<kRaw4G, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        if (bits == 8) return launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        return launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
     }
     if (n_jobs > kMaxJobs) return cudaErrorInvalidValue;
-    if (bits == 8)
-        return ring ? launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s)
-                    : launch_jobs<kRaw8G, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
-    return ring ? launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s)
-                : launch_jobs<kRaw4G, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+    if (bits == 8) return launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+    return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
 }
 
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s, const TcTuning* tune) {
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
     TcTuning plan_tune;
-    plan_tune.feed = p.tc_feed;
     plan_tune.op_stages = p.tc_op_stages;
-    plan_tune.l2_lead = p.tc_l2_lead;
     const int cpi = tc_default_cpi(p.n_inputs);
     // one launch covers fewer than 2^31 work items (the kernel decodes 32-bit item indices)
     const int64_t items_per_dump = (int64_t)((p.n_chan + cpi - 1) / cpi) * (p.nb * (p.nb + 1) / 2);

@@ -52,29 +52,28 @@ def test_small_ragged_bit_exact(engine, n, c, t, bits):
     assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
 
 
-# the fused kernel's two feeds of packed samples (TMA ring / global loads), with ring depths
-# and L2 prefetch leads away from the defaults: every setting must give the same bits
-FEED_CASES = [(8, 2, 100, 8), (16, 3, 64, 4), (32, 3, 1000, 8), (64, 5, 1100, 8), (96, 1, 77, 4),
+# the fused kernel with operand-ring depths away from the default (single-block arrays use 4
+# epilogue + 8 converter warps, multi-block arrays 8 + 6): every setting gives the same bits
+RING_CASES = [(8, 2, 100, 8), (16, 3, 64, 4), (32, 3, 1000, 8), (64, 5, 1100, 8), (96, 1, 77, 4),
               (128, 2, 256, 4), (136, 3, 130, 8), (192, 1, 65, 8), (48, 2, 300, 4), (64, 1, 1, 8)]
-TUNINGS = [(1, 0, 0), (2, 0, 0), (2, 2, 1), (2, 3, 32), (1, 3, 0)]
 
 
-@pytest.mark.parametrize("tuning", TUNINGS)
-@pytest.mark.parametrize("n,c,t,bits", FEED_CASES)
-def test_fused_feeds_bit_exact(tuning, n, c, t, bits):
+@pytest.mark.parametrize("op_stages", [0, 2, 3, 5])
+@pytest.mark.parametrize("n,c,t,bits", RING_CASES)
+def test_fused_ring_depths_bit_exact(op_stages, n, c, t, bits):
     p = int_case(5000 + n + 3 * c + t, n, c, t, bits)
-    v = run_engine(p, n, c, t, bits, TC, tuning=tuning)[0]
+    v = run_engine(p, n, c, t, bits, TC, tuning=(op_stages,))[0]
     assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
 
 
-@pytest.mark.parametrize("feed", [1, 2])
-def test_fused_feeds_dumps_and_accumulate(feed):
-    n, c, t, bits, d = 64, 3, 200, 8, 3
+@pytest.mark.parametrize("n", [64, 192])
+def test_fused_dumps_and_accumulate(n):
+    c, t, bits, d = 3, 200, 8, 3
     p = np.concatenate([int_case(77 + k, n, c, t, bits) for k in range(d)])
     ref = np.stack([oracle.xcorr_int(p[k * t:(k + 1) * t], n, c, t, bits) for k in range(d)])
-    v = run_engine(p, n, c, t, bits, TC, n_dumps=d, tuning=(feed, 0, 0))
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=d)
     assert np.array_equal(v, ref)
-    v = run_engine(p, n, c, t, bits, TC, n_dumps=d, accumulate=True, vis_init=ref, tuning=(feed, 0, 0))
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=d, accumulate=True, vis_init=ref)
     assert np.array_equal(v, 2 * ref)
 
 
@@ -213,17 +212,16 @@ def test_float_engines_ragged(n, c, t):
     assert normwise_error(run_engine(x, n, c, t, 32, BF16X3)[0], ref, n) <= 1e-2
 
 
-@pytest.mark.parametrize("feed", [1, 2])
-def test_bounded_wait_gives_up_and_context_survives(feed):
-    # Failure detection without a GPU fault: one stage is withheld (by the TMA producer with
-    # the ring feed, by a converter warp with the global feed), the MMA issuer's bounded
-    # wait (100 ms) runs out, the kernel records a status and returns.
+@pytest.mark.parametrize("n", [64, 192])
+def test_bounded_wait_gives_up_and_context_survives(n):
+    # Failure detection without a GPU fault: the producer withholds one stage, the waiting
+    # role's bounded wait (100 ms) runs out, the kernel records a status and returns
+    # (single-block and multi-block arrays run different warp splits).
     import time
     from paper_0906_1887_gb300 import corr
-    n, c, t = 64, 16, 256
+    c, t = 16, 256
     p = int_case(31, n, c, t, 8)
     plan = corr.Plan(n, c, t, 8)
-    plan.set_tuning(feed, 0, 0)
     x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
     vis = plan.empty_vis(1, "cuda")
     t0 = time.time()
