@@ -46,9 +46,9 @@ SIGMA, RHO, SEED = 16.0, 0.1, 2000
 CHANNEL_RATE_HZ = 1.28e6 / 128.0
 WORKLOAD = "stream64_8bit: 64 inputs x 768 channels x 1000 samples/dump x 200 dumps, 8-bit complex Gaussian sigma=16 rho=0.1"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per dump of the fused kernel on this
-# workload, from one ncu capture of an 8-dump launch (786.7 MB read + 177.4 MB written), scaled
+# workload, from one ncu capture of an 8-dump launch (786.6 MB read + 177.0 MB written), scaled
 # by dumps; set to None whenever the kernel changes until it is captured again.
-DRAM_BYTES_PER_DUMP = (786.671104e6 + 177.364736e6) / 8
+DRAM_BYTES_PER_DUMP = (786.616576e6 + 177.040384e6) / 8
 
 
 def rank_max(x: float, dist, device) -> float:
@@ -190,7 +190,9 @@ def run_large(args):
     import torch
 
     from paper_0906_1887_gb300 import corr, synth
-    n, c, t, d = 1024, 1536, 256, 20
+    n, c, t, d = 1024, args.large_chans, 256, 20
+    if c != 1536:   # a reduced case for profiling captures: one dump
+        d = 1
     dev = torch.device("cuda", 0)
     plan = corr.Plan(n, c, t, 8)
     P = plan.n_baselines
@@ -239,7 +241,8 @@ def run_large(args):
     bytes_launch = per_dump + out_bytes
     gbs = bytes_launch / (ms_one / 1e3) / 1e9
     line = {"metric": "X-engine TeraCMAC/s", "value": cm / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s",
-            "workload": "large1024_8bit: 1024 inputs x 1536 channels x 256 samples/dump x 20 dumps, sigma 8",
+            "workload": f"large1024_8bit: 1024 inputs x {c} channels x 256 samples/dump x {d} dumps, sigma 8"
+                        + ("" if c == 1536 else " (reduced for profiling)"),
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "real_time_factor": (t * d / CHANNEL_RATE_HZ) / (ms / 1e3),
             "fp32_path": {"value": P * c * t / (ms32 / 1e3) / 1e12, "ms_per_dump": ms32,
@@ -409,6 +412,8 @@ def main():
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
     ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--large-chans", type=int, default=1536,
+                    help="channels of the large-array workload (fewer only for profiling captures)")
     args = ap.parse_args()
 
     if args.impl == "reference":
