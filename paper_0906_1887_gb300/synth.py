@@ -85,6 +85,14 @@ def packf32(re: np.ndarray, im: np.ndarray) -> np.ndarray:
     return out
 
 
+def pack_real8(x: np.ndarray) -> np.ndarray:
+    """Real 8-bit samples (int8 two's complement), one byte each, same order as ``x``."""
+    x = np.asarray(x)
+    if x.min(initial=0) < -128 or x.max(initial=0) > 127:
+        raise ValueError("8-bit samples must lie in [-128, 127]")
+    return x.astype(np.int8).view(np.uint8)
+
+
 def pack(re: np.ndarray, im: np.ndarray, bits: int) -> np.ndarray:
     if bits == 4:
         return pack4(re, im)
