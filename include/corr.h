@@ -192,6 +192,44 @@ corr_status corr_xengine_run_host(corr_plan plan, const void *host_packed, int n
                                   int dumps_per_chunk, int engine);
 
 /*
+ * F stage (Sec. 2, Sec. 4): the step in front of the X stage.  Each input's time samples are
+ * cut into frames and every frame is Fourier transformed into spectral channels:
+ *   complex samples: N_C samples -> N_C-point complex DFT -> N_C channels;
+ *   real samples:    2 N_C samples -> 2 N_C-point complex-to-complex DFT, channels 0 .. N_C
+ *                    (DC to Nyquist, N_C + 1 channels) kept, the mirrored half dropped
+ *                    (the paper transforms real input this way to keep power-of-two sizes).
+ * The DFT is the forward, unnormalised X_k = sum_s x_s exp(-2 pi i k s / L); channel c is
+ * bin c.  Computed in float32 on the GPU (Stockham radix-4/2 stages, twiddles rounded from
+ * double); the relative L2 error of a frame's spectrum against an exact transform is a few
+ * times 2^-24 log2 L.
+ *
+ *   kind               packed time samples, [time][n_inputs], input index fastest (Sec. 3)
+ *   CORR_F_COMPLEX8    2 bytes: re byte, im byte, int8
+ *   CORR_F_COMPLEX4    1 byte: high nibble re, low nibble im, two's complement
+ *   CORR_F_REAL8       1 byte: int8 real sample
+ *
+ * corr_fplan_create: n_inputs in [1, 8192]; the transform length (n_chan, or 2 n_chan for
+ * real samples) a power of two in [8, 4096].  Allocates a small twiddle table on the current
+ * device; the plan owns it.
+ * corr_fplan_info: channels produced per frame, transform length, and the bytes of one frame
+ * of input (L x n_inputs x bytes per sample) and of output (n_out_chan x n_inputs x 8).
+ * corr_fengine_run: n_frames consecutive frames; d_time holds n_frames x L time samples
+ * (2-byte aligned), d_spectra receives [n_frames][n_out_chan][n_inputs] complex float32
+ * (re, im; 8-byte aligned) -- the float sample layout of the X stage, so a plan with
+ * n_time = n_frames, n_chan = n_out_chan, sample_bits = 32 correlates it.  Asynchronous on
+ * `stream`; both buffers are the caller's.
+ */
+#define CORR_F_COMPLEX8 0
+#define CORR_F_COMPLEX4 1
+#define CORR_F_REAL8 2
+typedef struct corr_fplan_s *corr_fplan;
+corr_status corr_fplan_create(corr_fplan *out, int n_inputs, int n_chan, int kind);
+corr_status corr_fplan_destroy(corr_fplan plan);
+corr_status corr_fplan_info(corr_fplan plan, int *n_out_chan, int *transform_len, size_t *in_bytes_per_frame,
+                            size_t *out_bytes_per_frame);
+corr_status corr_fengine_run(corr_fplan plan, const void *d_time, int n_frames, void *d_spectra, void *stream);
+
+/*
  * Read and clear the plan's device status block (synchronises with the device).
  * *device_error receives 0, or the code a kernel recorded when one of its bounded
  * waits gave up.  Returns CORR_ETIMEOUT in that case, else CORR_OK / CORR_ECUDA.

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libcorr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, PENDING, EUNSUPPORTED = range(8)
 ENGINE_TC, ENGINE_FP32, ENGINE_BF16X3 = 0, 1, 2
+F_COMPLEX8, F_COMPLEX4, F_REAL8 = 0, 1, 2
 STATUS_NAMES = {OK: "CORR_OK", EINVAL: "CORR_EINVAL", ENOMEM: "CORR_ENOMEM", ECUDA: "CORR_ECUDA",
                 EBUSY: "CORR_EBUSY", ETIMEOUT: "CORR_ETIMEOUT", PENDING: "CORR_PENDING",
                 EUNSUPPORTED: "CORR_EUNSUPPORTED"}
@@ -57,6 +58,10 @@ SIGNATURES = {
     "corr_server_destroy": (_c_int, [_vp, ctypes.c_double]),
     "corr_host_alloc": (_c_int, [_P(_vp), _c_sz]),
     "corr_host_free": (_c_int, [_vp]),
+    "corr_fplan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int]),
+    "corr_fplan_destroy": (_c_int, [_vp]),
+    "corr_fplan_info": (_c_int, [_vp, _P(_c_int), _P(_c_int), _P(_c_sz), _P(_c_sz)]),
+    "corr_fengine_run": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
     "corr_average_host": (_c_int, [_vp, _c_sz, _c_i64, _vp]),
 }
 
@@ -108,6 +113,42 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+class FPlan:
+    """F-stage plan: n_inputs, n_chan channels, sample kind (F_COMPLEX8 / F_COMPLEX4 / F_REAL8)."""
+
+    def __init__(self, n_inputs: int, n_chan: int, kind: int):
+        h = ctypes.c_void_p()
+        check(lib().corr_fplan_create(ctypes.byref(h), n_inputs, n_chan, kind), "corr_fplan_create")
+        self._h = h
+        self.n_inputs, self.n_chan, self.kind = n_inputs, n_chan, kind
+        oc, tl, ib, ob = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().corr_fplan_info(h, ctypes.byref(oc), ctypes.byref(tl), ctypes.byref(ib), ctypes.byref(ob)),
+              "corr_fplan_info")
+        self.n_out_chan, self.transform_len = oc.value, tl.value
+        self.in_bytes_per_frame, self.out_bytes_per_frame = ib.value, ob.value
+
+    def run(self, time_samples, spectra, n_frames: int, stream=None):
+        """time_samples: n_frames x transform_len x n_inputs packed samples; spectra: float32
+        [n_frames][n_out_chan][n_inputs][2] (the X stage's float sample layout)."""
+        check(lib().corr_fengine_run(self._h, _ptr(time_samples), n_frames, _ptr(spectra), _stream_handle(stream)),
+              "corr_fengine_run")
+
+    def empty_spectra(self, n_frames: int, device="cuda"):
+        import torch
+        return torch.empty((n_frames, self.n_out_chan, self.n_inputs, 2), dtype=torch.float32, device=device)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().corr_fplan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -1,0 +1,229 @@
+// F stage of the FX correlator (Sec. 2, Sec. 4): unpack + per-input DFT of time blocks.
+//
+// The paper's GPU correlator unpacks a batch of time samples (input index fastest), reorders
+// it into per-input blocks and Fourier transforms each block into spectral channels: an
+// N_C-point complex transform for complex samples, and for real samples a 2 N_C-point
+// complex-to-complex transform of which channels 0 .. N_C are kept (Sec. 4).  Here one
+// kernel does both steps for a block of G inputs and one frame of L samples:
+//
+//   load    packed samples [t][input] -> float2 rows in shared memory, one row per input
+//           (coalesced along the inputs; rows padded to L + 1 so column reads do not
+//           collide in banks)
+//   FFT     Stockham autosort stages of radix 4 (radix 2 for the last one when log2 L is
+//           odd), ping-ponging between two shared buffers; twiddles exp(-2 pi i k / L) from
+//           a table computed on the host in double precision
+//   store   spectra [frame][channel][input] complex float32, coalesced along the inputs --
+//           exactly the float sample layout the X stage takes ([T][C][N], T = frames)
+//
+// A Stockham stage with sub-transform length Ns and radix R takes, for each j < L / R, the R
+// values v_r = x[j + r L / R], multiplies v_r by exp(-2 pi i (j mod Ns) r / (Ns R)), applies
+// the R-point DFT and writes output q to position (j - j mod Ns) R + j mod Ns + q Ns.  After
+// log_R L stages the result is in natural order.  The DFT is the forward, unnormalised one,
+// X_k = sum_s x_s exp(-2 pi i k s / L); channel c is bin c.
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "corr_internal.h"
+
+namespace corr {
+namespace {
+
+constexpr int kFPoints = 4096;   // complex points per CTA (inputs x transform length)
+constexpr int kFThreads = 256;
+constexpr int kFMinLen = 8, kFMaxLen = 4096;
+
+struct FPlan {
+    int n_inputs = 0;
+    int n_chan = 0;
+    int kind = 0;        // CORR_F_COMPLEX8 / CORR_F_COMPLEX4 / CORR_F_REAL8
+    int L = 0;           // transform length: N_C, or 2 N_C for real samples
+    int n_out = 0;       // channels produced: N_C, or N_C + 1
+    int G = 0;           // inputs per CTA
+    int device = 0;
+    float2* d_tw = nullptr;   // exp(-2 pi i k / L), k < L
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// one packed sample -> complex float (values are small integers: exact)
+template <int KIND>
+__device__ __forceinline__ float2 load_sample(const uint8_t* __restrict__ in, size_t idx) {
+    if constexpr (KIND == CORR_F_COMPLEX8) {
+        const char2 v = reinterpret_cast<const char2*>(in)[idx];
+        return make_float2((float)v.x, (float)v.y);
+    } else if constexpr (KIND == CORR_F_COMPLEX4) {
+        const int b = in[idx];
+        int re = b >> 4, im = b & 15;
+        re -= (re & 8) << 1;   // two's complement nibbles
+        im -= (im & 8) << 1;
+        return make_float2((float)re, (float)im);
+    } else {
+        const signed char v = reinterpret_cast<const signed char*>(in)[idx];
+        return make_float2((float)v, 0.f);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
+                                                            const float2* __restrict__ tw, int N, int L, int n_out,
+                                                            int G, int n_frames) {
+    extern __shared__ float2 fsm[];
+    const int pitch = L + 1;
+    const int n0 = blockIdx.x * G;
+    const int g_n = min(G, N - n0);
+    for (int f = blockIdx.y; f < n_frames; f += gridDim.y) {
+        float2* a = fsm;
+        float2* b = fsm + G * pitch;
+        // load: sample s of input n0 + g, time f L + s -> a[g][s]
+        const size_t row0 = (size_t)f * L;
+        for (int idx = threadIdx.x; idx < L * G; idx += blockDim.x) {
+            const int s = idx / G, g = idx - s * G;
+            float2 v = make_float2(0.f, 0.f);
+            if (g < g_n) v = load_sample<KIND>(in, (row0 + s) * N + n0 + g);
+            a[g * pitch + s] = v;
+        }
+        __syncthreads();
+        for (int Ns = 1; Ns < L;) {
+            const int R = Ns * 4 <= L ? 4 : 2;
+            const int LR = L / R;
+            const int tstep = L / (Ns * R);   // twiddle table step for (j mod Ns) r
+            for (int task = threadIdx.x; task < LR * G; task += blockDim.x) {
+                const int g = task / LR, j = task - g * LR;
+                const float2* src = a + g * pitch;
+                float2* dst = b + g * pitch;
+                const int k = j & (Ns - 1);
+                const int d = (j - k) * R + k;
+                if (R == 4) {
+                    float2 v0 = src[j], v1 = src[j + LR], v2 = src[j + 2 * LR], v3 = src[j + 3 * LR];
+                    if (k) {
+                        v1 = cmul(v1, tw[k * tstep]);
+                        v2 = cmul(v2, tw[2 * k * tstep]);
+                        v3 = cmul(v3, tw[3 * k * tstep]);
+                    }
+                    const float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
+                    const float2 e = csub(v1, v3);
+                    const float2 t3 = make_float2(e.y, -e.x);   // (v1 - v3) * (-i)
+                    dst[d] = cadd(t0, t2);
+                    dst[d + Ns] = cadd(t1, t3);
+                    dst[d + 2 * Ns] = csub(t0, t2);
+                    dst[d + 3 * Ns] = csub(t1, t3);
+                } else {
+                    float2 v0 = src[j], v1 = src[j + LR];
+                    if (k) v1 = cmul(v1, tw[k * tstep]);
+                    dst[d] = cadd(v0, v1);
+                    dst[d + Ns] = csub(v0, v1);
+                }
+            }
+            __syncthreads();
+            float2* t = a;
+            a = b;
+            b = t;
+            Ns *= R;
+        }
+        // store: channel c of input n0 + g -> out[f][c][n0 + g]
+        float2* o = out + (size_t)f * n_out * N + n0;
+        for (int idx = threadIdx.x; idx < n_out * G; idx += blockDim.x) {
+            const int c = idx / G, g = idx - c * G;
+            if (g < g_n) o[(size_t)c * N + g] = a[g * pitch + c];
+        }
+        __syncthreads();   // the next frame reuses the buffers
+    }
+}
+
+size_t fplan_smem(const FPlan& p) { return (size_t)2 * p.G * (p.L + 1) * sizeof(float2); }
+
+template <int KIND>
+cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
+    const int smem = (int)fplan_smem(p);
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((p.n_inputs + p.G - 1) / p.G, n_frames < 65535 ? n_frames : 65535);
+    fengine_kernel<KIND><<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in), static_cast<float2*>(d_out),
+                                                       p.d_tw, p.n_inputs, p.L, p.n_out, p.G, n_frames);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace corr
+
+using namespace corr;
+
+extern "C" {
+
+corr_status corr_fplan_create(corr_fplan* out, int n_inputs, int n_chan, int kind) {
+    if (!out) return set_error(CORR_EINVAL, "corr_fplan_create: out is NULL");
+    *out = nullptr;
+    if (n_inputs < 1 || n_inputs > kMaxInputs)
+        return set_error(CORR_EINVAL, "n_inputs=%d outside [1, %d]", n_inputs, kMaxInputs);
+    if (kind != CORR_F_COMPLEX8 && kind != CORR_F_COMPLEX4 && kind != CORR_F_REAL8)
+        return set_error(CORR_EINVAL, "kind=%d is not CORR_F_COMPLEX8/COMPLEX4/REAL8", kind);
+    const int L = kind == CORR_F_REAL8 ? 2 * n_chan : n_chan;
+    if (n_chan < 1 || L < kFMinLen || L > kFMaxLen || (L & (L - 1)))
+        return set_error(CORR_EINVAL, "transform length %d (n_chan=%d) must be a power of two in [%d, %d]", L, n_chan,
+                         kFMinLen, kFMaxLen);
+    FPlan* p = new (std::nothrow) FPlan();
+    if (!p) return set_error(CORR_ENOMEM, "corr_fplan_create: host allocation failed");
+    p->n_inputs = n_inputs;
+    p->n_chan = n_chan;
+    p->kind = kind;
+    p->L = L;
+    p->n_out = kind == CORR_F_REAL8 ? n_chan + 1 : n_chan;
+    p->G = kFPoints / L < 64 ? (kFPoints / L > 0 ? kFPoints / L : 1) : 64;
+    cudaError_t e = cudaGetDevice(&p->device);
+    std::vector<float2> tw(L);
+    for (int k = 0; k < L; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)L;
+        tw[k] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, (size_t)L * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), (size_t)L * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (p->d_tw) cudaFree(p->d_tw);
+        delete p;
+        return cuda_error(e, "corr_fplan_create");
+    }
+    *out = reinterpret_cast<corr_fplan>(p);
+    return CORR_OK;
+}
+
+corr_status corr_fplan_destroy(corr_fplan plan) {
+    if (!plan) return CORR_OK;
+    FPlan* p = reinterpret_cast<FPlan*>(plan);
+    if (p->d_tw) cudaFree(p->d_tw);
+    delete p;
+    return CORR_OK;
+}
+
+corr_status corr_fplan_info(corr_fplan plan, int* n_out_chan, int* transform_len, size_t* in_bytes_per_frame,
+                            size_t* out_bytes_per_frame) {
+    if (!plan) return set_error(CORR_EINVAL, "corr_fplan_info: plan is NULL");
+    const FPlan* p = reinterpret_cast<const FPlan*>(plan);
+    const size_t bps = p->kind == CORR_F_COMPLEX8 ? 2 : 1;
+    if (n_out_chan) *n_out_chan = p->n_out;
+    if (transform_len) *transform_len = p->L;
+    if (in_bytes_per_frame) *in_bytes_per_frame = (size_t)p->L * p->n_inputs * bps;
+    if (out_bytes_per_frame) *out_bytes_per_frame = (size_t)p->n_out * p->n_inputs * sizeof(float2);
+    return CORR_OK;
+}
+
+corr_status corr_fengine_run(corr_fplan plan, const void* d_time, int n_frames, void* d_spectra, void* stream) {
+    if (!plan || !d_time || !d_spectra) return set_error(CORR_EINVAL, "corr_fengine_run: NULL argument");
+    if (n_frames < 1) return set_error(CORR_EINVAL, "n_frames=%d must be >= 1", n_frames);
+    const FPlan* p = reinterpret_cast<const FPlan*>(plan);
+    if ((reinterpret_cast<uintptr_t>(d_time) & 1u) || (reinterpret_cast<uintptr_t>(d_spectra) & 7u))
+        return set_error(CORR_EINVAL, "corr_fengine_run: samples must be 2-byte and spectra 8-byte aligned");
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p->kind == CORR_F_COMPLEX8) e = launch_fengine<CORR_F_COMPLEX8>(*p, d_time, n_frames, d_spectra, s);
+    else if (p->kind == CORR_F_COMPLEX4) e = launch_fengine<CORR_F_COMPLEX4>(*p, d_time, n_frames, d_spectra, s);
+    else e = launch_fengine<CORR_F_REAL8>(*p, d_time, n_frames, d_spectra, s);
+    if (e != cudaSuccess) return cuda_error(e, "F-stage launch");
+    return CORR_OK;
+}
+
+}  // extern "C"

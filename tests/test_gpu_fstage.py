@@ -1,0 +1,147 @@
+"""GPU parity of the F stage (Sec. 2, Sec. 4) and of the FX chain, through the C ABI.
+
+F stage: the float32 spectra of every (frame, input) against the complex128 oracle, in
+relative L2 norm.  A radix-2/4 FFT in float32 with correctly rounded twiddles has a
+normwise error of a small multiple of 2^-24 log2 L; the bound used is 4 x 2^-24 x log2 L
+(a CPU model of the kernel's stages in complex64 stays below 1.2e-7 for L up to 4096).
+All-zero blocks (padded inputs) must come out exactly zero.
+
+FX chain: GPU F stage -> GPU X stage on the spectra, against the oracle's complex128 F and
+X stages, in the normwise metric max |V - V64| / sqrt(V64_ii V64_jj): each spectrum enters
+V twice, so the F-stage bound counts twice, plus the X engine's own bound (1e-6 for FP32,
+1e-2 for BF16x3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fstage
+from paper_0906_1887_gb300 import synth
+from _gpu_helpers import normwise_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KIND_ID = {"c8": 0, "c4": 1, "r8": 2}
+EPS = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0906_1887_gb300 import corr
+    corr.lib()
+
+
+def _time_samples(seed, n_samples, n_inputs, kind):
+    lo, hi = (-8, 7) if kind == "c4" else (-128, 127)
+    re, im = synth.uniform_ints(seed, n_samples, 1, n_inputs, lo, hi)
+    if kind == "r8":
+        return synth.pack_real8(re[:, 0, :])
+    return synth.pack(re, im, 8 if kind == "c8" else 4)
+
+
+def _run_f(packed, n_inputs, n_chan, n_frames, kind):
+    from paper_0906_1887_gb300 import corr
+    fp = corr.FPlan(n_inputs, n_chan, KIND_ID[kind])
+    x = torch.from_numpy(np.ascontiguousarray(packed).view(np.uint8).reshape(-1).copy()).cuda()
+    spec = fp.empty_spectra(n_frames)
+    spec.fill_(float("nan"))   # every element must be written
+    fp.run(x, spec, n_frames)
+    torch.cuda.synchronize()
+    out = spec.cpu().numpy()
+    fp.close()
+    return out[..., 0].astype(np.float64) + 1j * out[..., 1]
+
+
+def _check_spectra(got, ref, L):
+    bound = 4 * EPS * math.log2(L)
+    for f in range(ref.shape[0]):
+        for n in range(ref.shape[2]):
+            r = ref[f, :, n]
+            g = got[f, :, n]
+            nr = np.linalg.norm(r)
+            if nr == 0:
+                assert np.all(g == 0)
+            else:
+                assert np.linalg.norm(g - r) / nr <= bound, (f, n, np.linalg.norm(g - r) / nr, bound)
+
+
+CASES = [  # (kind, n_chan, n_inputs, n_frames): every transform length 8 .. 4096, ragged inputs
+    ("c8", 8, 1, 1), ("c8", 16, 3, 2), ("c8", 32, 64, 3), ("c8", 128, 64, 5), ("c8", 128, 70, 2),
+    ("c8", 256, 5, 2), ("c8", 1024, 33, 1), ("c8", 4096, 2, 2),
+    ("c4", 8, 7, 3), ("c4", 64, 64, 2), ("c4", 128, 130, 1), ("c4", 2048, 3, 1),
+    ("r8", 4, 2, 2), ("r8", 64, 64, 2), ("r8", 128, 9, 3), ("r8", 2048, 1, 1),
+]
+
+
+@pytest.mark.parametrize("kind,n_chan,n_inputs,n_frames", CASES)
+def test_fstage_matches_oracle(kind, n_chan, n_inputs, n_frames):
+    L = fstage.transform_length(n_chan, kind)
+    p = _time_samples(100 + n_chan + n_inputs, n_frames * L, n_inputs, kind)
+    got = _run_f(p, n_inputs, n_chan, n_frames, kind)
+    ref = fstage.fstage(p, n_inputs, n_chan, n_frames, kind)
+    assert got.shape == ref.shape
+    _check_spectra(got, ref, L)
+
+
+def test_fstage_tone_lands_in_its_channel():
+    # an integer tone at bin L/4 on input 1 only: one channel of one input carries A L
+    n_chan, N, F = 128, 4, 2
+    s = np.arange(F * n_chan)
+    tone = np.array([1, 1j, -1, -1j])[s % 4] * 100
+    re = np.zeros((F * n_chan, 1, N), np.int16); im = np.zeros_like(re)
+    re[:, 0, 1] = tone.real.round(); im[:, 0, 1] = tone.imag.round()
+    got = _run_f(synth.pack(re, im, 8), N, n_chan, F, "c8")
+    mag = np.abs(got)
+    assert np.allclose(mag[:, n_chan // 4, 1], 100 * n_chan, rtol=1e-6)
+    mag[:, n_chan // 4, 1] = 0
+    assert mag.max() <= 1e-3
+
+
+def test_fstage_more_frames_than_one_grid_row():
+    # 70000 frames: the kernel loops over frames beyond the 65535 grid rows
+    n_chan, N, F = 8, 1, 70000
+    p = _time_samples(7, F * n_chan, N, "c8")
+    got = _run_f(p, N, n_chan, F, "c8")
+    ref = fstage.fstage(p, N, n_chan, F, "c8")
+    err = np.linalg.norm((got - ref).reshape(F, -1), axis=1) / np.maximum(np.linalg.norm(ref.reshape(F, -1), axis=1), 1)
+    assert err.max() <= 4 * EPS * 3
+
+
+@pytest.mark.parametrize("engine,x_bound", [(1, 1e-6), (2, 1e-2)])
+@pytest.mark.parametrize("kind,n_chan,n_inputs,n_frames", [("c8", 128, 64, 40), ("c4", 64, 33, 25), ("r8", 32, 16, 30)])
+def test_fx_chain(engine, x_bound, kind, n_chan, n_inputs, n_frames):
+    from paper_0906_1887_gb300 import corr
+    L = fstage.transform_length(n_chan, kind)
+    p = _time_samples(300 + n_chan, n_frames * L, n_inputs, kind)
+    fp = corr.FPlan(n_inputs, n_chan, KIND_ID[kind])
+    x = torch.from_numpy(np.ascontiguousarray(p).view(np.uint8).reshape(-1).copy()).cuda()
+    spec = fp.empty_spectra(n_frames)
+    fp.run(x, spec, n_frames)
+    C = fp.n_out_chan
+    xplan = corr.Plan(n_inputs, C, n_frames, 32)
+    vis = xplan.empty_vis(1, "cuda")
+    ws = xplan.empty_workspace(engine, 1, "cuda")
+    xplan.run(spec, vis, ws, engine=engine)
+    torch.cuda.synchronize()
+    assert xplan.check_device() == 0
+    ref = fstage.xcorr_spectra(fstage.fstage(p, n_inputs, n_chan, n_frames, kind))
+    err = normwise_error(vis.cpu().numpy()[0].astype(np.float64), ref, n_inputs)
+    assert err <= 2 * 4 * EPS * math.log2(L) + x_bound, err
+    fp.close()
+    xplan.close()
+
+
+def test_fplan_rejects_bad_sizes():
+    from paper_0906_1887_gb300 import corr
+    with pytest.raises(corr.CorrError):
+        corr.FPlan(4, 100, 0)        # not a power of two
+    with pytest.raises(corr.CorrError):
+        corr.FPlan(4, 4, 0)          # transform shorter than 8
+    with pytest.raises(corr.CorrError):
+        corr.FPlan(4, 4096, 2)       # real: 8192-point transform
+    with pytest.raises(corr.CorrError):
+        corr.FPlan(4, 64, 3)         # unknown kind
