@@ -319,6 +319,74 @@ def run_batch(args):
     b.close()
 
 
+def run_fx(args):
+    """The paper's prototype configuration end to end on the GPU (Sec. 5, Table 3): 64 inputs of
+    1.28 MHz complex 8-bit samples, F stage into 128 channels, X stage over 1 s of frames."""
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    n, c, frames = 64, 128, 10000   # 1.28 MHz / 128 channels = 10 k frames per second of data
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    fplan = corr.FPlan(n, c, corr.F_COMPLEX8)
+    x = synth.torch_correlated_gaussian_packed8(1, frames * c, 1, n, 16.0, 0.1, 5000, dev).reshape(-1)
+    spec = fplan.empty_spectra(frames, dev)
+    xplan = corr.Plan(n, c, frames, 32)
+    vis = xplan.empty_vis(1, dev)
+    P = xplan.n_baselines
+    hbm, _, src = _peaks()
+    f_bytes = frames * (fplan.in_bytes_per_frame + fplan.out_bytes_per_frame)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2, written between steps
+
+    def timed(fn, steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[2 * k].record(stream)
+            fn()
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        return sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)) / steps
+
+    res = {}
+    for name, engine in (("fp32", corr.ENGINE_FP32), ("bf16x3", corr.ENGINE_BF16X3)):
+        ws = xplan.empty_workspace(engine, 1, dev)
+
+        def step():
+            fplan.run(x, spec, frames, stream=stream)
+            xplan.run(spec, vis, ws, engine=engine, stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        assert xplan.check_device() == 0
+        res[name] = timed(step, args.steps)
+        del ws
+    f_ms = timed(lambda: fplan.run(x, spec, frames, stream=stream), args.steps)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    timed(lambda: fplan.run(x, spec, frames, stream=stream), args.steps)
+    clk = clocks.stop()
+    ms = res["fp32"]
+    cm = P * c * frames
+    gbs = f_bytes / (f_ms / 1e3) / 1e9
+    line = {"metric": "FX chain TeraCMAC/s (F stage + X stage, FP32 X engine)", "value": cm / (ms / 1e3) / 1e12,
+            "unit": "TeraCMAC/s",
+            "workload": "mwa32t_fx: 64 inputs x 1.28 MHz complex 8-bit (sigma 16, rho 0.1), 128 channels, "
+                        "1 s of data per step (10000 frames), one dump",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "real_time_factor": 1000.0 / ms,
+            "bf16x3_chain": {"ms_per_step": res["bf16x3"], "value": cm / (res["bf16x3"] / 1e3) / 1e12,
+                             "real_time_factor": 1000.0 / res["bf16x3"]},
+            "fstage": {"kernel": "fengine_kernel<complex8>", "ms": f_ms, "bound": "hbm", "achieved": gbs,
+                       "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": f_bytes,
+                       "peak_source": src},
+            "paper_context": "C1060 (Table 3): unpack 53 + FFT 53 + CMAC (GP, G=4) 185 = 291 ms per second of data",
+            "l2": "256 MB flush written between timed steps", "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     import torch
 
@@ -410,7 +478,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--dumps", type=int, default=N_DUMPS,
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve"])
+    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--large-chans", type=int, default=1536,
                     help="channels of the large-array workload (fewer only for profiling captures)")
@@ -420,7 +488,7 @@ def main():
         reference_arm(args)
         return
     if args.workload != "stream":
-        {"large": run_large, "batch": run_batch, "serve": run_serve}[args.workload](args)
+        {"large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx}[args.workload](args)
         return
 
     import torch

@@ -40,7 +40,9 @@ struct FPlan {
     int L = 0;           // transform length: N_C, or 2 N_C for real samples
     int n_out = 0;       // channels produced: N_C, or N_C + 1
     int G = 0;           // inputs per CTA
+    int log2L = 0, log2G = 0;
     int device = 0;
+    int n_sm = 0;
     float2* d_tw = nullptr;   // exp(-2 pi i k / L), k < L
 };
 
@@ -50,60 +52,91 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// one packed sample -> complex float (values are small integers: exact)
+// raw packed sample: 2 bytes for complex 8-bit, 1 byte otherwise
 template <int KIND>
-__device__ __forceinline__ float2 load_sample(const uint8_t* __restrict__ in, size_t idx) {
+__device__ __forceinline__ uint32_t load_raw(const uint8_t* __restrict__ in, size_t idx) {
+    if constexpr (KIND == CORR_F_COMPLEX8) return reinterpret_cast<const unsigned short*>(in)[idx];
+    else return in[idx];
+}
+
+// the samples thread `tid` moves of one frame: element idx = tid + q x threads is sample
+// s = idx >> log2G of input n0 + (idx & (G - 1)); zero outside the array
+template <int KIND, int PER>
+__device__ __forceinline__ void fetch_frame(uint32_t (&raw)[PER], const uint8_t* __restrict__ in, size_t row0, int N,
+                                            int n0, int g_n, int log2G, int pts) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int idx = threadIdx.x + q * kFThreads;
+        const int s = idx >> log2G, g = idx & ((1 << log2G) - 1);
+        raw[q] = (idx < pts && g < g_n) ? load_raw<KIND>(in, (row0 + s) * N + n0 + g) : 0u;
+    }
+}
+
+// one packed sample -> complex float (small integers: exact)
+template <int KIND>
+__device__ __forceinline__ float2 unpack_raw(uint32_t r) {
     if constexpr (KIND == CORR_F_COMPLEX8) {
-        const char2 v = reinterpret_cast<const char2*>(in)[idx];
-        return make_float2((float)v.x, (float)v.y);
+        return make_float2((float)(signed char)(r & 0xFF), (float)(signed char)(r >> 8));
     } else if constexpr (KIND == CORR_F_COMPLEX4) {
-        const int b = in[idx];
-        int re = b >> 4, im = b & 15;
+        int re = (int)(r >> 4), im = (int)(r & 15);
         re -= (re & 8) << 1;   // two's complement nibbles
         im -= (im & 8) << 1;
         return make_float2((float)re, (float)im);
     } else {
-        const signed char v = reinterpret_cast<const signed char*>(in)[idx];
-        return make_float2((float)v, 0.f);
+        return make_float2((float)(signed char)r, 0.f);
     }
 }
 
+// Persistent over frames: frame f + gridDim.y's samples are fetched into registers (kPer per
+// thread) while frame f is transformed, so the global loads overlap the FFT.
 template <int KIND>
 __global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
-                                                            const float2* __restrict__ tw, int N, int L, int n_out,
-                                                            int G, int n_frames) {
+                                                            const float2* __restrict__ tw, int N, int log2L, int n_out,
+                                                            int log2G, int n_frames) {
+    constexpr int kPer = kFPoints / kFThreads;   // samples per thread per frame (at most)
     extern __shared__ float2 fsm[];
+    const int L = 1 << log2L, G = 1 << log2G;
     const int pitch = L + 1;
+    float2* const buf0 = fsm;
+    float2* const buf1 = fsm + G * pitch;
+    float2* const twl = fsm + 2 * G * pitch;
     const int n0 = blockIdx.x * G;
     const int g_n = min(G, N - n0);
-    for (int f = blockIdx.y; f < n_frames; f += gridDim.y) {
-        float2* a = fsm;
-        float2* b = fsm + G * pitch;
-        // load: sample s of input n0 + g, time f L + s -> a[g][s]
-        const size_t row0 = (size_t)f * L;
-        for (int idx = threadIdx.x; idx < L * G; idx += blockDim.x) {
-            const int s = idx / G, g = idx - s * G;
-            float2 v = make_float2(0.f, 0.f);
-            if (g < g_n) v = load_sample<KIND>(in, (row0 + s) * N + n0 + g);
-            a[g * pitch + s] = v;
+    const int pts = L * G;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) twl[k] = tw[k];
+
+    uint32_t raw[kPer];
+    int f = blockIdx.y;
+    if (f < n_frames) fetch_frame<KIND>(raw, in, (size_t)f * L, N, n0, g_n, log2G, pts);
+    for (; f < n_frames; f += gridDim.y) {
+        float2* a = buf0;
+        float2* b = buf1;
+        // sample s of input n0 + g, time f L + s -> a[g][s]
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = threadIdx.x + q * kFThreads;
+            if (idx < pts) a[(idx & (G - 1)) * pitch + (idx >> log2G)] = unpack_raw<KIND>(raw[q]);
         }
         __syncthreads();
-        for (int Ns = 1; Ns < L;) {
+        if (f + (int)gridDim.y < n_frames)
+            fetch_frame<KIND>(raw, in, (size_t)(f + gridDim.y) * L, N, n0, g_n, log2G, pts);
+        for (int Ns = 1, log2Ns = 0; Ns < L;) {
             const int R = Ns * 4 <= L ? 4 : 2;
-            const int LR = L / R;
-            const int tstep = L / (Ns * R);   // twiddle table step for (j mod Ns) r
+            const int log2LR = log2L - (R == 4 ? 2 : 1);
+            const int LR = 1 << log2LR;
+            const int tshift = log2L - log2Ns - (R == 4 ? 2 : 1);   // twiddle step L / (Ns R)
             for (int task = threadIdx.x; task < LR * G; task += blockDim.x) {
-                const int g = task / LR, j = task - g * LR;
+                const int g = task >> log2LR, j = task & (LR - 1);
                 const float2* src = a + g * pitch;
                 float2* dst = b + g * pitch;
                 const int k = j & (Ns - 1);
-                const int d = (j - k) * R + k;
+                const int d = ((j - k) << (R == 4 ? 2 : 1)) + k;
                 if (R == 4) {
                     float2 v0 = src[j], v1 = src[j + LR], v2 = src[j + 2 * LR], v3 = src[j + 3 * LR];
                     if (k) {
-                        v1 = cmul(v1, tw[k * tstep]);
-                        v2 = cmul(v2, tw[2 * k * tstep]);
-                        v3 = cmul(v3, tw[3 * k * tstep]);
+                        v1 = cmul(v1, twl[k << tshift]);
+                        v2 = cmul(v2, twl[(2 * k) << tshift]);
+                        v3 = cmul(v3, twl[(3 * k) << tshift]);
                     }
                     const float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
                     const float2 e = csub(v1, v3);
@@ -114,7 +147,7 @@ __global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __res
                     dst[d + 3 * Ns] = csub(t1, t3);
                 } else {
                     float2 v0 = src[j], v1 = src[j + LR];
-                    if (k) v1 = cmul(v1, tw[k * tstep]);
+                    if (k) v1 = cmul(v1, twl[k << tshift]);
                     dst[d] = cadd(v0, v1);
                     dst[d + Ns] = csub(v0, v1);
                 }
@@ -124,27 +157,36 @@ __global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __res
             a = b;
             b = t;
             Ns *= R;
+            log2Ns += R == 4 ? 2 : 1;
         }
-        // store: channel c of input n0 + g -> out[f][c][n0 + g]
+        // channel c of input n0 + g -> out[f][c][n0 + g]
         float2* o = out + (size_t)f * n_out * N + n0;
         for (int idx = threadIdx.x; idx < n_out * G; idx += blockDim.x) {
-            const int c = idx / G, g = idx - c * G;
+            const int c = idx >> log2G, g = idx & (G - 1);
             if (g < g_n) o[(size_t)c * N + g] = a[g * pitch + c];
         }
         __syncthreads();   // the next frame reuses the buffers
     }
 }
 
-size_t fplan_smem(const FPlan& p) { return (size_t)2 * p.G * (p.L + 1) * sizeof(float2); }
+size_t fplan_smem(const FPlan& p) { return ((size_t)2 * p.G * (p.L + 1) + p.L) * sizeof(float2); }
 
 template <int KIND>
 cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
     const int smem = (int)fplan_smem(p);
     cudaError_t e = cudaFuncSetAttribute(fengine_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((p.n_inputs + p.G - 1) / p.G, n_frames < 65535 ? n_frames : 65535);
+    // persistent over frames: enough CTAs to fill every SM a few times over
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fengine_kernel<KIND>, kFThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int groups = (p.n_inputs + p.G - 1) / p.G;
+    int rows = (p.n_sm * (per_sm > 0 ? per_sm : 1) * 4 + groups - 1) / groups;
+    if (rows > n_frames) rows = n_frames;
+    if (rows > 65535) rows = 65535;
+    const dim3 grid(groups, rows);
     fengine_kernel<KIND><<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in), static_cast<float2*>(d_out),
-                                                       p.d_tw, p.n_inputs, p.L, p.n_out, p.G, n_frames);
+                                                       p.d_tw, p.n_inputs, p.log2L, p.n_out, p.log2G, n_frames);
     return cudaGetLastError();
 }
 
@@ -174,7 +216,10 @@ corr_status corr_fplan_create(corr_fplan* out, int n_inputs, int n_chan, int kin
     p->L = L;
     p->n_out = kind == CORR_F_REAL8 ? n_chan + 1 : n_chan;
     p->G = kFPoints / L < 64 ? (kFPoints / L > 0 ? kFPoints / L : 1) : 64;
+    while ((1 << p->log2L) < L) ++p->log2L;
+    while ((1 << p->log2G) < p->G) ++p->log2G;
     cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
     std::vector<float2> tw(L);
     for (int k = 0; k < L; ++k) {
         const double ang = -2.0 * M_PI * (double)k / (double)L;
