@@ -9,9 +9,14 @@
 //   load    packed samples [t][input] -> float2 rows in shared memory, one row per input
 //           (coalesced along the inputs; rows padded to L + 1 so column reads do not
 //           collide in banks)
-//   FFT     Stockham autosort stages of radix 4 (radix 2 for the last one when log2 L is
-//           odd), ping-ponging between two shared buffers; twiddles exp(-2 pi i k / L) from
-//           a table computed on the host in double precision
+//   FFT     Stockham autosort stages of radix 16 (the last one of radix 8, 4 or 2 when
+//           log2 L is not a multiple of 4), ping-ponging between two shared buffers: each
+//           task loads R values, applies the stage twiddles (a table exp(-2 pi i k / L)
+//           computed on the host in double precision) and does the R-point DFT in registers
+//           (radix-2 butterflies with exact constant twiddles of the 16th roots of unity).
+//           L = 128, the paper's channel count, takes two stages (16 x 8).  Rows are padded
+//           one element per 16 so the strided stores of the first stage, and the column
+//           reads of the load and store phases, fall in distinct banks
 //   store   spectra [frame][channel][input] complex float32, coalesced along the inputs --
 //           exactly the float sample layout the X stage takes ([T][C][N], T = frames)
 //
@@ -52,6 +57,91 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
+// position of row element i: one pad element after every 16
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+// x * exp(-2 pi i a / 16) for a compile-time a in 0..7 (the roots a DFT of size <= 16 uses);
+// the constants are cos and sin of multiples of pi / 8, correctly rounded to float
+template <int A>
+__device__ __forceinline__ float2 rot16(float2 x) {
+    constexpr float kC1 = 0.92387953251128676f;   // cos(pi / 8)
+    constexpr float kS1 = 0.38268343236508977f;   // sin(pi / 8)
+    constexpr float kH = 0.70710678118654752f;    // cos(pi / 4)
+    if constexpr (A == 0) return x;
+    else if constexpr (A == 4) return make_float2(x.y, -x.x);
+    else if constexpr (A == 2) return make_float2(kH * (x.x + x.y), kH * (x.y - x.x));
+    else if constexpr (A == 6) return make_float2(kH * (x.y - x.x), -kH * (x.x + x.y));
+    else if constexpr (A == 1) return cmul(x, make_float2(kC1, -kS1));
+    else if constexpr (A == 3) return cmul(x, make_float2(kS1, -kC1));
+    else if constexpr (A == 5) return cmul(x, make_float2(-kS1, -kC1));
+    else return cmul(x, make_float2(-kC1, -kS1));
+}
+
+template <int M>
+__host__ __device__ constexpr int bit_reverse(int r) {
+    int o = 0;
+    for (int b = 0; b < M; ++b) o |= ((r >> b) & 1) << (M - 1 - b);
+    return o;
+}
+
+// one radix-2 butterfly level of an in-register DIT DFT: groups of SIZE, element j of a group
+// combined with j + SIZE / 2 after a rotation by exp(-2 pi i j / SIZE)
+template <int R, int SIZE, int J>
+__device__ __forceinline__ void dit_level(float2 (&x)[R], int k0) {
+    if constexpr (J < SIZE / 2) {
+        const float2 u = x[k0 + J];
+        const float2 t = rot16<J * (16 / SIZE)>(x[k0 + J + SIZE / 2]);
+        x[k0 + J] = cadd(u, t);
+        x[k0 + J + SIZE / 2] = csub(u, t);
+        dit_level<R, SIZE, J + 1>(x, k0);
+    }
+}
+
+template <int R, int SIZE>
+__device__ __forceinline__ void dit_levels(float2 (&x)[R]) {
+    if constexpr (SIZE <= R) {
+#pragma unroll
+        for (int k0 = 0; k0 < R; k0 += SIZE) dit_level<R, SIZE, 0>(x, k0);
+        dit_levels<R, SIZE * 2>(x);
+    }
+}
+
+// forward R-point DFT in registers (R = 2, 4, 8, 16): y_q = sum_r v_r exp(-2 pi i r q / R)
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+    constexpr int M = R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1;
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[bit_reverse<M>(r)] = v[r];
+    dit_levels<R, 2>(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[r];
+}
+
+// one Stockham stage of radix R over the G rows of `a` into `b`
+template <int R>
+__device__ __forceinline__ void stockham_stage(const float2* a, float2* b, const float2* twl, int pitch, int G,
+                                               int log2LR, int Ns, int tshift) {
+    const int LR = 1 << log2LR;
+    for (int task = threadIdx.x; task < LR * G; task += kFThreads) {
+        const int g = task >> log2LR, j = task & (LR - 1);
+        const float2* src = a + g * pitch;
+        float2* dst = b + g * pitch;
+        const int k = j & (Ns - 1);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[pad(j + r * LR)];
+        if (k) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twl[(r * k) << tshift]);
+        }
+        dft_reg<R>(v);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[pad(d + q * Ns)] = v[q];
+    }
+}
+
 // raw packed sample: 2 bytes for complex 8-bit, 1 byte otherwise
 template <int KIND>
 __device__ __forceinline__ uint32_t load_raw(const uint8_t* __restrict__ in, size_t idx) {
@@ -90,13 +180,13 @@ __device__ __forceinline__ float2 unpack_raw(uint32_t r) {
 // Persistent over frames: frame f + gridDim.y's samples are fetched into registers (kPer per
 // thread) while frame f is transformed, so the global loads overlap the FFT.
 template <int KIND>
-__global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
+__global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
                                                             const float2* __restrict__ tw, int N, int log2L, int n_out,
                                                             int log2G, int n_frames) {
     constexpr int kPer = kFPoints / kFThreads;   // samples per thread per frame (at most)
     extern __shared__ float2 fsm[];
     const int L = 1 << log2L, G = 1 << log2G;
-    const int pitch = L + 1;
+    const int pitch = L + (L >> 4) + 1;   // padded row: element i at pad(i)
     float2* const buf0 = fsm;
     float2* const buf1 = fsm + G * pitch;
     float2* const twl = fsm + 2 * G * pitch;
@@ -115,61 +205,37 @@ __global__ void __launch_bounds__(kFThreads) fengine_kernel(const uint8_t* __res
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int idx = threadIdx.x + q * kFThreads;
-            if (idx < pts) a[(idx & (G - 1)) * pitch + (idx >> log2G)] = unpack_raw<KIND>(raw[q]);
+            if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = unpack_raw<KIND>(raw[q]);
         }
         __syncthreads();
         if (f + (int)gridDim.y < n_frames)
             fetch_frame<KIND>(raw, in, (size_t)(f + gridDim.y) * L, N, n0, g_n, log2G, pts);
         for (int Ns = 1, log2Ns = 0; Ns < L;) {
-            const int R = Ns * 4 <= L ? 4 : 2;
-            const int log2LR = log2L - (R == 4 ? 2 : 1);
-            const int LR = 1 << log2LR;
-            const int tshift = log2L - log2Ns - (R == 4 ? 2 : 1);   // twiddle step L / (Ns R)
-            for (int task = threadIdx.x; task < LR * G; task += blockDim.x) {
-                const int g = task >> log2LR, j = task & (LR - 1);
-                const float2* src = a + g * pitch;
-                float2* dst = b + g * pitch;
-                const int k = j & (Ns - 1);
-                const int d = ((j - k) << (R == 4 ? 2 : 1)) + k;
-                if (R == 4) {
-                    float2 v0 = src[j], v1 = src[j + LR], v2 = src[j + 2 * LR], v3 = src[j + 3 * LR];
-                    if (k) {
-                        v1 = cmul(v1, twl[k << tshift]);
-                        v2 = cmul(v2, twl[(2 * k) << tshift]);
-                        v3 = cmul(v3, twl[(3 * k) << tshift]);
-                    }
-                    const float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3);
-                    const float2 e = csub(v1, v3);
-                    const float2 t3 = make_float2(e.y, -e.x);   // (v1 - v3) * (-i)
-                    dst[d] = cadd(t0, t2);
-                    dst[d + Ns] = cadd(t1, t3);
-                    dst[d + 2 * Ns] = csub(t0, t2);
-                    dst[d + 3 * Ns] = csub(t1, t3);
-                } else {
-                    float2 v0 = src[j], v1 = src[j + LR];
-                    if (k) v1 = cmul(v1, twl[k << tshift]);
-                    dst[d] = cadd(v0, v1);
-                    dst[d + Ns] = csub(v0, v1);
-                }
-            }
+            const int log2R = log2L - log2Ns < 4 ? log2L - log2Ns : 4;
+            const int log2LR = log2L - log2R;
+            const int tshift = log2L - log2Ns - log2R;   // twiddle step L / (Ns R)
+            if (log2R == 4) stockham_stage<16>(a, b, twl, pitch, G, log2LR, Ns, tshift);
+            else if (log2R == 3) stockham_stage<8>(a, b, twl, pitch, G, log2LR, Ns, tshift);
+            else if (log2R == 2) stockham_stage<4>(a, b, twl, pitch, G, log2LR, Ns, tshift);
+            else stockham_stage<2>(a, b, twl, pitch, G, log2LR, Ns, tshift);
             __syncthreads();
             float2* t = a;
             a = b;
             b = t;
-            Ns *= R;
-            log2Ns += R == 4 ? 2 : 1;
+            Ns <<= log2R;
+            log2Ns += log2R;
         }
         // channel c of input n0 + g -> out[f][c][n0 + g]
         float2* o = out + (size_t)f * n_out * N + n0;
         for (int idx = threadIdx.x; idx < n_out * G; idx += blockDim.x) {
             const int c = idx >> log2G, g = idx & (G - 1);
-            if (g < g_n) o[(size_t)c * N + g] = a[g * pitch + c];
+            if (g < g_n) o[(size_t)c * N + g] = a[g * pitch + pad(c)];
         }
         __syncthreads();   // the next frame reuses the buffers
     }
 }
 
-size_t fplan_smem(const FPlan& p) { return ((size_t)2 * p.G * (p.L + 1) + p.L) * sizeof(float2); }
+size_t fplan_smem(const FPlan& p) { return ((size_t)2 * p.G * (p.L + (p.L >> 4) + 1) + p.L) * sizeof(float2); }
 
 template <int KIND>
 cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
