@@ -230,6 +230,28 @@ corr_status corr_fplan_info(corr_fplan plan, int *n_out_chan, int *transform_len
 corr_status corr_fengine_run(corr_fplan plan, const void *d_time, int n_frames, void *d_spectra, void *stream);
 
 /*
+ * Dump step (Fig. 1) with post-correlation phase correction (Sec. 2) for one dump of `plan`:
+ * the accumulators are read, divided by the number of updates, rotated to remove the phase
+ * that per-input delays add, and optionally reset:
+ *     V'_ij(c) = V_ij(c) / n_accum * exp(+2 pi i nu_c (tau_i - tau_j))
+ * (a delay tau_i multiplies input i's spectrum by exp(-2 pi i nu tau_i); the paper applies the
+ * MWA's geometric delay correction this way, after correlation).
+ *   d_acc       accumulators [n_chan][P][2] of this plan (device): int64 for 4/8-bit plans,
+ *               float32 for float plans; 16-byte aligned
+ *   n_accum     update count >= 1 (the output is divided by it)
+ *   d_delays    double [n_inputs], seconds (device), or NULL: no rotation, averaging only
+ *   d_freqs     double [n_chan], channel sky frequencies in Hz (device); needed with d_delays
+ *   d_workspace corr_dump_workspace_size bytes (device; per-input phasors), needed with d_delays
+ *   d_out       float32 [n_chan][P][2] averaged, corrected visibilities (device, 8-byte aligned)
+ *   reset       1: zero d_acc in the same pass, ready for the next interval
+ * Phasors are formed in double precision and rounded to float; the rotation and the division
+ * are float32 (relative error a few times 2^-24).  Asynchronous on `stream`.
+ */
+corr_status corr_dump_workspace_size(corr_plan plan, size_t *bytes);
+corr_status corr_dump(corr_plan plan, void *d_acc, int n_accum, const double *d_delays, const double *d_freqs,
+                      void *d_workspace, void *d_out, int reset, void *stream);
+
+/*
  * Read and clear the plan's device status block (synchronises with the device).
  * *device_error receives 0, or the code a kernel recorded when one of its bounded
  * waits gave up.  Returns CORR_ETIMEOUT in that case, else CORR_OK / CORR_ECUDA.

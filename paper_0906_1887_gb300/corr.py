@@ -58,6 +58,8 @@ SIGNATURES = {
     "corr_server_destroy": (_c_int, [_vp, ctypes.c_double]),
     "corr_host_alloc": (_c_int, [_P(_vp), _c_sz]),
     "corr_host_free": (_c_int, [_vp]),
+    "corr_dump_workspace_size": (_c_int, [_vp, _P(_c_sz)]),
+    "corr_dump": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _c_int, _vp]),
     "corr_fplan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int]),
     "corr_fplan_destroy": (_c_int, [_vp]),
     "corr_fplan_info": (_c_int, [_vp, _P(_c_int), _P(_c_int), _P(_c_sz), _P(_c_sz)]),
@@ -183,6 +185,18 @@ class Plan:
     @property
     def n_baselines(self) -> int:
         return self.info()[0]
+
+    def dump(self, acc, out, n_accum: int = 1, delays=None, freqs=None, workspace=None, reset: bool = False,
+             stream=None):
+        """Dump step: out = acc / n_accum rotated by exp(+2 pi i nu_c (tau_i - tau_j)); optional reset.
+        delays (float64 [n_inputs], s) and freqs (float64 [n_chan], Hz) are device tensors."""
+        if delays is not None and workspace is None:
+            import torch
+            b = ctypes.c_size_t()
+            check(lib().corr_dump_workspace_size(self._h, ctypes.byref(b)), "corr_dump_workspace_size")
+            workspace = torch.empty(max(1, b.value), dtype=torch.uint8, device=delays.device)
+        check(lib().corr_dump(self._h, _ptr(acc), n_accum, _ptr(delays), _ptr(freqs), _ptr(workspace), _ptr(out),
+                              1 if reset else 0, _stream_handle(stream)), "corr_dump")
 
     def set_tuning(self, op_stages: int = 0):
         """Operand ring depth of the packed-sample tensor-core kernel (results do not depend on it)."""

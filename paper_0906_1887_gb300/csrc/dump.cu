@@ -1,0 +1,135 @@
+// Dump step (Fig. 1) with post-correlation phase correction (Sec. 2).
+//
+// At the end of a dump interval the accumulators are read, divided by the number of times
+// they were updated and reset (Fig. 1).  The MWA corrects the geometric delay after
+// correlation, as a phase (Sec. 2): a delay tau_i multiplies input i's spectrum by
+// exp(-2 pi i nu tau_i), so baseline (i, j) carries exp(-2 pi i nu_c (tau_i - tau_j)), which
+// the correction removes:
+//
+//     V'_ij(c) = V_ij(c) / n_accum * g_i(c) conj(g_j(c)),   g_n(c) = exp(+2 pi i nu_c tau_n)
+//
+// The per-input phasors g_n(c) are formed once per call in double precision (sincospi of
+// 2 nu tau, whose argument reduction keeps large phases accurate) and rounded to float; the
+// per-baseline work is two complex products in float32 -- the kernel is a stream over the
+// accumulators (16 bytes read, 8 written, 16 more written when resetting).
+#include "corr_internal.h"
+
+namespace corr {
+namespace {
+
+constexpr int kDumpThreads = 256;
+
+__global__ void phasor_kernel(const double* __restrict__ tau, const double* __restrict__ nu, int N, int C,
+                              float2* __restrict__ g) {
+    const int64_t total = (int64_t)N * C;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / N), n = (int)(idx - (int64_t)c * N);
+        double s, co;
+        sincospi(2.0 * nu[c] * tau[n], &s, &co);
+        g[idx] = make_float2((float)co, (float)s);
+    }
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {   // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// baseline b -> (i, j): row i starts at off(i) = i N - i (i - 1) / 2; i is the larger root of
+// off(i) <= b, taken in float and corrected exactly
+__device__ __forceinline__ void baseline_ij(int64_t b, int N, int& i, int& j) {
+    const double B = 2.0 * N + 1.0;
+    int r = (int)((B - sqrt(B * B - 8.0 * (double)b)) * 0.5);
+    r = max(0, min(r, N - 1));
+    while (r > 0 && (int64_t)r * N - (int64_t)r * (r - 1) / 2 > b) --r;
+    while (r + 1 < N && (int64_t)(r + 1) * N - (int64_t)(r + 1) * r / 2 <= b) ++r;
+    i = r;
+    j = r + (int)(b - ((int64_t)r * N - (int64_t)r * (r - 1) / 2));
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(kDumpThreads) dump_kernel(AccT* __restrict__ acc, const float2* __restrict__ g,
+                                                            int N, int64_t P, int C, float inv_n,
+                                                            float2* __restrict__ out, int reset) {
+    for (int c = blockIdx.y; c < C; c += gridDim.y) {
+        AccT* a = acc + (size_t)c * P * 2;
+        float2* o = out + (size_t)c * P;
+        const float2* gc = g ? g + (size_t)c * N : nullptr;
+        for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < P; b += (int64_t)gridDim.x * blockDim.x) {
+            AccT re, im;
+            if constexpr (sizeof(AccT) == 8) {
+                const longlong2 v = reinterpret_cast<const longlong2*>(a)[b];
+                re = v.x;
+                im = v.y;
+            } else {
+                const float2 v = reinterpret_cast<const float2*>(a)[b];
+                re = v.x;
+                im = v.y;
+            }
+            float2 w = make_float2((float)re * inv_n, (float)im * inv_n);
+            if (gc) {
+                int i, j;
+                baseline_ij(b, N, i, j);
+                w = cmulf_conj(cmulf(w, gc[i]), gc[j]);
+            }
+            o[b] = w;
+            if (reset) {
+                if constexpr (sizeof(AccT) == 8) reinterpret_cast<longlong2*>(a)[b] = make_longlong2(0, 0);
+                else reinterpret_cast<float2*>(a)[b] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace corr
+
+using namespace corr;
+
+extern "C" {
+
+corr_status corr_dump_workspace_size(corr_plan plan, size_t* bytes) {
+    if (!plan || !bytes) return set_error(CORR_EINVAL, "corr_dump_workspace_size: NULL argument");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    *bytes = (size_t)p->n_chan * p->n_inputs * sizeof(float2);
+    return CORR_OK;
+}
+
+corr_status corr_dump(corr_plan plan, void* d_acc, int n_accum, const double* d_delays, const double* d_freqs,
+                      void* d_workspace, void* d_out, int reset, void* stream) {
+    if (!plan || !d_acc || !d_out) return set_error(CORR_EINVAL, "corr_dump: NULL argument");
+    if (n_accum < 1) return set_error(CORR_EINVAL, "n_accum=%d must be >= 1", n_accum);
+    if (d_delays && (!d_freqs || !d_workspace))
+        return set_error(CORR_EINVAL, "corr_dump: delays need channel frequencies and the phasor workspace");
+    if ((reinterpret_cast<uintptr_t>(d_acc) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 7u))
+        return set_error(CORR_EINVAL, "corr_dump: accumulators must be 16-byte and output 8-byte aligned");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float2* g = nullptr;
+    if (d_delays) {
+        g = static_cast<float2*>(d_workspace);
+        const int64_t total = (int64_t)p->n_inputs * p->n_chan;
+        const int blocks = (int)((total + kDumpThreads - 1) / kDumpThreads < 4096 ? (total + kDumpThreads - 1) / kDumpThreads : 4096);
+        phasor_kernel<<<blocks, kDumpThreads, 0, s>>>(d_delays, d_freqs, p->n_inputs, p->n_chan, g);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "phasor launch");
+    }
+    const int64_t P = p->n_baselines;
+    const int64_t bx = (P + kDumpThreads - 1) / kDumpThreads;
+    const dim3 grid((unsigned)(bx < 1024 ? bx : 1024), (unsigned)(p->n_chan < 65535 ? p->n_chan : 65535));
+    const float inv_n = 1.0f / (float)n_accum;
+    if (p->sample_bits == 32)
+        dump_kernel<float><<<grid, kDumpThreads, 0, s>>>(static_cast<float*>(d_acc), g, p->n_inputs, P, p->n_chan,
+                                                          inv_n, static_cast<float2*>(d_out), reset);
+    else
+        dump_kernel<long long><<<grid, kDumpThreads, 0, s>>>(static_cast<long long*>(d_acc), g, p->n_inputs, P,
+                                                              p->n_chan, inv_n, static_cast<float2*>(d_out), reset);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "dump launch");
+    return CORR_OK;
+}
+
+}  // extern "C"
