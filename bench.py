@@ -387,6 +387,49 @@ def run_fx(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dump(args):
+    """Dump step with phase correction (Fig. 1, Sec. 2) on one dump of the 1024-input array's
+    accumulators: a pure HBM stream (int64 in, float32 out, zeros back when resetting)."""
+    import torch
+
+    from paper_0906_1887_gb300 import corr
+    n, c, t = 1024, 1536, 256
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    plan = corr.Plan(n, c, t, 8)
+    P = plan.n_baselines
+    g = torch.Generator(device=dev)
+    g.manual_seed(6000)
+    acc = torch.randint(-(1 << 30), 1 << 30, (c, P, 2), generator=g, dtype=torch.int64, device=dev)   # 12.9 GB
+    out = torch.empty((c, P, 2), dtype=torch.float32, device=dev)                                    # 6.45 GB
+    tau = torch.randn(n, generator=g, dtype=torch.float64, device=dev) * 1e-6
+    nu = 1.5e8 + 1e4 * torch.arange(c, dtype=torch.float64, device=dev)
+    ws = torch.empty(plan.dump_workspace_size(), dtype=torch.uint8, device=dev)
+    hbm, _, src = _peaks()
+    res = {}
+    for reset in (False, True):
+        for _ in range(args.warmup):
+            plan.dump(acc, out, 4, tau, nu, ws, reset=reset, stream=stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.steps):
+            plan.dump(acc, out, 4, tau, nu, ws, reset=reset, stream=stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[-1]) / args.steps
+        by = c * P * (16 + 8 + (16 if reset else 0))
+        res["reset" if reset else "read_only"] = {"ms": ms, "algorithmic_bytes": by, "achieved": by / (ms / 1e3) / 1e9,
+                                                  "frac": by / (ms / 1e3) / 1e9 / hbm}
+    line = {"metric": "dump step GB/s (average + phase correction)", "value": res["reset"]["achieved"], "unit": "GB/s",
+            "workload": "dump1024: accumulators of one 1024-input x 1536-channel dump (12.9 GB int64) -> "
+                        "float32 corrected visibilities, accumulators reset",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["reset"]["ms"],
+            "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s", "frac": res["reset"]["frac"],
+                         "peak_source": src},
+            "without_reset": res["read_only"], "with_reset": res["reset"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     import torch
 
@@ -478,7 +521,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--dumps", type=int, default=N_DUMPS,
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx"])
+    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx", "dump"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--large-chans", type=int, default=1536,
                     help="channels of the large-array workload (fewer only for profiling captures)")
@@ -488,7 +531,7 @@ def main():
         reference_arm(args)
         return
     if args.workload != "stream":
-        {"large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx}[args.workload](args)
+        {"large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx, "dump": run_dump}[args.workload](args)
         return
 
     import torch

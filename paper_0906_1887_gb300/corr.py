@@ -192,11 +192,14 @@ class Plan:
         delays (float64 [n_inputs], s) and freqs (float64 [n_chan], Hz) are device tensors."""
         if delays is not None and workspace is None:
             import torch
-            b = ctypes.c_size_t()
-            check(lib().corr_dump_workspace_size(self._h, ctypes.byref(b)), "corr_dump_workspace_size")
-            workspace = torch.empty(max(1, b.value), dtype=torch.uint8, device=delays.device)
+            workspace = torch.empty(max(1, self.dump_workspace_size()), dtype=torch.uint8, device=delays.device)
         check(lib().corr_dump(self._h, _ptr(acc), n_accum, _ptr(delays), _ptr(freqs), _ptr(workspace), _ptr(out),
                               1 if reset else 0, _stream_handle(stream)), "corr_dump")
+
+    def dump_workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        check(lib().corr_dump_workspace_size(self._h, ctypes.byref(b)), "corr_dump_workspace_size")
+        return b.value
 
     def set_tuning(self, op_stages: int = 0):
         """Operand ring depth of the packed-sample tensor-core kernel (results do not depend on it)."""

@@ -39,10 +39,12 @@ __device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {   // a * conj
 }
 
 // baseline b -> (i, j): row i starts at off(i) = i N - i (i - 1) / 2; i is the larger root of
-// off(i) <= b, taken in float and corrected exactly
+// off(i) <= b.  The discriminant (2N + 1)^2 - 8b is exact in int64; its float square root
+// (relative error 2^-24) puts the estimate within one row, which the integer steps correct.
+// (No double precision here: this runs once per baseline and FP64 is slow on this GPU.)
 __device__ __forceinline__ void baseline_ij(int64_t b, int N, int& i, int& j) {
-    const double B = 2.0 * N + 1.0;
-    int r = (int)((B - sqrt(B * B - 8.0 * (double)b)) * 0.5);
+    const int64_t B = 2 * (int64_t)N + 1;
+    int r = (int)(((float)B - sqrtf((float)(B * B - 8 * b))) * 0.5f);
     r = max(0, min(r, N - 1));
     while (r > 0 && (int64_t)r * N - (int64_t)r * (r - 1) / 2 > b) --r;
     while (r + 1 < N && (int64_t)(r + 1) * N - (int64_t)(r + 1) * r / 2 <= b) ++r;
