@@ -81,3 +81,37 @@ def xcorr_spectra(X: np.ndarray) -> np.ndarray:
     out[..., 0] = V[:, iu, ju].real
     out[..., 1] = V[:, iu, ju].imag
     return out
+
+
+# ---- polyphase filterbank (Sec. 6.1: a PFB instead of the FFT, the extra cost in the unpack) ----
+#
+# Critically sampled PFB with M taps: output frame f weights the M input frames f .. f+M-1 by a
+# prototype filter h of length M L and transforms the sum,
+#     y_f[s] = sum_m h[m L + s] x[(f + m) L + s],   X_f[k] = sum_s y_f[s] exp(-2 pi i k s / L),
+# so n_in frames give n_in - M + 1 output frames.  The paper names no filter; the default
+# prototype is the windowed sinc h[n] = sinc((n - (M L - 1) / 2) / L) * w[n] with the Hamming
+# window w[n] = 0.54 - 0.46 cos(2 pi n / (M L - 1)) (M = 1: the plain DFT, h = 1).
+
+def default_prototype(n_taps: int, L: int) -> np.ndarray:
+    n = np.arange(n_taps * L, dtype=np.float64)
+    if n_taps == 1:
+        return np.ones(L)
+    x = (n - (n_taps * L - 1) / 2.0) / L
+    w = 0.54 - 0.46 * np.cos(2.0 * np.pi * n / (n_taps * L - 1))
+    return np.sinc(x) * w
+
+
+def pfb(packed: np.ndarray, n_inputs: int, n_chan: int, n_frames_out: int, kind: str, h: np.ndarray) -> np.ndarray:
+    """PFB spectra ``[n_frames_out][n_out_chan][n_inputs]`` (complex128) with prototype h (M L taps)."""
+    L = transform_length(n_chan, kind)
+    M = len(h) // L
+    if M * L != len(h) or M < 1:
+        raise ValueError("prototype length must be a multiple of the transform length")
+    n_in = n_frames_out + M - 1
+    x = unpack_time(packed, n_inputs, n_in * L, kind).reshape(n_in, L, n_inputs)
+    hm = np.asarray(h, np.float64).reshape(M, L)
+    y = np.zeros((n_frames_out, L, n_inputs), np.complex128)
+    for m in range(M):
+        y += hm[m][None, :, None] * x[m:m + n_frames_out]
+    X = np.fft.fft(y, axis=1)
+    return X[:, : n_out_chan(n_chan, kind), :]

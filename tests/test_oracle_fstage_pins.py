@@ -145,3 +145,73 @@ def test_fx_closed_forms():
     V = fstage.xcorr_spectra(fstage.fstage(_time_packed(re, im, "c8"), 2, n_chan, F, "c8"))
     assert np.allclose(V[:, 1], 0, atol=1e-6)                      # baseline (0, 1)
     assert np.isclose(V[L // 4, 0, 0], F * (A * L) ** 2) and np.isclose(V[L // 2, 2, 0], F * (A * L) ** 2)
+
+
+# ---- polyphase filterbank ----
+
+def test_pfb_matches_definition_double_sum():
+    rng = np.random.default_rng(21)
+    n_chan, N, M, F = 8, 2, 3, 2
+    L = n_chan
+    h = rng.normal(size=M * L)
+    re = rng.integers(-128, 128, ((F + M - 1) * L, N)); im = rng.integers(-128, 128, ((F + M - 1) * L, N))
+    X = fstage.pfb(_time_packed(re, im, "c8"), N, n_chan, F, "c8", h)
+    for f in range(F):
+        for n in range(N):
+            y = [sum(h[m * L + s] * complex(int(re[(f + m) * L + s, n]), int(im[(f + m) * L + s, n]))
+                     for m in range(M)) for s in range(L)]
+            assert np.allclose(X[f, :, n], _dft_brute(y), atol=1e-8 * 128 * L * M)
+
+
+@pytest.mark.parametrize("kind", fstage.KINDS)
+def test_pfb_with_one_unit_tap_is_the_plain_transform(kind):
+    rng = np.random.default_rng(22)
+    n_chan, N, F = 16, 3, 4
+    L = fstage.transform_length(n_chan, kind)
+    lo, hi = (-8, 7) if kind == "c4" else (-128, 127)
+    re = rng.integers(lo, hi + 1, (F * L, N)); im = rng.integers(lo, hi + 1, (F * L, N))
+    p = _time_packed(re, im, kind)
+    assert np.allclose(fstage.pfb(p, N, n_chan, F, kind, fstage.default_prototype(1, L)),
+                       fstage.fstage(p, N, n_chan, F, kind), atol=1e-9)
+
+
+def test_pfb_frame_shift_and_linearity():
+    rng = np.random.default_rng(23)
+    n_chan, N, M, F = 16, 2, 4, 5
+    L = n_chan
+    re = rng.integers(-128, 128, ((F + M) * L, N)); im = rng.integers(-128, 128, ((F + M) * L, N))
+    p = _time_packed(re, im, "c8")
+    h1 = rng.normal(size=M * L); h2 = rng.normal(size=M * L)
+    X = fstage.pfb(p, N, n_chan, F + 1, "c8", h1)
+    Xs = fstage.pfb(_time_packed(re[L:], im[L:], "c8"), N, n_chan, F, "c8", h1)
+    assert np.allclose(X[1:], Xs, atol=1e-8)                     # one frame later in, one frame later out
+    lin = fstage.pfb(p, N, n_chan, F, "c8", 2 * h1 - 3 * h2)
+    assert np.allclose(lin, 2 * fstage.pfb(p, N, n_chan, F, "c8", h1) - 3 * fstage.pfb(p, N, n_chan, F, "c8", h2),
+                       atol=1e-6)
+
+
+def test_pfb_prototype_shape():
+    L, M = 64, 8
+    h = fstage.default_prototype(M, L)
+    assert h.shape == (M * L,)
+    assert np.allclose(h, h[::-1])                                # symmetric
+    assert np.argmax(h) in ((M * L - 1) // 2, M * L // 2)          # peak at the centre
+    # zeros of the sinc at whole multiples of L from the centre (window aside)
+    c = (M * L - 1) / 2.0
+    assert abs(np.sinc((0 - c) / L)) < 1.0 and np.isclose(np.sinc(L / L), 0)
+
+
+def test_pfb_confines_an_off_centre_tone():
+    # a tone a third of a channel off a bin centre: the plain FFT leaks into many channels,
+    # the 8-tap PFB keeps almost all the power within its two neighbouring channels
+    n_chan, F, M = 64, 16, 8
+    L = n_chan
+    s = np.arange((F + M - 1) * L)
+    tone = 100 * np.exp(2j * np.pi * (10 + 1 / 3) * s / L)
+    re = np.round(tone.real).astype(int)[:, None]; im = np.round(tone.imag).astype(int)[:, None]
+    p = _time_packed(re, im, "c8")
+    power_pfb = (np.abs(fstage.pfb(p, 1, n_chan, F, "c8", fstage.default_prototype(M, L))[:, :, 0]) ** 2).sum(0)
+    power_fft = (np.abs(fstage.fstage(p, 1, n_chan, F, "c8")[:, :, 0]) ** 2).sum(0)
+    far = np.r_[0:8, 13:64]
+    assert power_pfb[far].sum() / power_pfb.sum() < 1e-3
+    assert power_fft[far].sum() / power_fft.sum() > 1e-2
