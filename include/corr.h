@@ -230,6 +230,22 @@ corr_status corr_fplan_info(corr_fplan plan, int *n_out_chan, int *transform_len
 corr_status corr_fengine_run(corr_fplan plan, const void *d_time, int n_frames, void *d_spectra, void *stream);
 
 /*
+ * Polyphase filterbank in place of the plain transform (Sec. 6.1: less spectral leakage, the
+ * extra cost in the unpack): output frame f weights the n_taps input frames f .. f+M-1 by a
+ * prototype filter h of M L taps and transforms the sum,
+ *     y_f[s] = sum_m h[m L + s] x[(f + m) L + s],   X_f[k] = sum_s y_f[s] exp(-2 pi i k s / L).
+ * h_taps: host array of n_taps x L floats (L = the transform length), copied into the plan; or
+ * NULL for the default prototype, the windowed sinc sinc((n - (M L - 1) / 2) / L) times the
+ * Hamming window 0.54 - 0.46 cos(2 pi n / (M L - 1)) (computed in double, rounded to float;
+ * n_taps = 1 with NULL is the plain transform).  n_taps in [1, 64].  For such a plan
+ * corr_fengine_run's d_time must hold n_frames + n_taps - 1 frames of L samples; n_frames
+ * spectra are produced.  Destroy with corr_fplan_destroy.
+ */
+corr_status corr_fplan_create_pfb(corr_fplan *out, int n_inputs, int n_chan, int kind, int n_taps, const float *h_taps);
+/* Taps of an F-stage plan (1 for a plain-transform plan). */
+corr_status corr_fplan_taps(corr_fplan plan, int *n_taps);
+
+/*
  * Dump step (Fig. 1) with post-correlation phase correction (Sec. 2) for one dump of `plan`:
  * the accumulators are read, divided by the number of updates, rotated to remove the phase
  * that per-input delays add, and optionally reset:

@@ -64,6 +64,8 @@ SIGNATURES = {
     "corr_fplan_destroy": (_c_int, [_vp]),
     "corr_fplan_info": (_c_int, [_vp, _P(_c_int), _P(_c_int), _P(_c_sz), _P(_c_sz)]),
     "corr_fengine_run": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
+    "corr_fplan_create_pfb": (_c_int, [_P(_vp), _c_int, _c_int, _c_int, _c_int, _vp]),
+    "corr_fplan_taps": (_c_int, [_vp, _P(_c_int)]),
     "corr_average_host": (_c_int, [_vp, _c_sz, _c_i64, _vp]),
 }
 
@@ -120,15 +122,26 @@ def _stream_handle(stream):
 class FPlan:
     """F-stage plan: n_inputs, n_chan channels, sample kind (F_COMPLEX8 / F_COMPLEX4 / F_REAL8)."""
 
-    def __init__(self, n_inputs: int, n_chan: int, kind: int):
+    def __init__(self, n_inputs: int, n_chan: int, kind: int, n_taps: int = 0, taps=None):
+        """n_taps > 0: polyphase filterbank with that many taps; taps = numpy float32 prototype of
+        n_taps x transform_len values, or None for the default windowed sinc."""
         h = ctypes.c_void_p()
-        check(lib().corr_fplan_create(ctypes.byref(h), n_inputs, n_chan, kind), "corr_fplan_create")
+        if n_taps > 0:
+            import numpy as np
+            tp = None if taps is None else np.ascontiguousarray(taps, dtype=np.float32)
+            check(lib().corr_fplan_create_pfb(ctypes.byref(h), n_inputs, n_chan, kind, n_taps,
+                                              None if tp is None else tp.ctypes.data), "corr_fplan_create_pfb")
+        else:
+            check(lib().corr_fplan_create(ctypes.byref(h), n_inputs, n_chan, kind), "corr_fplan_create")
         self._h = h
         self.n_inputs, self.n_chan, self.kind = n_inputs, n_chan, kind
         oc, tl, ib, ob = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_size_t()
         check(lib().corr_fplan_info(h, ctypes.byref(oc), ctypes.byref(tl), ctypes.byref(ib), ctypes.byref(ob)),
               "corr_fplan_info")
         self.n_out_chan, self.transform_len = oc.value, tl.value
+        nt = ctypes.c_int()
+        check(lib().corr_fplan_taps(h, ctypes.byref(nt)), "corr_fplan_taps")
+        self.n_taps = nt.value
         self.in_bytes_per_frame, self.out_bytes_per_frame = ib.value, ob.value
 
     def run(self, time_samples, spectra, n_frames: int, stream=None):

@@ -49,6 +49,8 @@ struct FPlan {
     int device = 0;
     int n_sm = 0;
     float2* d_tw = nullptr;   // exp(-2 pi i k / L), k < L
+    int n_taps = 1;           // PFB taps M (input frames per output frame)
+    float* d_taps = nullptr;  // PFB prototype, M L values; nullptr: plain transform
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -178,11 +180,15 @@ __device__ __forceinline__ float2 unpack_raw(uint32_t r) {
 }
 
 // Persistent over frames: frame f + gridDim.y's samples are fetched into registers (kPer per
-// thread) while frame f is transformed, so the global loads overlap the FFT.
-template <int KIND>
+// thread) while frame f is transformed, so the global loads overlap the FFT.  PFB = true is
+// the polyphase filterbank (Sec. 6.1): the load phase forms y[s] = sum_m h[m L + s] x[(f + m)
+// L + s] over M input frames (the extra cost the paper places in the unpack), then the same
+// transform runs.
+template <int KIND, bool PFB>
 __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
                                                             const float2* __restrict__ tw, int N, int log2L, int n_out,
-                                                            int log2G, int n_frames) {
+                                                            int log2G, int n_frames, const float* __restrict__ taps,
+                                                            int M) {
     constexpr int kPer = kFPoints / kFThreads;   // samples per thread per frame (at most)
     extern __shared__ float2 fsm[];
     const int L = 1 << log2L, G = 1 << log2G;
@@ -197,19 +203,48 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
 
     uint32_t raw[kPer];
     int f = blockIdx.y;
-    if (f < n_frames) fetch_frame<KIND>(raw, in, (size_t)f * L, N, n0, g_n, log2G, pts);
+    if constexpr (!PFB) {
+        if (f < n_frames) fetch_frame<KIND>(raw, in, (size_t)f * L, N, n0, g_n, log2G, pts);
+    }
     for (; f < n_frames; f += gridDim.y) {
         float2* a = buf0;
         float2* b = buf1;
-        // sample s of input n0 + g, time f L + s -> a[g][s]
+        if constexpr (PFB) {
+            // weighted overlap of input frames f .. f + M - 1 -> a[g][s]; each frame's loads are
+            // issued together before its taps are applied
+            float2 acc[kPer];
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int idx = threadIdx.x + q * kFThreads;
-            if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = unpack_raw<KIND>(raw[q]);
+            for (int q = 0; q < kPer; ++q) acc[q] = make_float2(0.f, 0.f);
+            for (int m = 0; m < M; ++m) {
+                fetch_frame<KIND>(raw, in, (size_t)(f + m) * L, N, n0, g_n, log2G, pts);
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int idx = threadIdx.x + q * kFThreads;
+                    if (idx < pts) {
+                        const float hw = taps[m * L + (idx >> log2G)];
+                        const float2 v = unpack_raw<KIND>(raw[q]);
+                        acc[q].x = fmaf(hw, v.x, acc[q].x);
+                        acc[q].y = fmaf(hw, v.y, acc[q].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int idx = threadIdx.x + q * kFThreads;
+                if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = acc[q];
+            }
+            __syncthreads();
+        } else {
+            // sample s of input n0 + g, time f L + s -> a[g][s]
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int idx = threadIdx.x + q * kFThreads;
+                if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = unpack_raw<KIND>(raw[q]);
+            }
+            __syncthreads();
+            if (f + (int)gridDim.y < n_frames)
+                fetch_frame<KIND>(raw, in, (size_t)(f + gridDim.y) * L, N, n0, g_n, log2G, pts);
         }
-        __syncthreads();
-        if (f + (int)gridDim.y < n_frames)
-            fetch_frame<KIND>(raw, in, (size_t)(f + gridDim.y) * L, N, n0, g_n, log2G, pts);
         for (int Ns = 1, log2Ns = 0; Ns < L;) {
             const int log2R = log2L - log2Ns < 4 ? log2L - log2Ns : 4;
             const int log2LR = log2L - log2R;
@@ -237,22 +272,23 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
 
 size_t fplan_smem(const FPlan& p) { return ((size_t)2 * p.G * (p.L + (p.L >> 4) + 1) + p.L) * sizeof(float2); }
 
-template <int KIND>
+template <int KIND, bool PFB>
 cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
     const int smem = (int)fplan_smem(p);
-    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<KIND, PFB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // persistent over frames: enough CTAs to fill every SM a few times over
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fengine_kernel<KIND>, kFThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fengine_kernel<KIND, PFB>, kFThreads, smem);
     if (e != cudaSuccess) return e;
     const int groups = (p.n_inputs + p.G - 1) / p.G;
     int rows = (p.n_sm * (per_sm > 0 ? per_sm : 1) * 4 + groups - 1) / groups;
     if (rows > n_frames) rows = n_frames;
     if (rows > 65535) rows = 65535;
     const dim3 grid(groups, rows);
-    fengine_kernel<KIND><<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in), static_cast<float2*>(d_out),
-                                                       p.d_tw, p.n_inputs, p.log2L, p.n_out, p.log2G, n_frames);
+    fengine_kernel<KIND, PFB><<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in),
+                                                            static_cast<float2*>(d_out), p.d_tw, p.n_inputs, p.log2L,
+                                                            p.n_out, p.log2G, n_frames, p.d_taps, p.n_taps);
     return cudaGetLastError();
 }
 
@@ -306,7 +342,48 @@ corr_status corr_fplan_destroy(corr_fplan plan) {
     if (!plan) return CORR_OK;
     FPlan* p = reinterpret_cast<FPlan*>(plan);
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_taps) cudaFree(p->d_taps);
     delete p;
+    return CORR_OK;
+}
+
+corr_status corr_fplan_create_pfb(corr_fplan* out, int n_inputs, int n_chan, int kind, int n_taps, const float* h_taps) {
+    if (!out) return set_error(CORR_EINVAL, "corr_fplan_create_pfb: out is NULL");
+    *out = nullptr;
+    if (n_taps < 1 || n_taps > 64) return set_error(CORR_EINVAL, "n_taps=%d outside [1, 64]", n_taps);
+    corr_fplan h = nullptr;
+    corr_status st = corr_fplan_create(&h, n_inputs, n_chan, kind);
+    if (st != CORR_OK) return st;
+    FPlan* p = reinterpret_cast<FPlan*>(h);
+    const int ML = n_taps * p->L;
+    std::vector<float> taps(ML);
+    if (h_taps) {
+        for (int n = 0; n < ML; ++n) taps[n] = h_taps[n];
+    } else if (n_taps == 1) {
+        for (int n = 0; n < ML; ++n) taps[n] = 1.0f;
+    } else {
+        // windowed sinc: sinc((n - (M L - 1) / 2) / L) x Hamming(n), in double, rounded to float
+        for (int n = 0; n < ML; ++n) {
+            const double x = ((double)n - (ML - 1) / 2.0) / (double)p->L;
+            const double sinc = x == 0.0 ? 1.0 : sin(M_PI * x) / (M_PI * x);
+            const double w = 0.54 - 0.46 * cos(2.0 * M_PI * (double)n / (double)(ML - 1));
+            taps[n] = (float)(sinc * w);
+        }
+    }
+    cudaError_t e = cudaMalloc(&p->d_taps, (size_t)ML * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_taps, taps.data(), (size_t)ML * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        corr_fplan_destroy(h);
+        return cuda_error(e, "corr_fplan_create_pfb");
+    }
+    p->n_taps = n_taps;
+    *out = h;
+    return CORR_OK;
+}
+
+corr_status corr_fplan_taps(corr_fplan plan, int* n_taps) {
+    if (!plan || !n_taps) return set_error(CORR_EINVAL, "corr_fplan_taps: NULL argument");
+    *n_taps = reinterpret_cast<const FPlan*>(plan)->n_taps;
     return CORR_OK;
 }
 
@@ -330,9 +407,16 @@ corr_status corr_fengine_run(corr_fplan plan, const void* d_time, int n_frames, 
         return set_error(CORR_EINVAL, "corr_fengine_run: samples must be 2-byte and spectra 8-byte aligned");
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (p->kind == CORR_F_COMPLEX8) e = launch_fengine<CORR_F_COMPLEX8>(*p, d_time, n_frames, d_spectra, s);
-    else if (p->kind == CORR_F_COMPLEX4) e = launch_fengine<CORR_F_COMPLEX4>(*p, d_time, n_frames, d_spectra, s);
-    else e = launch_fengine<CORR_F_REAL8>(*p, d_time, n_frames, d_spectra, s);
+    const bool pfb = p->d_taps != nullptr;
+    if (p->kind == CORR_F_COMPLEX8)
+        e = pfb ? launch_fengine<CORR_F_COMPLEX8, true>(*p, d_time, n_frames, d_spectra, s)
+                : launch_fengine<CORR_F_COMPLEX8, false>(*p, d_time, n_frames, d_spectra, s);
+    else if (p->kind == CORR_F_COMPLEX4)
+        e = pfb ? launch_fengine<CORR_F_COMPLEX4, true>(*p, d_time, n_frames, d_spectra, s)
+                : launch_fengine<CORR_F_COMPLEX4, false>(*p, d_time, n_frames, d_spectra, s);
+    else
+        e = pfb ? launch_fengine<CORR_F_REAL8, true>(*p, d_time, n_frames, d_spectra, s)
+                : launch_fengine<CORR_F_REAL8, false>(*p, d_time, n_frames, d_spectra, s);
     if (e != cudaSuccess) return cuda_error(e, "F-stage launch");
     return CORR_OK;
 }

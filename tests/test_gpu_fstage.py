@@ -145,3 +145,48 @@ def test_fplan_rejects_bad_sizes():
         corr.FPlan(4, 4096, 2)       # real: 8192-point transform
     with pytest.raises(corr.CorrError):
         corr.FPlan(4, 64, 3)         # unknown kind
+
+
+# ---- polyphase filterbank (Sec. 6.1) ----
+
+def _run_pfb(packed, n_inputs, n_chan, n_frames, kind, n_taps, taps):
+    from paper_0906_1887_gb300 import corr
+    fp = corr.FPlan(n_inputs, n_chan, KIND_ID[kind], n_taps=n_taps, taps=taps)
+    assert fp.n_taps == n_taps
+    x = torch.from_numpy(np.ascontiguousarray(packed).view(np.uint8).reshape(-1).copy()).cuda()
+    spec = fp.empty_spectra(n_frames)
+    spec.fill_(float("nan"))
+    fp.run(x, spec, n_frames)
+    torch.cuda.synchronize()
+    out = spec.cpu().numpy()
+    fp.close()
+    return out[..., 0].astype(np.float64) + 1j * out[..., 1]
+
+
+@pytest.mark.parametrize("kind,n_chan,n_inputs,n_frames,n_taps", [
+    ("c8", 128, 64, 6, 8), ("c8", 64, 70, 3, 4), ("c4", 32, 17, 5, 2), ("r8", 64, 9, 4, 8), ("c8", 1024, 3, 2, 4),
+])
+@pytest.mark.parametrize("custom", [False, True])
+def test_pfb_matches_oracle(kind, n_chan, n_inputs, n_frames, n_taps, custom):
+    L = fstage.transform_length(n_chan, kind)
+    p = _time_samples(700 + n_chan, (n_frames + n_taps - 1) * L, n_inputs, kind)
+    if custom:
+        taps = np.random.default_rng(n_chan).normal(size=n_taps * L).astype(np.float32)
+    else:
+        taps = None
+    got = _run_pfb(p, n_inputs, n_chan, n_frames, kind, n_taps, taps)
+    h = fstage.default_prototype(n_taps, L) if taps is None else taps.astype(np.float64)
+    ref = fstage.pfb(p, n_inputs, n_chan, n_frames, kind, h)
+    bound = (4 * math.log2(L) + 4 * n_taps) * EPS
+    for f in range(n_frames):
+        for n in range(n_inputs):
+            r = ref[f, :, n]
+            assert np.linalg.norm(got[f, :, n] - r) <= bound * np.linalg.norm(r) + 1e-30, (f, n)
+
+
+def test_pfb_one_tap_equals_plain_transform():
+    n_chan, N, F = 128, 16, 4
+    p = _time_samples(77, F * n_chan, N, "c8")
+    a = _run_pfb(p, N, n_chan, F, "c8", 1, None)
+    b = _run_f(p, N, n_chan, F, "c8")
+    assert np.array_equal(a, b)
