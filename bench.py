@@ -363,6 +363,15 @@ def run_fx(args):
         res[name] = timed(step, args.steps)
         del ws
     f_ms = timed(lambda: fplan.run(x, spec, frames, stream=stream), args.steps)
+    # the polyphase filterbank variant (8 taps, default prototype) on the same second of data
+    taps = 8
+    pplan = corr.FPlan(n, c, corr.F_COMPLEX8, n_taps=taps)
+    xp = synth.torch_correlated_gaussian_packed8(1, (frames + taps - 1) * c, 1, n, 16.0, 0.1, 5001, dev).reshape(-1)
+    pfb_run = lambda: pplan.run(xp, spec, frames, stream=stream)   # noqa: E731
+    for _ in range(args.warmup):
+        pfb_run()
+    pfb_ms = timed(pfb_run, args.steps)
+    pfb_bytes = (frames + taps - 1) * pplan.in_bytes_per_frame + frames * pplan.out_bytes_per_frame
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
@@ -382,6 +391,9 @@ def run_fx(args):
             "fstage": {"kernel": "fengine_kernel<complex8>", "ms": f_ms, "bound": "hbm", "achieved": gbs,
                        "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": f_bytes,
                        "peak_source": src},
+            "pfb_fstage": {"taps": taps, "ms": pfb_ms, "achieved": pfb_bytes / (pfb_ms / 1e3) / 1e9,
+                           "frac": pfb_bytes / (pfb_ms / 1e3) / 1e9 / hbm, "algorithmic_bytes": pfb_bytes,
+                           "note": "each input frame is read by 8 output frames (through L2); bytes counted once"},
             "paper_context": "C1060 (Table 3): unpack 53 + FFT 53 + CMAC (GP, G=4) 185 = 291 ms per second of data",
             "l2": "256 MB flush written between timed steps", "clocks": clk}
     print(json.dumps(line), flush=True)
