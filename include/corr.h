@@ -264,6 +264,18 @@ corr_status corr_fplan_taps(corr_fplan plan, int *n_taps);
  * are float32 (relative error a few times 2^-24).  Asynchronous on `stream`.
  */
 corr_status corr_dump_workspace_size(corr_plan plan, size_t *bytes);
+
+/*
+ * The X stage and the dump step of one or more dumps in one pass (the dump step fused into
+ * the tensor-core kernel's epilogue): d_out[d] = V_d / n_accum rotated as corr_dump does,
+ * float32 [n_dumps][n_chan][P][2], never the int64 sums.  Arguments as corr_xengine_run_batch
+ * and corr_dump (phasor workspace of corr_dump_workspace_size bytes when delays are given).
+ * CORR_EUNSUPPORTED unless the plan takes the packed-sample tensor-core path (4/8-bit samples,
+ * packed rows a multiple of 16 bytes) and a dump fits one exact chunk (n_time <= 1024 for
+ * 8-bit, <= 131072 for 4-bit).  Asynchronous on `stream`.
+ */
+corr_status corr_xengine_run_dump(corr_plan plan, const void *d_packed, int n_dumps, void *d_out, int n_accum,
+                                  const double *d_delays, const double *d_freqs, void *d_workspace, void *stream);
 corr_status corr_dump(corr_plan plan, void *d_acc, int n_accum, const double *d_delays, const double *d_freqs,
                       void *d_workspace, void *d_out, int reset, void *stream);
 

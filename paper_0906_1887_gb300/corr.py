@@ -60,6 +60,7 @@ SIGNATURES = {
     "corr_host_free": (_c_int, [_vp]),
     "corr_dump_workspace_size": (_c_int, [_vp, _P(_c_sz)]),
     "corr_dump": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _c_int, _vp]),
+    "corr_xengine_run_dump": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _vp, _vp, _vp, _vp]),
     "corr_fplan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int]),
     "corr_fplan_destroy": (_c_int, [_vp]),
     "corr_fplan_info": (_c_int, [_vp, _P(_c_int), _P(_c_int), _P(_c_sz), _P(_c_sz)]),
@@ -208,6 +209,16 @@ class Plan:
             workspace = torch.empty(max(1, self.dump_workspace_size()), dtype=torch.uint8, device=delays.device)
         check(lib().corr_dump(self._h, _ptr(acc), n_accum, _ptr(delays), _ptr(freqs), _ptr(workspace), _ptr(out),
                               1 if reset else 0, _stream_handle(stream)), "corr_dump")
+
+    def run_dump(self, packed, out, n_accum: int = 1, delays=None, freqs=None, workspace=None, n_dumps: int = 1,
+                 stream=None):
+        """X stage + dump step fused: out float32 [n_dumps][C][P][2] = V / n_accum, phase-corrected."""
+        if delays is not None and workspace is None:
+            import torch
+            workspace = torch.empty(max(1, self.dump_workspace_size()), dtype=torch.uint8, device=delays.device)
+        check(lib().corr_xengine_run_dump(self._h, _ptr(packed), n_dumps, _ptr(out), n_accum, _ptr(delays),
+                                          _ptr(freqs), _ptr(workspace), _stream_handle(stream)),
+              "corr_xengine_run_dump")
 
     def dump_workspace_size(self) -> int:
         b = ctypes.c_size_t()

@@ -78,6 +78,9 @@ struct TcJobSpec {
     const void* data;   // packed samples [n_dumps][T][C][N] (device)
     void* vis;          // [n_dumps][C][P][2] int64 (device)
     int cpi;            // channels per work item: 1, or 2 for arrays of at most 64 inputs
+    int out_mode = 0;   // 1: dump mode, float32 [n_dumps][C][P][2] of V / n_accum * phasor_i conj(phasor_j)
+    const void* phasor = nullptr;   // float2 [C][N] (device) or nullptr
+    float inv_n = 1.0f;
 };
 // Launch-shape knobs the autotuner chooses (0 = default).
 struct TcTuning {
@@ -86,6 +89,12 @@ struct TcTuning {
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };
 int tc_default_cpi(int n_inputs);
+// Fused dump mode: float32 [n_dumps][C][P][2] = V / n_accum * phasor_i conj(phasor_j) (phasor
+// float2 [C][N] or nullptr); every dump must fit one exact chunk.
+cudaError_t launch_xeng_tc_raw_dump(const Plan& p, const void* d_packed, int n_dumps, void* d_out, const void* phasor,
+                                    float inv_n, cudaStream_t s);
+// Per-input phasors exp(+2 pi i nu_c tau_n) as float2 [C][N], formed in double precision.
+cudaError_t launch_phasors(const Plan& p, const double* d_delays, const double* d_freqs, void* d_g, cudaStream_t s);
 bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp);
 // All jobs of one launch share a sample mode (4 or 8 bits) and must be TMA-addressable.
 cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,

@@ -87,6 +87,15 @@ __global__ void __launch_bounds__(kDumpThreads) dump_kernel(AccT* __restrict__ a
 }
 
 }  // namespace
+
+cudaError_t launch_phasors(const Plan& p, const double* d_delays, const double* d_freqs, void* d_g, cudaStream_t s) {
+    const int64_t total = (int64_t)p.n_inputs * p.n_chan;
+    const int64_t want = (total + kDumpThreads - 1) / kDumpThreads;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    phasor_kernel<<<blocks, kDumpThreads, 0, s>>>(d_delays, d_freqs, p.n_inputs, p.n_chan, static_cast<float2*>(d_g));
+    return cudaGetLastError();
+}
+
 }  // namespace corr
 
 using namespace corr;
@@ -113,10 +122,7 @@ corr_status corr_dump(corr_plan plan, void* d_acc, int n_accum, const double* d_
     float2* g = nullptr;
     if (d_delays) {
         g = static_cast<float2*>(d_workspace);
-        const int64_t total = (int64_t)p->n_inputs * p->n_chan;
-        const int blocks = (int)((total + kDumpThreads - 1) / kDumpThreads < 4096 ? (total + kDumpThreads - 1) / kDumpThreads : 4096);
-        phasor_kernel<<<blocks, kDumpThreads, 0, s>>>(d_delays, d_freqs, p->n_inputs, p->n_chan, g);
-        const cudaError_t e = cudaGetLastError();
+        const cudaError_t e = launch_phasors(*p, d_delays, d_freqs, g, s);
         if (e != cudaSuccess) return cuda_error(e, "phasor launch");
     }
     const int64_t P = p->n_baselines;
@@ -131,6 +137,34 @@ corr_status corr_dump(corr_plan plan, void* d_acc, int n_accum, const double* d_
                                                               p->n_chan, inv_n, static_cast<float2*>(d_out), reset);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "dump launch");
+    return CORR_OK;
+}
+
+corr_status corr_xengine_run_dump(corr_plan plan, const void* d_packed, int n_dumps, void* d_out, int n_accum,
+                                  const double* d_delays, const double* d_freqs, void* d_workspace, void* stream) {
+    if (!plan || !d_packed || !d_out) return set_error(CORR_EINVAL, "corr_xengine_run_dump: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    if (n_accum < 1) return set_error(CORR_EINVAL, "n_accum=%d must be >= 1", n_accum);
+    if (d_delays && (!d_freqs || !d_workspace))
+        return set_error(CORR_EINVAL, "corr_xengine_run_dump: delays need channel frequencies and the phasor workspace");
+    if (reinterpret_cast<uintptr_t>(d_out) & 7u) return set_error(CORR_EINVAL, "corr_xengine_run_dump: output not 8-byte aligned");
+    const Plan* p = reinterpret_cast<const Plan*>(plan);
+    if (!tc_raw_supported(*p))
+        return set_error(CORR_EUNSUPPORTED, "the fused dump runs the packed-sample tensor-core path (4/8-bit samples, "
+                                            "packed rows a multiple of 16 bytes)");
+    const int64_t chunk = p->sample_bits == 8 ? 1024 : 131072;
+    if (p->kp > chunk)
+        return set_error(CORR_EUNSUPPORTED, "the fused dump needs a dump of at most %lld samples (one exact chunk)",
+                         (long long)chunk);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const void* g = nullptr;
+    if (d_delays) {
+        const cudaError_t e = launch_phasors(*p, d_delays, d_freqs, d_workspace, s);
+        if (e != cudaSuccess) return cuda_error(e, "phasor launch");
+        g = d_workspace;
+    }
+    const cudaError_t e = launch_xeng_tc_raw_dump(*p, d_packed, n_dumps, d_out, g, 1.0f / (float)n_accum, s);
+    if (e != cudaSuccess) return cuda_error(e, "fused dump launch");
     return CORR_OK;
 }
 

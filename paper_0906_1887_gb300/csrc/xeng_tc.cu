@@ -67,6 +67,10 @@ constexpr int kSmemBudget = 227 * 1024 - kBarBytes - 1024;  // ring space after 
 // that the 16-byte stores of a quarter-warp fall in 8 distinct bank groups.
 constexpr int kStageRowBytes = 65 * 16;
 constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
+// Dump mode stages 8-byte float pairs: rows of 66 slots (16-byte aligned pitch), element j of a
+// row at slot (j - J0) + s, with s the parity of the row's first global element index, so a
+// slot and its destination are 16-byte aligned together and the bulk copies stay aligned.
+constexpr int kStageRowBytesF = 66 * 8;
 
 enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
 
@@ -106,6 +110,12 @@ struct TcJob {
     // 1: every D element of a chunk is at most 2^23 in magnitude, so rr + ii and ir - ri are
     // exact in fp32 and each needs one conversion (4-bit samples; 8-bit with <= 512 samples)
     int f32_combine;
+    // 1: dump mode (Fig. 1, Sec. 2) -- the epilogue writes float32 V / n_accum rotated by
+    // phasor_i conj(phasor_j) (phasor [n_chan][n_inputs] or nullptr: no rotation) instead of
+    // the exact int64 sums; a dump must fit one exact chunk and is never accumulated
+    int out_mode;
+    const float2* phasor;
+    float inv_n;
 };
 
 template <int MAXJ>
@@ -199,6 +209,16 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 __device__ __forceinline__ void st_shared_v2_u64(uint32_t addr, uint64_t a, uint64_t b) {
     asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v2_f32(uint32_t addr, float a, float b) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ float2 ld_shared_v2_f32(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
@@ -339,7 +359,9 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-template <int MODE, int MAXJ>
+// DUMP: the epilogue writes the dump-mode float pairs (out_mode = 1 jobs) instead of int64
+// sums; a separate instantiation so the exact-output kernels keep their registers.
+template <int MODE, int MAXJ, bool DUMP>
 __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const __grid_constant__ TcLaunch<MAXJ> prm) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
@@ -606,6 +628,26 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     if (lane < 16) bulk_wait_read();
                     __syncwarp();
                 }
+                // dump mode: this channel's phasors -- gi for the lane's row, and the J block's
+                // 64 in shared memory after the warp's staging rows (staged launches)
+                const float2* gch = nullptr;
+                float2 gi = make_float2(1.f, 0.f);
+                uint32_t phs = 0;
+                if constexpr (DUMP) {
+                    if (jb.phasor && (it.c0 + ch) < jb.n_chan) {   // warp-uniform: every lane stages
+                        gch = jb.phasor + (size_t)(it.c0 + ch) * n_in;
+                        if (row_ok) gi = gch[i];
+                        if (prm.staged) {
+                            phs = staging_q + 16u * (uint32_t)kStageRowBytesF;
+                            for (int u = lane; u < kBlockInputs; u += 32) {
+                                const int j = J * kBlockInputs + u;
+                                const float2 g = j < n_in ? gch[j] : make_float2(1.f, 0.f);
+                                st_shared_v2_f32(phs + 8u * (uint32_t)u, g.x, g.y);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
 #pragma unroll 1
                 for (int m = 0; m < 4; ++m) {
                     uint32_t v[32];
@@ -625,7 +667,42 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         own1[k] = odd ? v[2 * k + 17] : v[2 * k + 1];
                     }
                     const int j0 = J * kBlockInputs + 16 * m + (odd ? 8 : 0);
-                    if constexpr (kIntOut) {
+                    if constexpr (kIntOut && DUMP) {
+                        // dump mode: rr + ii and ir - ri in fp32 (each term exact, the sum rounded
+                        // once), scaled by 1 / n_accum and rotated by phasor_i conj(phasor_j)
+                        float2 wv[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int j = j0 + k;
+                            const float rr = __uint_as_float(odd ? oth0[k] : own0[k]);
+                            const float ri = __uint_as_float(odd ? oth1[k] : own1[k]);
+                            const float ir = __uint_as_float(odd ? own0[k] : oth0[k]);
+                            const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
+                            float2 w = make_float2((rr + ii) * jb.inv_n, (ir - ri) * jb.inv_n);
+                            if (gch && j < n_in) {
+                                const float2 gj = prm.staged ? ld_shared_v2_f32(phs + 8u * (uint32_t)(j - J * kBlockInputs))
+                                                             : gch[j];
+                                const float2 t = make_float2(w.x * gi.x - w.y * gi.y, w.x * gi.y + w.y * gi.x);
+                                w = make_float2(t.x * gj.x + t.y * gj.y, t.y * gj.x - t.x * gj.y);
+                            }
+                            wv[k] = w;
+                        }
+                        if (prm.staged) {
+                            // slot (j - J0) + s of row lane/2, s = parity of the row's element J0
+                            const int s_r = (int)((chan_base + row_off + J * kBlockInputs) & 1);
+                            const uint32_t rowp = staging_q + (uint32_t)(lane >> 1) * kStageRowBytesF +
+                                                  (uint32_t)(j0 - J * kBlockInputs + s_r) * 8u;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) st_shared_v2_f32(rowp + 8u * (uint32_t)k, wv[k].x, wv[k].y);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int j = j0 + k;
+                                if (!ch_ok || j < i || j >= n_in) continue;
+                                reinterpret_cast<float2*>(jb.vis)[row_base + j] = wv[k];
+                            }
+                        }
+                    } else if constexpr (kIntOut) {
                         // (rr, ri) from the real-part row, (ir, ii) from the imaginary-part row;
                         // every D element is an integer of magnitude <= 2^24: exact in int32
                         long long re[8], imv[8];
@@ -698,7 +775,39 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         }
                     }
                 }
-                if (kIntOut && prm.staged) {
+                if (DUMP && prm.staged) {
+                    // lane r (< 16) writes row r's float pairs [max(J0, i_r), min(J0 + 64, N)):
+                    // an unaligned first element by a plain store, the 16-byte-aligned body by a
+                    // bulk copy, an odd last element by a plain store
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane < 16) {
+                        const int ir_ = I * kBlockInputs + 16 * q + lane;
+                        const int j_lo = max(J * kBlockInputs, ir_);
+                        const int j_hi = min(J * kBlockInputs + kBlockInputs, n_in);
+                        if (ir_ < n_in && j_lo < j_hi && (it.c0 + ch) < jb.n_chan) {
+                            const int64_t rstart = chan_base + (int64_t)ir_ * n_in - (int64_t)ir_ * (ir_ - 1) / 2 - ir_;
+                            const int s_r = (int)((rstart + J * kBlockInputs) & 1);
+                            const uint32_t row_src = staging_q + (uint32_t)lane * kStageRowBytesF;
+                            float2* vis2 = reinterpret_cast<float2*>(jb.vis);
+                            int j = j_lo;
+                            if ((rstart + j) & 1) {
+                                vis2[rstart + j] =
+                                    ld_shared_v2_f32(row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u);
+                                ++j;
+                            }
+                            const int body = (j_hi - j) & ~1;
+                            if (body > 0)
+                                bulk_store(vis2 + rstart + j, row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u,
+                                           (uint32_t)body * 8u);
+                            j += body;
+                            if (j < j_hi)
+                                vis2[rstart + j] =
+                                    ld_shared_v2_f32(row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u);
+                        }
+                        bulk_commit();
+                    }
+                } else if (kIntOut && prm.staged) {
                     // make the staged rows visible to the bulk-copy engine, then lane r (< 16)
                     // copies row r's valid run of baselines [max(J0, i_r), min(J0 + 64, N))
                     fence_async_shared();
@@ -908,6 +1017,13 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock) : (sp.sample_bits == 4 ? 2048 : 16);
         // |D| <= chunk samples x max |x_a x_b|: 4-bit 2^17 x 2^6 = 2^23, 8-bit 512 x 2^14 = 2^23
         jb.f32_combine = !C::kSplit && (sp.sample_bits == 4 || jb.kp <= 512) ? 1 : 0;
+        jb.out_mode = sp.out_mode;
+        jb.phasor = static_cast<const float2*>(sp.phasor);
+        jb.inv_n = sp.inv_n;
+        if (jb.out_mode && (accumulate || jb.kp > jb.chunk_kb * kTimeBlock)) {   // one exact chunk per dump
+            delete prm;
+            return cudaErrorInvalidValue;
+        }
         jb.item_begin = items;
         const int64_t job_items = (int64_t)sp.n_dumps * jb.n_groups * jb.n_tiles;
         if (job_items >= (int64_t{1} << 31)) {   // decode_item divides 32-bit item indices
@@ -925,8 +1041,11 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->n_items = items;
     prm->tmem_cols = any_pair ? 512u : 256u;
     // shared-memory carve-up; multi-block arrays (output-heavy tiles) stage their epilogue rows
-    bool any_multi = false;
-    for (int j = 0; j < n_jobs; ++j) any_multi = any_multi || prm->jobs[j].nb > 1;
+    bool any_multi = false, any_dump = false;
+    for (int j = 0; j < n_jobs; ++j) {
+        any_multi = any_multi || prm->jobs[j].nb > 1;
+        any_dump = any_dump || prm->jobs[j].out_mode != 0;
+    }
     prm->staged = (!C::kSplit && any_multi) ? 1 : 0;
     const int stage_space = prm->staged ? kStageBytes : 0;
     const int operand_bytes = C::kTilesPerOperand * kTileBytes;
@@ -960,11 +1079,17 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->staging_offset = prm->raw_offset + prm->raw_stages * prm->raw_stage_bytes;
     prm->bar_offset = prm->staging_offset + stage_space;
     const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
-    cudaError_t e =
-        cudaFuncSetAttribute(xeng_tc_kernel<MODE, MAXJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    auto kern = xeng_tc_kernel<MODE, MAXJ, false>;
+    if constexpr (C::kRaw && MAXJ == 1) {
+        if (any_dump) kern = xeng_tc_kernel<MODE, MAXJ, true>;
+    } else if (any_dump) {   // dump mode is built for single-job packed-sample launches only
+        delete prm;
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e == cudaSuccess && items > 0) {
         const int grid = (int)(items < n_sm ? items : n_sm);
-        xeng_tc_kernel<MODE, MAXJ><<<grid, C::kThreads, smem_bytes, s>>>(*prm);
+        kern<<<grid, C::kThreads, smem_bytes, s>>>(*prm);
         e = cudaGetLastError();
     }
     delete prm;
@@ -1023,8 +1148,9 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
     return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
 }
 
-cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
-                               cudaStream_t s, const TcTuning* tune) {
+namespace {
+cudaError_t launch_raw_impl(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                            cudaStream_t s, const TcTuning* tune, int out_mode, const void* phasor, float inv_n) {
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
     TcTuning plan_tune;
     plan_tune.op_stages = p.tc_op_stages;
@@ -1034,12 +1160,15 @@ cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps,
     const int64_t max_dumps = ((int64_t{1} << 31) - 1) / items_per_dump;
     if (max_dumps < 1) return cudaErrorInvalidValue;
     const size_t packed_dump = (size_t)p.n_time * p.n_chan * p.n_inputs * (p.sample_bits == 8 ? 2 : 1);
-    const size_t vis_dump = (size_t)p.n_chan * (size_t)p.n_baselines * 16;
+    const size_t vis_dump = (size_t)p.n_chan * (size_t)p.n_baselines * (out_mode ? 8 : 16);
     for (int d0 = 0; d0 < n_dumps;) {
         const int nd = (int)((n_dumps - d0) < max_dumps ? (n_dumps - d0) : max_dumps);
         TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, nd, p.sample_bits,
                      static_cast<const uint8_t*>(d_packed) + (size_t)d0 * packed_dump,
                      static_cast<uint8_t*>(d_vis) + (size_t)d0 * vis_dump, cpi};
+        sp.out_mode = out_mode;
+        sp.phasor = phasor;
+        sp.inv_n = inv_n;
         CUtensorMap m;
         if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
         const cudaError_t e =
@@ -1048,6 +1177,17 @@ cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps,
         d0 += nd;
     }
     return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                               cudaStream_t s, const TcTuning* tune) {
+    return launch_raw_impl(p, d_packed, n_dumps, d_vis, accumulate, s, tune, 0, nullptr, 1.0f);
+}
+
+cudaError_t launch_xeng_tc_raw_dump(const Plan& p, const void* d_packed, int n_dumps, void* d_out, const void* phasor,
+                                    float inv_n, cudaStream_t s) {
+    return launch_raw_impl(p, d_packed, n_dumps, d_out, 0, s, nullptr, 1, phasor, inv_n);
 }
 
 }  // namespace corr

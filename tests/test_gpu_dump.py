@@ -104,3 +104,47 @@ def test_dump_rejects_bad_arguments():
     with pytest.raises(corr.CorrError):
         plan.dump(acc, out, 1, delays=tau, freqs=None)
     plan.close()
+
+
+# ---- the dump step fused into the tensor-core kernel's epilogue ----
+
+@pytest.mark.parametrize("n,c,t,bits,n_dumps,n_accum,delays", [
+    (64, 5, 1000, 8, 1, 1, True), (64, 4, 1024, 8, 2, 3, False), (136, 3, 200, 8, 1, 1, True),
+    (16, 4, 300, 4, 3, 2, True), (192, 2, 256, 8, 2, 1, True), (8, 3, 64, 8, 1, 5, False),
+])
+def test_fused_dump_matches_oracle(n, c, t, bits, n_dumps, n_accum, delays):
+    from paper_0906_1887_gb300 import corr
+    rng = np.random.default_rng(n * 7 + t)
+    dumps = [int_case(900 + n + k, n, c, t, bits) for k in range(n_dumps)]
+    plan = corr.Plan(n, c, t, bits)
+    x = torch.from_numpy(np.concatenate(dumps).view(np.uint8).reshape(-1).copy()).cuda()
+    out = torch.full((n_dumps, c, plan.n_baselines, 2), float("nan"), dtype=torch.float32, device="cuda")
+    tau = rng.normal(0, 2e-6, n) if delays else np.zeros(n)
+    nu = 1.5e8 + 1e4 * np.arange(c)
+    if delays:
+        plan.run_dump(x, out, n_accum, torch.from_numpy(tau).cuda(), torch.from_numpy(nu).cuda(), n_dumps=n_dumps)
+    else:
+        plan.run_dump(x, out, n_accum, n_dumps=n_dumps)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    got = out.cpu().numpy().astype(np.float64)
+    for k in range(n_dumps):
+        ref = odump.dump_corrected(oracle.xcorr_int(dumps[k], n, c, t, bits), n_accum, tau, nu)
+        _check(got[k], ref)
+    plan.close()
+
+
+def test_fused_dump_refuses_what_it_cannot_do():
+    from paper_0906_1887_gb300 import corr
+    plan = corr.Plan(64, 2, 1025, 8)           # two exact chunks per dump
+    x = torch.zeros(1025 * 2 * 64 * 2, dtype=torch.uint8, device="cuda")
+    out = torch.empty((2, plan.n_baselines, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(corr.CorrError):
+        plan.run_dump(x, out, 1)
+    plan.close()
+    plan = corr.Plan(66, 2, 64, 8)             # packed rows of 132 bytes: not TMA-addressable
+    x = torch.zeros(64 * 2 * 66 * 2, dtype=torch.uint8, device="cuda")
+    out = torch.empty((2, plan.n_baselines, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(corr.CorrError):
+        plan.run_dump(x, out, 1)
+    plan.close()
