@@ -41,7 +41,8 @@ __device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {   // a * conj
 // baseline b -> (i, j): row i starts at off(i) = i N - i (i - 1) / 2; i is the larger root of
 // off(i) <= b.  The discriminant (2N + 1)^2 - 8b is exact in int64; its float square root
 // (relative error 2^-24) puts the estimate within one row, which the integer steps correct.
-// (No double precision here: this runs once per baseline and FP64 is slow on this GPU.)
+// (No double precision here: this runs once per baseline, and sm_103a executes FP64 at a small
+// fraction of its FP32 rate.)
 __device__ __forceinline__ void baseline_ij(int64_t b, int N, int& i, int& j) {
     const int64_t B = 2 * (int64_t)N + 1;
     int r = (int)(((float)B - sqrtf((float)(B * B - 8 * b))) * 0.5f);
