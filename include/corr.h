@@ -237,7 +237,9 @@ corr_status corr_fengine_run(corr_fplan plan, const void *d_time, int n_frames, 
  * h_taps: host array of n_taps x L floats (L = the transform length), copied into the plan; or
  * NULL for the default prototype, the windowed sinc sinc((n - (M L - 1) / 2) / L) times the
  * Hamming window 0.54 - 0.46 cos(2 pi n / (M L - 1)) (computed in double, rounded to float;
- * n_taps = 1 with NULL is the plain transform).  n_taps in [1, 64].  For such a plan
+ * n_taps = 1 with NULL is the plain transform).  n_taps in [1, 64], and the prototype (n_taps
+ * x L floats) must fit in shared memory beside the transform buffers (n_taps x L <= about
+ * 28000; CORR_EINVAL otherwise).  For such a plan
  * corr_fengine_run's d_time must hold n_frames + n_taps - 1 frames of L samples; n_frames
  * spectra are produced.  Destroy with corr_fplan_destroy.
  */

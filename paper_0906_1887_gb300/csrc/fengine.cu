@@ -196,10 +196,13 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
     float2* const buf0 = fsm;
     float2* const buf1 = fsm + G * pitch;
     float2* const twl = fsm + 2 * G * pitch;
+    float* const tapl = reinterpret_cast<float*>(twl + L);   // PFB: the prototype, M L values
     const int n0 = blockIdx.x * G;
     const int g_n = min(G, N - n0);
     const int pts = L * G;
     for (int k = threadIdx.x; k < L; k += blockDim.x) twl[k] = tw[k];
+    if constexpr (PFB)
+        for (int k = threadIdx.x; k < M * L; k += blockDim.x) tapl[k] = taps[k];
 
     uint32_t raw[kPer];
     int f = blockIdx.y;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
                 for (int q = 0; q < kPer; ++q) {
                     const int idx = threadIdx.x + q * kFThreads;
                     if (idx < pts) {
-                        const float hw = taps[m * L + (idx >> log2G)];
+                        const float hw = tapl[m * L + (idx >> log2G)];
                         const float2 v = unpack_raw<KIND>(raw[q]);
                         acc[q].x = fmaf(hw, v.x, acc[q].x);
                         acc[q].y = fmaf(hw, v.y, acc[q].y);
@@ -270,7 +273,10 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
     }
 }
 
-size_t fplan_smem(const FPlan& p) { return ((size_t)2 * p.G * (p.L + (p.L >> 4) + 1) + p.L) * sizeof(float2); }
+size_t fplan_smem(const FPlan& p) {
+    const size_t taps = p.d_taps ? (size_t)p.n_taps * p.L * sizeof(float) : 0;
+    return ((size_t)2 * p.G * (p.L + (p.L >> 4) + 1) + p.L) * sizeof(float2) + taps;
+}
 
 template <int KIND, bool PFB>
 cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
@@ -356,6 +362,13 @@ corr_status corr_fplan_create_pfb(corr_fplan* out, int n_inputs, int n_chan, int
     if (st != CORR_OK) return st;
     FPlan* p = reinterpret_cast<FPlan*>(h);
     const int ML = n_taps * p->L;
+    // the prototype sits in shared memory beside the transform buffers
+    const size_t smem = ((size_t)2 * p->G * (p->L + (p->L >> 4) + 1) + p->L) * sizeof(float2) + (size_t)ML * sizeof(float);
+    if (smem > (size_t)227 * 1024) {
+        corr_fplan_destroy(h);
+        return set_error(CORR_EINVAL, "n_taps=%d x transform length %d: the prototype does not fit in shared memory",
+                         n_taps, p->L);
+    }
     std::vector<float> taps(ML);
     if (h_taps) {
         for (int n = 0; n < ML; ++n) taps[n] = h_taps[n];
