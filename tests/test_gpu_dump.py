@@ -134,6 +134,15 @@ def test_fused_dump_matches_oracle(n, c, t, bits, n_dumps, n_accum, delays):
     plan.close()
 
 
+def test_tuning_rejects_bad_values():
+    from paper_0906_1887_gb300 import corr
+    plan = corr.Plan(64, 2, 64, 8)
+    for bad in (-1, 17):
+        with pytest.raises(corr.CorrError):
+            plan.set_tuning(bad)
+    plan.close()
+
+
 def test_fused_dump_refuses_what_it_cannot_do():
     from paper_0906_1887_gb300 import corr
     plan = corr.Plan(64, 2, 1025, 8)           # two exact chunks per dump
