@@ -6,19 +6,21 @@
 // complex-to-complex transform of which channels 0 .. N_C are kept (Sec. 4).  Here one
 // kernel does both steps for a block of G inputs and one frame of L samples:
 //
-//   load    packed samples [t][input] -> float2 rows in shared memory, one row per input
-//           (coalesced along the inputs; rows padded to L + 1 so column reads do not
-//           collide in banks)
+//   load    packed samples [t][input] -> float2 rows in shared memory, one row per input;
+//           each thread loads 4 adjacent inputs of a sample at once (8 or 4 bytes) and
+//           converts bytes and nibbles to float with the 2^23 exponent trick
 //   FFT     Stockham autosort stages of radix 16 (the last one of radix 8, 4 or 2 when
 //           log2 L is not a multiple of 4), ping-ponging between two shared buffers: each
-//           task loads R values, applies the stage twiddles (a table exp(-2 pi i k / L)
-//           computed on the host in double precision) and does the R-point DFT in registers
-//           (radix-2 butterflies with exact constant twiddles of the 16th roots of unity).
-//           L = 128, the paper's channel count, takes two stages (16 x 8).  Rows are padded
-//           one element per 16 so the strided stores of the first stage, and the column
-//           reads of the load and store phases, fall in distinct banks
+//           task loads R values, applies the stage twiddles (per-stage tables computed on the
+//           host in double precision) and does the R-point DFT in registers (radix-2
+//           butterflies with exact constant twiddles of the 16th roots of unity).  L = 128,
+//           the paper's channel count, takes two stages (16 x 8)
 //   store   spectra [frame][channel][input] complex float32, coalesced along the inputs --
 //           exactly the float sample layout the X stage takes ([T][C][N], T = frames)
+//
+// L is a template parameter (one kernel per power of two from 8 to 4096): every index is then
+// a shift or a compile-time offset from a per-thread base, and the row pitch and task layout
+// of each length keep all shared-memory phases free of bank conflicts.
 //
 // A Stockham stage with sub-transform length Ns and radix R takes, for each j < L / R, the R
 // values v_r = x[j + r L / R], multiplies v_r by exp(-2 pi i (j mod Ns) r / (Ns R)), applies
@@ -27,6 +29,7 @@
 // X_k = sum_s x_s exp(-2 pi i k s / L); channel c is bin c.
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "corr_internal.h"
@@ -38,6 +41,46 @@ constexpr int kFPoints = 4096;   // complex points per CTA (inputs x transform l
 constexpr int kFThreads = 256;
 constexpr int kFMinLen = 8, kFMaxLen = 4096;
 
+// position of row element i: one pad element after every 16.  For a power of two P and
+// j < P, pad(j + r P) = pad(j) + pad(r P): every strided access below is a per-thread base
+// plus compile-time offsets.
+__host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
+
+// Geometry of the transform length L = 2^LG.  G inputs per CTA (G L = 4096 points, at most
+// 64 inputs).  The row pitch (float2 elements, at least pad(L - 1) + 1) is chosen per length so
+// that the load, transform and store phases below all fall in distinct shared-memory banks
+// (each access pattern was modelled bank by bank on the CPU).
+__host__ __device__ constexpr int f_groups(int LG) { return LG >= 6 ? kFPoints >> LG : 64; }
+__host__ __device__ constexpr int f_pitch(int LG) {
+    return LG == 3 ? 9 : LG == 4 ? 17 : LG == 5 ? 35 : LG == 6 ? 69 : LG == 7 ? 137 : LG == 8 ? 273 :
+           LG == 9 ? 546 : LG == 10 ? 1092 : LG == 11 ? 2184 : 4352;
+}
+__host__ __device__ constexpr int f_stages(int LG) { return (LG + 3) / 4; }
+__host__ __device__ constexpr int f_stage_lgr(int LG, int st) { return LG - 4 * st < 4 ? LG - 4 * st : 4; }
+// Stage st (sub-transform length Ns = 16^st, radix R) uses twiddles exp(-2 pi i k r / (Ns R))
+// for k < Ns, 1 <= r < R, stored k-major at entry k (R - 1) + r - 1 of the stage's table;
+// the tables of stages 1, 2, ... follow one another (stage 0 has Ns = 1: no twiddles).
+__host__ __device__ constexpr int f_tw_offset(int LG, int st) {
+    int o = 0;
+    for (int u = 1; u < st; ++u) o += (1 << (4 * u)) * ((1 << f_stage_lgr(LG, u)) - 1);
+    return o;
+}
+__host__ __device__ constexpr int f_tw_entries(int LG) { return f_tw_offset(LG, f_stages(LG)); }
+
+template <int LG>
+struct FGeom {
+    static constexpr int L = 1 << LG;
+    static constexpr int G = f_groups(LG);
+    static constexpr int LGG = LG >= 6 ? 12 - LG : 6;
+    static constexpr int PITCH = f_pitch(LG);
+    static constexpr int PTS = L * G;
+    static constexpr int V = G < 4 ? G : 4;                      // inputs per vector load
+    static constexpr int VPR = G / V;                            // vector loads per sample row
+    static constexpr int NVEC = (PTS / V + kFThreads - 1) / kFThreads;   // per thread per frame
+    static_assert(PITCH >= pad(L - 1) + 1, "row shorter than the padded transform");
+    static_assert((1 << LGG) == G, "inputs per CTA");
+};
+
 struct FPlan {
     int n_inputs = 0;
     int n_chan = 0;
@@ -48,7 +91,7 @@ struct FPlan {
     int log2L = 0, log2G = 0;
     int device = 0;
     int n_sm = 0;
-    float2* d_tw = nullptr;   // exp(-2 pi i k / L), k < L
+    float2* d_tw = nullptr;   // the stage twiddle tables (f_tw_entries(log2L) values, at least one)
     int n_taps = 1;           // PFB taps M (input frames per output frame)
     float* d_taps = nullptr;  // PFB prototype, M L values; nullptr: plain transform
 };
@@ -58,9 +101,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
-// position of row element i: one pad element after every 16
-__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
 // x * exp(-2 pi i a / 16) for a compile-time a in 0..7 (the roots a DFT of size <= 16 uses);
 // the constants are cos and sin of multiples of pi / 8, correctly rounded to float
@@ -120,182 +160,352 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     for (int r = 0; r < R; ++r) v[r] = x[r];
 }
 
-// one Stockham stage of radix R over the G rows of `a` into `b`
-template <int R>
-__device__ __forceinline__ void stockham_stage(const float2* a, float2* b, const float2* twl, int pitch, int G,
-                                               int log2LR, int Ns, int tshift) {
-    const int LR = 1 << log2LR;
-    for (int task = threadIdx.x; task < LR * G; task += kFThreads) {
-        const int g = task >> log2LR, j = task & (LR - 1);
-        const float2* src = a + g * pitch;
-        float2* dst = b + g * pitch;
-        const int k = j & (Ns - 1);
+// Task -> row of a Stockham stage.  When a half-warp spans several rows (L / R < 16), the
+// rows it takes are spread by rotating the low four bits of the row index, which puts their
+// bank windows side by side instead of on top of one another (L = 32, 64, 128).
+template <int LG, int ST>
+__device__ __forceinline__ int stage_row(int gi) {
+    if constexpr (ST == 0 && LG == 5) return ((gi & 7) << 1) | ((gi >> 3) & 1) | (gi & ~15);
+    else if constexpr (ST == 0 && LG == 6) return ((gi & 3) << 2) | ((gi >> 2) & 3) | (gi & ~15);
+    else if constexpr (ST == 0 && LG == 7) return ((gi & 1) << 3) | ((gi >> 1) & 7) | (gi & ~15);
+    else return gi;
+}
+
+// Stockham stage ST over the G rows of `a` into `b`: Ns = 16^ST, radix R, L / R tasks per row
+template <int LG, int ST>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ a, float2* __restrict__ b,
+                                          const float2* __restrict__ tws) {
+    using Geo = FGeom<LG>;
+    constexpr int LGNS = 4 * ST, NS = 1 << LGNS;
+    constexpr int LGR = f_stage_lgr(LG, ST), R = 1 << LGR;
+    constexpr int LGLR = LG - LGR, LR = 1 << LGLR;
+    constexpr int NTASK = LR * Geo::G;
+    constexpr int NIT = (NTASK + kFThreads - 1) / kFThreads;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int task = threadIdx.x + it * kFThreads;
+        if (NTASK % kFThreads != 0 && task >= NTASK) break;
+        const int g = stage_row<LG, ST>(task >> LGLR), j = task & (LR - 1);
+        const float2* src = a + g * Geo::PITCH + pad(j);
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[pad(j + r * LR)];
-        if (k) {
+        for (int r = 0; r < R; ++r) v[r] = src[pad(r * LR)];
+        const int k = j & (NS - 1);
+        if constexpr (ST > 0) {
+            if (k) {
+                const float2* t = tws + f_tw_offset(LG, ST) + k * (R - 1) - 1;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twl[(r * k) << tshift]);
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
+            }
         }
         dft_reg<R>(v);
-        const int d = (j - k) * R + k;
+        float2* dst = b + g * Geo::PITCH + pad((j - k) * R + k);
 #pragma unroll
-        for (int q = 0; q < R; ++q) dst[pad(d + q * Ns)] = v[q];
+        for (int q = 0; q < R; ++q) dst[pad(q * NS)] = v[q];
     }
 }
 
-// raw packed sample: 2 bytes for complex 8-bit, 1 byte otherwise
-template <int KIND>
-__device__ __forceinline__ uint32_t load_raw(const uint8_t* __restrict__ in, size_t idx) {
-    if constexpr (KIND == CORR_F_COMPLEX8) return reinterpret_cast<const unsigned short*>(in)[idx];
-    else return in[idx];
-}
-
-// the samples thread `tid` moves of one frame: element idx = tid + q x threads is sample
-// s = idx >> log2G of input n0 + (idx & (G - 1)); zero outside the array
-template <int KIND, int PER>
-__device__ __forceinline__ void fetch_frame(uint32_t (&raw)[PER], const uint8_t* __restrict__ in, size_t row0, int N,
-                                            int n0, int g_n, int log2G, int pts) {
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int idx = threadIdx.x + q * kFThreads;
-        const int s = idx >> log2G, g = idx & ((1 << log2G) - 1);
-        raw[q] = (idx < pts && g < g_n) ? load_raw<KIND>(in, (row0 + s) * N + n0 + g) : 0u;
-    }
-}
-
-// one packed sample -> complex float (small integers: exact)
-template <int KIND>
-__device__ __forceinline__ float2 unpack_raw(uint32_t r) {
-    if constexpr (KIND == CORR_F_COMPLEX8) {
-        return make_float2((float)(signed char)(r & 0xFF), (float)(signed char)(r >> 8));
-    } else if constexpr (KIND == CORR_F_COMPLEX4) {
-        int re = (int)(r >> 4), im = (int)(r & 15);
-        re -= (re & 8) << 1;   // two's complement nibbles
-        im -= (im & 8) << 1;
-        return make_float2((float)re, (float)im);
+// all stages, ping-ponging between the buffers; returns the one holding the spectrum
+template <int LG, int ST>
+__device__ __forceinline__ float2* fft_stages(float2* a, float2* b, const float2* tws) {
+    if constexpr (ST < f_stages(LG)) {
+        fft_stage<LG, ST>(a, b, tws);
+        __syncthreads();
+        return fft_stages<LG, ST + 1>(b, a, tws);
     } else {
-        return make_float2((float)(signed char)r, 0.f);
+        return a;
     }
 }
 
-// Persistent over frames: frame f + gridDim.y's samples are fetched into registers (kPer per
-// thread) while frame f is transformed, so the global loads overlap the FFT.  PFB = true is
-// the polyphase filterbank (Sec. 6.1): the load phase forms y[s] = sum_m h[m L + s] x[(f + m)
-// L + s] over M input frames (the extra cost the paper places in the unpack), then the same
-// transform runs.
-template <int KIND, bool PFB>
+// bytes per packed sample: 2 for complex 8-bit, 1 otherwise
+template <int KIND>
+__host__ __device__ constexpr int f_bps() { return KIND == CORR_F_COMPLEX8 ? 2 : 1; }
+
+// V consecutive inputs of one sample: 8 bytes (complex 8-bit, V = 4) or at most 4
+template <int KIND, int LG>
+using FRaw = std::conditional_t<KIND == CORR_F_COMPLEX8 && FGeom<LG>::V == 4, uint2, uint32_t>;
+
+// one vector: exactly V x (bytes per sample) bytes, aligned to that size
+template <int KIND, int LG>
+__device__ __forceinline__ FRaw<KIND, LG> load_vec(const uint8_t* src) {
+    constexpr int B = FGeom<LG>::V * f_bps<KIND>();
+    if constexpr (B == 8) return *reinterpret_cast<const uint2*>(src);
+    else if constexpr (B == 4) return *reinterpret_cast<const uint32_t*>(src);
+    else if constexpr (B == 2) return (uint32_t)*reinterpret_cast<const unsigned short*>(src);
+    else return (uint32_t)*src;
+}
+
+// vector load e of a frame -> sample s and first input g.  For rows of 8 or more vectors a warp
+// takes 4 samples x 8 vectors (each half-warp 4 x 4), whose shared-memory rows fall in
+// distinct banks; the global reads stay 32-byte sectors
+template <int LG>
+__device__ __forceinline__ void vec_pos(int e, int& s, int& g) {
+    using Geo = FGeom<LG>;
+    if constexpr (Geo::VPR >= 8) {
+        constexpr int NB = Geo::VPR / 8;
+        const int b = e >> 5, t = e & 31;
+        const int m = (t & 3) | ((t >> 4) << 2);
+        s = (b / NB) * 4 + ((t >> 2) & 3);
+        g = ((b % NB) * 8 + m) * Geo::V;
+    } else {
+        s = e / Geo::VPR;
+        g = (e % Geo::VPR) * Geo::V;
+    }
+}
+
+// the packed samples thread `threadIdx.x` moves of one frame (zeros outside the array).
+// `in_f` points at sample 0 of input n0 of the frame; vec: one aligned load per vector
+template <int KIND, int LG>
+__device__ __forceinline__ void fetch_frame(FRaw<KIND, LG> (&raw)[FGeom<LG>::NVEC], const uint8_t* __restrict__ in_f,
+                                            int N, int g_n, bool vec) {
+    using Geo = FGeom<LG>;
+    using RawT = FRaw<KIND, LG>;
+    constexpr int BPS = f_bps<KIND>();
+#pragma unroll
+    for (int q = 0; q < Geo::NVEC; ++q) {
+        const int e = threadIdx.x + q * kFThreads;
+        RawT r{};
+        if (Geo::NVEC * kFThreads * Geo::V == Geo::PTS || e < Geo::PTS / Geo::V) {
+            int s, g;
+            vec_pos<LG>(e, s, g);
+            const uint8_t* src = in_f + (s * N + g) * BPS;
+            if (vec) {
+                if (g < g_n) r = load_vec<KIND, LG>(src);
+            } else {
+                uint32_t w[2] = {0u, 0u};
+#pragma unroll
+                for (int k = 0; k < Geo::V; ++k) {
+                    if (g + k < g_n) {
+                        const uint32_t x = BPS == 2 ? (uint32_t)*reinterpret_cast<const unsigned short*>(src + 2 * k)
+                                                    : (uint32_t)src[k];
+                        w[(k * BPS) >> 2] |= x << (((k * BPS) & 3) * 8);
+                    }
+                }
+                if constexpr (sizeof(RawT) == 8) r = make_uint2(w[0], w[1]);
+                else r = w[0];
+            }
+        }
+        raw[q] = r;
+    }
+}
+
+// small integers to float by the 2^23 exponent trick: a byte u (or nibble) placed in the low
+// mantissa of 2^23 gives the float 2^23 + u exactly; the sign offset is flipped into u first
+// (u = x + 128 for a signed byte, x + 8 for a signed nibble), then one exact subtraction
+__device__ __forceinline__ float f_byte(uint32_t w, uint32_t sel, float bias) {
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, sel)) - bias;
+}
+constexpr float kBias8 = 8388736.0f;   // 2^23 + 128
+constexpr float kBias4 = 8388616.0f;   // 2^23 + 8
+
+// vector load -> V complex values (inputs g .. g + V - 1)
+template <int KIND, int LG>
+__device__ __forceinline__ void unpack_vec(FRaw<KIND, LG> r, float2 (&x)[FGeom<LG>::V]) {
+    constexpr int V = FGeom<LG>::V;
+    if constexpr (KIND == CORR_F_COMPLEX8) {
+        uint32_t w[2];
+        if constexpr (V == 4) {
+            w[0] = r.x ^ 0x80808080u;
+            w[1] = r.y ^ 0x80808080u;
+        } else {
+            w[0] = r ^ 0x80808080u;
+            w[1] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const uint32_t ww = w[k >> 1];
+            const uint32_t b0 = (uint32_t)(2 * (k & 1));
+            x[k] = make_float2(f_byte(ww, 0x7540u | b0, kBias8), f_byte(ww, 0x7540u | (b0 + 1), kBias8));
+        }
+    } else if constexpr (KIND == CORR_F_COMPLEX4) {
+        const uint32_t w = r ^ 0x88888888u;   // high nibble re, low nibble im
+        const uint32_t hi = (w >> 4) & 0x0F0F0F0Fu, lo = w & 0x0F0F0F0Fu;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            x[k] = make_float2(f_byte(hi, 0x7540u | (uint32_t)k, kBias4), f_byte(lo, 0x7540u | (uint32_t)k, kBias4));
+    } else {
+        const uint32_t w = r ^ 0x80808080u;
+#pragma unroll
+        for (int k = 0; k < V; ++k) x[k] = make_float2(f_byte(w, 0x7540u | (uint32_t)k, kBias8), 0.f);
+    }
+}
+
+// Persistent over frames: frame f + gridDim.y's samples are fetched into registers while frame
+// f is transformed, so the global loads overlap the FFT.  PFB = true is the polyphase
+// filterbank (Sec. 6.1): the load phase forms y[s] = sum_m h[m L + s] x[(f + m) L + s] over M
+// input frames (the extra cost the paper places in the unpack), then the same transform runs.
+template <int KIND, bool PFB, int LG>
 __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out,
-                                                            const float2* __restrict__ tw, int N, int log2L, int n_out,
-                                                            int log2G, int n_frames, const float* __restrict__ taps,
-                                                            int M) {
-    constexpr int kPer = kFPoints / kFThreads;   // samples per thread per frame (at most)
+                                                            const float2* __restrict__ tw, int N, int n_frames,
+                                                            const float* __restrict__ taps, int M, int vec) {
+    using Geo = FGeom<LG>;
+    using RawT = FRaw<KIND, LG>;
+    constexpr int L = Geo::L, G = Geo::G, V = Geo::V, NVEC = Geo::NVEC;
+    constexpr int BPS = f_bps<KIND>();
+    constexpr int TWN = f_tw_entries(LG);
+    constexpr int NOUT = KIND == CORR_F_REAL8 ? L / 2 + 1 : L;
+    constexpr int CSTEP = kFThreads / G;   // channels per pass of the store phase
     extern __shared__ float2 fsm[];
-    const int L = 1 << log2L, G = 1 << log2G;
-    const int pitch = L + (L >> 4) + 1;   // padded row: element i at pad(i)
     float2* const buf0 = fsm;
-    float2* const buf1 = fsm + G * pitch;
-    float2* const twl = fsm + 2 * G * pitch;
-    float* const tapl = reinterpret_cast<float*>(twl + L);   // PFB: the prototype, M L values
+    float2* const buf1 = fsm + G * Geo::PITCH;
+    float2* const tws = fsm + 2 * G * Geo::PITCH;
+    float* const tapl = reinterpret_cast<float*>(tws + TWN);   // PFB: the prototype, M L values
     const int n0 = blockIdx.x * G;
     const int g_n = min(G, N - n0);
-    const int pts = L * G;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) twl[k] = tw[k];
+    for (int k = threadIdx.x; k < TWN; k += kFThreads) tws[k] = tw[k];
     if constexpr (PFB)
-        for (int k = threadIdx.x; k < M * L; k += blockDim.x) tapl[k] = taps[k];
+        for (int k = threadIdx.x; k < M * L; k += kFThreads) tapl[k] = taps[k];
+    __syncthreads();   // the tables are read by other threads (the taps before the first barrier below)
+    const size_t frame_bytes = (size_t)L * N * BPS;
+    const uint8_t* const in_n0 = in + (size_t)n0 * BPS;
 
-    uint32_t raw[kPer];
+    RawT raw[NVEC];
     int f = blockIdx.y;
     if constexpr (!PFB) {
-        if (f < n_frames) fetch_frame<KIND>(raw, in, (size_t)f * L, N, n0, g_n, log2G, pts);
+        if (f < n_frames) fetch_frame<KIND, LG>(raw, in_n0 + (size_t)f * frame_bytes, N, g_n, vec != 0);
     }
     for (; f < n_frames; f += gridDim.y) {
-        float2* a = buf0;
-        float2* b = buf1;
         if constexpr (PFB) {
-            // weighted overlap of input frames f .. f + M - 1 -> a[g][s]; each frame's loads are
-            // issued together before its taps are applied
-            float2 acc[kPer];
+            // weighted overlap of input frames f .. f + M - 1; each frame's loads are issued
+            // together before its taps are applied
+            float2 acc[NVEC][V];
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) acc[q] = make_float2(0.f, 0.f);
+            for (int q = 0; q < NVEC; ++q)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[q][k] = make_float2(0.f, 0.f);
             for (int m = 0; m < M; ++m) {
-                fetch_frame<KIND>(raw, in, (size_t)(f + m) * L, N, n0, g_n, log2G, pts);
+                fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + m) * frame_bytes, N, g_n, vec != 0);
 #pragma unroll
-                for (int q = 0; q < kPer; ++q) {
-                    const int idx = threadIdx.x + q * kFThreads;
-                    if (idx < pts) {
-                        const float hw = tapl[m * L + (idx >> log2G)];
-                        const float2 v = unpack_raw<KIND>(raw[q]);
-                        acc[q].x = fmaf(hw, v.x, acc[q].x);
-                        acc[q].y = fmaf(hw, v.y, acc[q].y);
+                for (int q = 0; q < NVEC; ++q) {
+                    const int e = threadIdx.x + q * kFThreads;
+                    if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
+                        int s, g;
+                        vec_pos<LG>(e, s, g);
+                        const float hw = tapl[m * L + s];
+                        float2 x[V];
+                        unpack_vec<KIND, LG>(raw[q], x);
+#pragma unroll
+                        for (int k = 0; k < V; ++k) {
+                            acc[q][k].x = fmaf(hw, x[k].x, acc[q][k].x);
+                            acc[q][k].y = fmaf(hw, x[k].y, acc[q][k].y);
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int idx = threadIdx.x + q * kFThreads;
-                if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = acc[q];
+            for (int q = 0; q < NVEC; ++q) {
+                const int e = threadIdx.x + q * kFThreads;
+                if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
+                    int s, g;
+                    vec_pos<LG>(e, s, g);
+                    float2* d = buf0 + g * Geo::PITCH + pad(s);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = acc[q][k];
+                }
             }
             __syncthreads();
         } else {
-            // sample s of input n0 + g, time f L + s -> a[g][s]
+            // sample s of input n0 + g + k, time f L + s -> buf0[g + k][s]
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int idx = threadIdx.x + q * kFThreads;
-                if (idx < pts) a[(idx & (G - 1)) * pitch + pad(idx >> log2G)] = unpack_raw<KIND>(raw[q]);
+            for (int q = 0; q < NVEC; ++q) {
+                const int e = threadIdx.x + q * kFThreads;
+                if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
+                    int s, g;
+                    vec_pos<LG>(e, s, g);
+                    float2 x[V];
+                    unpack_vec<KIND, LG>(raw[q], x);
+                    float2* d = buf0 + g * Geo::PITCH + pad(s);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = x[k];
+                }
             }
             __syncthreads();
             if (f + (int)gridDim.y < n_frames)
-                fetch_frame<KIND>(raw, in, (size_t)(f + gridDim.y) * L, N, n0, g_n, log2G, pts);
+                fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + gridDim.y) * frame_bytes, N, g_n, vec != 0);
         }
-        for (int Ns = 1, log2Ns = 0; Ns < L;) {
-            const int log2R = log2L - log2Ns < 4 ? log2L - log2Ns : 4;
-            const int log2LR = log2L - log2R;
-            const int tshift = log2L - log2Ns - log2R;   // twiddle step L / (Ns R)
-            if (log2R == 4) stockham_stage<16>(a, b, twl, pitch, G, log2LR, Ns, tshift);
-            else if (log2R == 3) stockham_stage<8>(a, b, twl, pitch, G, log2LR, Ns, tshift);
-            else if (log2R == 2) stockham_stage<4>(a, b, twl, pitch, G, log2LR, Ns, tshift);
-            else stockham_stage<2>(a, b, twl, pitch, G, log2LR, Ns, tshift);
-            __syncthreads();
-            float2* t = a;
-            a = b;
-            b = t;
-            Ns <<= log2R;
-            log2Ns += log2R;
-        }
-        // channel c of input n0 + g -> out[f][c][n0 + g]
-        float2* o = out + (size_t)f * n_out * N + n0;
-        for (int idx = threadIdx.x; idx < n_out * G; idx += blockDim.x) {
-            const int c = idx >> log2G, g = idx & (G - 1);
-            if (g < g_n) o[(size_t)c * N + g] = a[g * pitch + pad(c)];
+        const float2* spec = fft_stages<LG, 0>(buf0, buf1, tws);
+        // channel c of input n0 + g -> out[f][c][n0 + g]; thread: g = tid mod G, channels
+        // c0 + CSTEP u (pad(c0 + CSTEP u) = pad(c0) + pad(CSTEP u) as c0 < CSTEP)
+        {
+            const int g = threadIdx.x & (G - 1), c0 = threadIdx.x >> Geo::LGG;
+            if (g < g_n) {
+                const float2* srow = spec + g * Geo::PITCH + pad(c0);
+                float2* o = out + (size_t)f * NOUT * N + n0 + (size_t)c0 * N + g;
+                const size_t ostep = (size_t)CSTEP * N;
+#pragma unroll 4
+                for (int u = 0; u < (NOUT + CSTEP - 1) / CSTEP; ++u) {
+                    if (NOUT % CSTEP == 0 || c0 + CSTEP * u < NOUT) o[u * ostep] = srow[pad(CSTEP * u)];
+                }
+            }
         }
         __syncthreads();   // the next frame reuses the buffers
     }
 }
 
-size_t fplan_smem(const FPlan& p) {
-    const size_t taps = p.d_taps ? (size_t)p.n_taps * p.L * sizeof(float) : 0;
-    return ((size_t)2 * p.G * (p.L + (p.L >> 4) + 1) + p.L) * sizeof(float2) + taps;
+size_t fplan_smem(int log2L, int n_taps_pfb) {
+    const size_t G = (size_t)f_groups(log2L);
+    return (2 * G * (size_t)f_pitch(log2L) + (size_t)f_tw_entries(log2L)) * sizeof(float2) +
+           (size_t)n_taps_pfb * ((size_t)1 << log2L) * sizeof(float);
+}
+
+size_t fplan_smem(const FPlan& p) { return fplan_smem(p.log2L, p.d_taps ? p.n_taps : 0); }
+
+template <int KIND, bool PFB, int LG>
+cudaError_t launch_fengine_l(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
+    auto kern = fengine_kernel<KIND, PFB, LG>;
+    const int smem = (int)fplan_smem(p);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    // persistent over frames: enough CTAs to fill every SM a few times over
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFThreads, smem);
+    if (e != cudaSuccess) return e;
+    constexpr int G = FGeom<LG>::G, V = FGeom<LG>::V;
+    const int groups = (p.n_inputs + G - 1) / G;
+    int rows = (p.n_sm * (per_sm > 0 ? per_sm : 1) * 4 + groups - 1) / groups;
+    if (rows > n_frames) rows = n_frames;
+    if (rows > 65535) rows = 65535;
+    // one load per V inputs when every such group starts on a V-sample boundary in memory
+    const int vec = (p.n_inputs % V == 0 && (reinterpret_cast<uintptr_t>(d_in) % (size_t)(V * f_bps<KIND>())) == 0) ? 1 : 0;
+    const dim3 grid(groups, rows);
+    kern<<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in), static_cast<float2*>(d_out), p.d_tw,
+                                       p.n_inputs, n_frames, p.d_taps, p.n_taps, vec);
+    return cudaGetLastError();
 }
 
 template <int KIND, bool PFB>
 cudaError_t launch_fengine(const FPlan& p, const void* d_in, int n_frames, void* d_out, cudaStream_t s) {
-    const int smem = (int)fplan_smem(p);
-    cudaError_t e = cudaFuncSetAttribute(fengine_kernel<KIND, PFB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    // persistent over frames: enough CTAs to fill every SM a few times over
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fengine_kernel<KIND, PFB>, kFThreads, smem);
-    if (e != cudaSuccess) return e;
-    const int groups = (p.n_inputs + p.G - 1) / p.G;
-    int rows = (p.n_sm * (per_sm > 0 ? per_sm : 1) * 4 + groups - 1) / groups;
-    if (rows > n_frames) rows = n_frames;
-    if (rows > 65535) rows = 65535;
-    const dim3 grid(groups, rows);
-    fengine_kernel<KIND, PFB><<<grid, kFThreads, smem, s>>>(static_cast<const uint8_t*>(d_in),
-                                                            static_cast<float2*>(d_out), p.d_tw, p.n_inputs, p.log2L,
-                                                            p.n_out, p.log2G, n_frames, p.d_taps, p.n_taps);
-    return cudaGetLastError();
+    switch (p.log2L) {
+        case 3: return launch_fengine_l<KIND, PFB, 3>(p, d_in, n_frames, d_out, s);
+        case 4: return launch_fengine_l<KIND, PFB, 4>(p, d_in, n_frames, d_out, s);
+        case 5: return launch_fengine_l<KIND, PFB, 5>(p, d_in, n_frames, d_out, s);
+        case 6: return launch_fengine_l<KIND, PFB, 6>(p, d_in, n_frames, d_out, s);
+        case 7: return launch_fengine_l<KIND, PFB, 7>(p, d_in, n_frames, d_out, s);
+        case 8: return launch_fengine_l<KIND, PFB, 8>(p, d_in, n_frames, d_out, s);
+        case 9: return launch_fengine_l<KIND, PFB, 9>(p, d_in, n_frames, d_out, s);
+        case 10: return launch_fengine_l<KIND, PFB, 10>(p, d_in, n_frames, d_out, s);
+        case 11: return launch_fengine_l<KIND, PFB, 11>(p, d_in, n_frames, d_out, s);
+        case 12: return launch_fengine_l<KIND, PFB, 12>(p, d_in, n_frames, d_out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// the stage twiddle tables for L = 2^LG, each entry rounded from double precision
+std::vector<float2> make_twiddles(int LG) {
+    const int L = 1 << LG;
+    std::vector<float2> tw((size_t)(f_tw_entries(LG) > 0 ? f_tw_entries(LG) : 1), make_float2(1.f, 0.f));
+    for (int st = 1; st < f_stages(LG); ++st) {
+        const int Ns = 1 << (4 * st), lgr = f_stage_lgr(LG, st), R = 1 << lgr;
+        const int tshift = LG - 4 * st - lgr;   // exp(-2 pi i k r / (Ns R)) = w_L^((k r) << tshift)
+        for (int k = 0; k < Ns; ++k)
+            for (int r = 1; r < R; ++r) {
+                const int m = (r * k) << tshift;
+                const double ang = -2.0 * M_PI * (double)m / (double)L;
+                tw[(size_t)f_tw_offset(LG, st) + (size_t)k * (R - 1) + (r - 1)] =
+                    make_float2((float)cos(ang), (float)sin(ang));
+            }
+    }
+    return tw;
 }
 
 }  // namespace
@@ -323,18 +533,14 @@ corr_status corr_fplan_create(corr_fplan* out, int n_inputs, int n_chan, int kin
     p->kind = kind;
     p->L = L;
     p->n_out = kind == CORR_F_REAL8 ? n_chan + 1 : n_chan;
-    p->G = kFPoints / L < 64 ? (kFPoints / L > 0 ? kFPoints / L : 1) : 64;
     while ((1 << p->log2L) < L) ++p->log2L;
+    p->G = f_groups(p->log2L);
     while ((1 << p->log2G) < p->G) ++p->log2G;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device);
-    std::vector<float2> tw(L);
-    for (int k = 0; k < L; ++k) {
-        const double ang = -2.0 * M_PI * (double)k / (double)L;
-        tw[k] = make_float2((float)cos(ang), (float)sin(ang));
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, (size_t)L * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), (size_t)L * sizeof(float2), cudaMemcpyHostToDevice);
+    const std::vector<float2> tw = make_twiddles(p->log2L);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, tw.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (p->d_tw) cudaFree(p->d_tw);
         delete p;
@@ -363,8 +569,7 @@ corr_status corr_fplan_create_pfb(corr_fplan* out, int n_inputs, int n_chan, int
     FPlan* p = reinterpret_cast<FPlan*>(h);
     const int ML = n_taps * p->L;
     // the prototype sits in shared memory beside the transform buffers
-    const size_t smem = ((size_t)2 * p->G * (p->L + (p->L >> 4) + 1) + p->L) * sizeof(float2) + (size_t)ML * sizeof(float);
-    if (smem > (size_t)227 * 1024) {
+    if (fplan_smem(p->log2L, n_taps) > (size_t)227 * 1024) {
         corr_fplan_destroy(h);
         return set_error(CORR_EINVAL, "n_taps=%d x transform length %d: the prototype does not fit in shared memory",
                          n_taps, p->L);
