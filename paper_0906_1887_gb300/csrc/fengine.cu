@@ -160,9 +160,10 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
     for (int r = 0; r < R; ++r) v[r] = x[r];
 }
 
-// Task -> row of a Stockham stage.  When a half-warp spans several rows (L / R < 16), the
-// rows it takes are spread by rotating the low four bits of the row index, which puts their
-// bank windows side by side instead of on top of one another (L = 32, 64, 128).
+// Task -> row of a transposed-path stage.  When a half-warp spans several rows (L / R < 16),
+// the rows it takes are spread by rotating the low four bits of the row index, which puts
+// their bank windows side by side instead of on top of one another (first stage of L = 32,
+// 64, 128).
 template <int LG, int ST>
 __device__ __forceinline__ int stage_row(int gi) {
     if constexpr (ST == 0 && LG == 5) return ((gi & 7) << 1) | ((gi >> 3) & 1) | (gi & ~15);
@@ -171,7 +172,8 @@ __device__ __forceinline__ int stage_row(int gi) {
     else return gi;
 }
 
-// Stockham stage ST over the G rows of `a` into `b`: Ns = 16^ST, radix R, L / R tasks per row
+// Stockham stage ST over the G rows of `a` into `b` (Ns = 16^ST, radix R, L / R tasks per
+// row).  The transposed path runs every stage but the last one this way.
 template <int LG, int ST>
 __device__ __forceinline__ void fft_stage(const float2* __restrict__ a, float2* __restrict__ b,
                                           const float2* __restrict__ tws) {
@@ -205,15 +207,55 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ a, float2* 
     }
 }
 
-// all stages, ping-ponging between the buffers; returns the one holding the spectrum
+// stages ST .. (last - 1), ping-ponging between the buffers; returns the one the last stage reads
 template <int LG, int ST>
-__device__ __forceinline__ float2* fft_stages(float2* a, float2* b, const float2* tws) {
-    if constexpr (ST < f_stages(LG)) {
+__device__ __forceinline__ const float2* fft_mid_stages(float2* a, float2* b, const float2* tws) {
+    if constexpr (ST < f_stages(LG) - 1) {
         fft_stage<LG, ST>(a, b, tws);
         __syncthreads();
-        return fft_stages<LG, ST + 1>(b, a, tws);
+        return fft_mid_stages<LG, ST + 1>(b, a, tws);
     } else {
         return a;
+    }
+}
+
+// The last stage stores the spectrum itself: its sub-transform length is Ns = L / R, so task
+// j < Ns yields channels j + q Ns.  Tasks run inputs fastest, so a warp's stores of a channel
+// are contiguous.  out_f points at channel 0 of input n0 of the frame.
+template <int KIND, int LG>
+__device__ __forceinline__ void fft_last_stage(const float2* __restrict__ a, const float2* __restrict__ tws,
+                                               float2* __restrict__ out_f, int N, int g_n) {
+    using Geo = FGeom<LG>;
+    constexpr int ST = f_stages(LG) - 1;
+    constexpr int NS = 1 << (4 * ST);
+    constexpr int LGR = f_stage_lgr(LG, ST), R = 1 << LGR;
+    constexpr int LR = 1 << (LG - LGR);
+    static_assert(LR == NS, "the last stage's tasks are its sub-transform offsets");
+    constexpr int NOUT = KIND == CORR_F_REAL8 ? Geo::L / 2 + 1 : Geo::L;
+    constexpr int NTASK = LR * Geo::G;
+    constexpr int NIT = (NTASK + kFThreads - 1) / kFThreads;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int task = threadIdx.x + it * kFThreads;
+        if (NTASK % kFThreads != 0 && task >= NTASK) break;
+        const int g = task & (Geo::G - 1), j = task >> Geo::LGG;
+        if (g >= g_n) continue;
+        const float2* src = a + g * Geo::PITCH + pad(j);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[pad(r * LR)];
+        if constexpr (ST > 0) {
+            if (j) {
+                const float2* t = tws + f_tw_offset(LG, ST) + j * (R - 1) - 1;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], t[r]);
+            }
+        }
+        dft_reg<R>(v);
+        float2* o = out_f + j * N + g;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (NOUT == Geo::L || j + q * NS < NOUT) o[q * NS * N] = v[q];
     }
 }
 
@@ -330,6 +372,48 @@ __device__ __forceinline__ void unpack_vec(FRaw<KIND, LG> r, float2 (&x)[FGeom<L
     }
 }
 
+// Fused first stage (G >= 16, i.e. L <= 256): thread t takes input g = t mod G and offset
+// j = t / G (< L / R), and loads the R samples j + r L / R of its input straight from global
+// memory -- lanes run along the inputs, so each load of a warp reads whole sample rows of the
+// CTA's inputs -- then does the first radix-R DFT in registers (Ns = 1: no twiddles).  The
+// transposing pass through shared memory disappears.
+template <int LG>
+struct FFirst {
+    static constexpr int R = 1 << f_stage_lgr(LG, 0);
+    static constexpr int LR = FGeom<LG>::L / R;
+    static constexpr int NTASK = LR * FGeom<LG>::G;
+    static_assert(NTASK <= kFThreads, "one first-stage task per thread");
+};
+
+template <int KIND, int LG>
+__device__ __forceinline__ void fetch_task(uint32_t (&raw)[FFirst<LG>::R], const uint8_t* __restrict__ in_f, int N,
+                                           bool active) {
+    using F = FFirst<LG>;
+    constexpr int BPS = f_bps<KIND>();
+    const int g = threadIdx.x & (FGeom<LG>::G - 1), j = threadIdx.x >> FGeom<LG>::LGG;
+    const uint8_t* src = in_f + (j * N + g) * BPS;
+    const int step = F::LR * N * BPS;
+#pragma unroll
+    for (int r = 0; r < F::R; ++r)
+        raw[r] = !active ? 0u
+                         : (BPS == 2 ? (uint32_t)*reinterpret_cast<const unsigned short*>(src + r * step)
+                                     : (uint32_t)src[r * step]);
+}
+
+// one packed sample -> complex float (exact)
+template <int KIND>
+__device__ __forceinline__ float2 unpack1(uint32_t r) {
+    if constexpr (KIND == CORR_F_COMPLEX8) {
+        const uint32_t w = r ^ 0x8080u;
+        return make_float2(f_byte(w, 0x7540u, kBias8), f_byte(w, 0x7541u, kBias8));
+    } else if constexpr (KIND == CORR_F_COMPLEX4) {
+        const uint32_t w = r ^ 0x88u;
+        return make_float2(f_byte((w >> 4) & 15u, 0x7540u, kBias4), f_byte(w & 15u, 0x7540u, kBias4));
+    } else {
+        return make_float2(f_byte(r ^ 0x80u, 0x7540u, kBias8), 0.f);
+    }
+}
+
 // Persistent over frames: frame f + gridDim.y's samples are fetched into registers while frame
 // f is transformed, so the global loads overlap the FFT.  PFB = true is the polyphase
 // filterbank (Sec. 6.1): the load phase forms y[s] = sum_m h[m L + s] x[(f + m) L + s] over M
@@ -339,12 +423,13 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
                                                             const float2* __restrict__ tw, int N, int n_frames,
                                                             const float* __restrict__ taps, int M, int vec) {
     using Geo = FGeom<LG>;
-    using RawT = FRaw<KIND, LG>;
-    constexpr int L = Geo::L, G = Geo::G, V = Geo::V, NVEC = Geo::NVEC;
+    constexpr int L = Geo::L, G = Geo::G;
     constexpr int BPS = f_bps<KIND>();
     constexpr int TWN = f_tw_entries(LG);
     constexpr int NOUT = KIND == CORR_F_REAL8 ? L / 2 + 1 : L;
-    constexpr int CSTEP = kFThreads / G;   // channels per pass of the store phase
+    // first stage straight from global memory for L <= 256; the filterbank keeps the vector
+    // loads (M input frames per output frame: four times fewer load instructions)
+    constexpr bool kFused = G >= 16 && !PFB;
     extern __shared__ float2 fsm[];
     float2* const buf0 = fsm;
     float2* const buf1 = fsm + G * Geo::PITCH;
@@ -359,86 +444,135 @@ __global__ void __launch_bounds__(kFThreads, 3) fengine_kernel(const uint8_t* __
     const size_t frame_bytes = (size_t)L * N * BPS;
     const uint8_t* const in_n0 = in + (size_t)n0 * BPS;
 
-    RawT raw[NVEC];
-    int f = blockIdx.y;
-    if constexpr (!PFB) {
-        if (f < n_frames) fetch_frame<KIND, LG>(raw, in_n0 + (size_t)f * frame_bytes, N, g_n, vec != 0);
-    }
-    for (; f < n_frames; f += gridDim.y) {
-        if constexpr (PFB) {
-            // weighted overlap of input frames f .. f + M - 1; each frame's loads are issued
-            // together before its taps are applied
-            float2 acc[NVEC][V];
+    if constexpr (kFused) {
+        using F = FFirst<LG>;
+        constexpr int R = F::R;
+        const int g = threadIdx.x & (G - 1), j = threadIdx.x >> Geo::LGG;
+        const bool active = (F::NTASK == kFThreads || (int)threadIdx.x < F::NTASK) && g < g_n;
+        uint32_t raw[R];
+        int f = blockIdx.y;
+        if constexpr (!PFB) {
+            if (f < n_frames) fetch_task<KIND, LG>(raw, in_n0 + (size_t)f * frame_bytes, N, active);
+        }
+        int par = 0;
+        for (; f < n_frames; f += gridDim.y) {
+            float2 v[R];
+            if constexpr (PFB) {
+                // weighted overlap of input frames f .. f + M - 1 for samples j + r L / R
 #pragma unroll
-            for (int q = 0; q < NVEC; ++q)
+                for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+                for (int m = 0; m < M; ++m) {
+                    fetch_task<KIND, LG>(raw, in_n0 + (size_t)(f + m) * frame_bytes, N, active);
+                    if (active) {   // a thread without a task has j >= L / R: no taps of its own
+                        const float* hm = tapl + m * L + j;
 #pragma unroll
-                for (int k = 0; k < V; ++k) acc[q][k] = make_float2(0.f, 0.f);
-            for (int m = 0; m < M; ++m) {
-                fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + m) * frame_bytes, N, g_n, vec != 0);
+                        for (int r = 0; r < R; ++r) {
+                            const float hw = hm[r * F::LR];
+                            const float2 x = unpack1<KIND>(raw[r]);
+                            v[r].x = fmaf(hw, x.x, v[r].x);
+                            v[r].y = fmaf(hw, x.y, v[r].y);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = unpack1<KIND>(raw[r]);
+                if (f + (int)gridDim.y < n_frames)
+                    fetch_task<KIND, LG>(raw, in_n0 + (size_t)(f + gridDim.y) * frame_bytes, N, active);
+            }
+            dft_reg<R>(v);
+            float2* const out_f = out + (size_t)f * NOUT * N + n0;
+            if constexpr (f_stages(LG) == 1) {
+                // the whole transform (L = R): channel q of input g
+                if (active) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (q < NOUT) out_f[q * N + g] = v[q];
+                }
+            } else {
+                // first-stage outputs j R + q of row g; the buffers alternate between frames, so
+                // one barrier per frame orders every write against every read
+                float2* const buf = par ? buf1 : buf0;
+                if (active) {
+                    float2* dst = buf + g * Geo::PITCH + pad(j * R);
+#pragma unroll
+                    for (int q = 0; q < R; ++q) dst[pad(q)] = v[q];
+                }
+                __syncthreads();
+                fft_last_stage<KIND, LG>(buf, tws, out_f, N, g_n);
+                par ^= 1;
+            }
+        }
+    } else {
+        // coalesced vector loads transposed into rows, then the stages
+        using RawT = FRaw<KIND, LG>;
+        constexpr int V = Geo::V, NVEC = Geo::NVEC;
+        RawT raw[NVEC];
+        int f = blockIdx.y;
+        if constexpr (!PFB) {
+            if (f < n_frames) fetch_frame<KIND, LG>(raw, in_n0 + (size_t)f * frame_bytes, N, g_n, vec != 0);
+        }
+        for (; f < n_frames; f += gridDim.y) {
+            if constexpr (PFB) {
+                float2 acc[NVEC][V];
+#pragma unroll
+                for (int q = 0; q < NVEC; ++q)
+#pragma unroll
+                    for (int k = 0; k < V; ++k) acc[q][k] = make_float2(0.f, 0.f);
+                for (int m = 0; m < M; ++m) {
+                    fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + m) * frame_bytes, N, g_n, vec != 0);
+#pragma unroll
+                    for (int q = 0; q < NVEC; ++q) {
+                        const int e = threadIdx.x + q * kFThreads;
+                        if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
+                            int s, g;
+                            vec_pos<LG>(e, s, g);
+                            const float hw = tapl[m * L + s];
+                            float2 x[V];
+                            unpack_vec<KIND, LG>(raw[q], x);
+#pragma unroll
+                            for (int k = 0; k < V; ++k) {
+                                acc[q][k].x = fmaf(hw, x[k].x, acc[q][k].x);
+                                acc[q][k].y = fmaf(hw, x[k].y, acc[q][k].y);
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < NVEC; ++q) {
                     const int e = threadIdx.x + q * kFThreads;
                     if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
                         int s, g;
                         vec_pos<LG>(e, s, g);
-                        const float hw = tapl[m * L + s];
-                        float2 x[V];
-                        unpack_vec<KIND, LG>(raw[q], x);
+                        float2* d = buf0 + g * Geo::PITCH + pad(s);
 #pragma unroll
-                        for (int k = 0; k < V; ++k) {
-                            acc[q][k].x = fmaf(hw, x[k].x, acc[q][k].x);
-                            acc[q][k].y = fmaf(hw, x[k].y, acc[q][k].y);
-                        }
+                        for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = acc[q][k];
                     }
                 }
-            }
+                __syncthreads();
+            } else {
+                // sample s of input n0 + g + k, time f L + s -> buf0[g + k][s]
 #pragma unroll
-            for (int q = 0; q < NVEC; ++q) {
-                const int e = threadIdx.x + q * kFThreads;
-                if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
-                    int s, g;
-                    vec_pos<LG>(e, s, g);
-                    float2* d = buf0 + g * Geo::PITCH + pad(s);
+                for (int q = 0; q < NVEC; ++q) {
+                    const int e = threadIdx.x + q * kFThreads;
+                    if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
+                        int s, g;
+                        vec_pos<LG>(e, s, g);
+                        float2 x[V];
+                        unpack_vec<KIND, LG>(raw[q], x);
+                        float2* d = buf0 + g * Geo::PITCH + pad(s);
 #pragma unroll
-                    for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = acc[q][k];
+                        for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = x[k];
+                    }
                 }
+                __syncthreads();
+                if (f + (int)gridDim.y < n_frames)
+                    fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + gridDim.y) * frame_bytes, N, g_n, vec != 0);
             }
-            __syncthreads();
-        } else {
-            // sample s of input n0 + g + k, time f L + s -> buf0[g + k][s]
-#pragma unroll
-            for (int q = 0; q < NVEC; ++q) {
-                const int e = threadIdx.x + q * kFThreads;
-                if (NVEC * kFThreads * V == Geo::PTS || e < Geo::PTS / V) {
-                    int s, g;
-                    vec_pos<LG>(e, s, g);
-                    float2 x[V];
-                    unpack_vec<KIND, LG>(raw[q], x);
-                    float2* d = buf0 + g * Geo::PITCH + pad(s);
-#pragma unroll
-                    for (int k = 0; k < V; ++k) d[k * Geo::PITCH] = x[k];
-                }
-            }
-            __syncthreads();
-            if (f + (int)gridDim.y < n_frames)
-                fetch_frame<KIND, LG>(raw, in_n0 + (size_t)(f + gridDim.y) * frame_bytes, N, g_n, vec != 0);
+            const float2* last = fft_mid_stages<LG, 0>(buf0, buf1, tws);
+            fft_last_stage<KIND, LG>(last, tws, out + (size_t)f * NOUT * N + n0, N, g_n);
+            __syncthreads();   // the next frame rewrites the buffers
         }
-        const float2* spec = fft_stages<LG, 0>(buf0, buf1, tws);
-        // channel c of input n0 + g -> out[f][c][n0 + g]; thread: g = tid mod G, channels
-        // c0 + CSTEP u (pad(c0 + CSTEP u) = pad(c0) + pad(CSTEP u) as c0 < CSTEP)
-        {
-            const int g = threadIdx.x & (G - 1), c0 = threadIdx.x >> Geo::LGG;
-            if (g < g_n) {
-                const float2* srow = spec + g * Geo::PITCH + pad(c0);
-                float2* o = out + (size_t)f * NOUT * N + n0 + (size_t)c0 * N + g;
-                const size_t ostep = (size_t)CSTEP * N;
-#pragma unroll 4
-                for (int u = 0; u < (NOUT + CSTEP - 1) / CSTEP; ++u) {
-                    if (NOUT % CSTEP == 0 || c0 + CSTEP * u < NOUT) o[u * ostep] = srow[pad(CSTEP * u)];
-                }
-            }
-        }
-        __syncthreads();   // the next frame reuses the buffers
     }
 }
 
