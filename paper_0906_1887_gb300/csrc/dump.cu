@@ -12,6 +12,9 @@
 // 2 nu tau, whose argument reduction keeps large phases accurate) and rounded to float; the
 // per-baseline work is two complex products in float32 -- the kernel is a stream over the
 // accumulators (16 bytes read, 8 written, 16 more written when resetting).
+#include <algorithm>
+#include <type_traits>
+
 #include "corr_internal.h"
 
 namespace corr {
@@ -38,50 +41,54 @@ __device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {   // a * conj
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// baseline b -> (i, j): row i starts at off(i) = i N - i (i - 1) / 2; i is the larger root of
-// off(i) <= b.  The discriminant (2N + 1)^2 - 8b is exact in int64; its float square root
-// (relative error 2^-24) puts the estimate within one row, which the integer steps correct.
-// (No double precision here: this runs once per baseline, and sm_103a executes FP64 at a small
-// fraction of its FP32 rate.)
-__device__ __forceinline__ void baseline_ij(int64_t b, int N, int& i, int& j) {
-    const int64_t B = 2 * (int64_t)N + 1;
-    int r = (int)(((float)B - sqrtf((float)(B * B - 8 * b))) * 0.5f);
-    r = max(0, min(r, N - 1));
-    while (r > 0 && (int64_t)r * N - (int64_t)r * (r - 1) / 2 > b) --r;
-    while (r + 1 < N && (int64_t)(r + 1) * N - (int64_t)(r + 1) * r / 2 <= b) ++r;
-    i = r;
-    j = r + (int)(b - ((int64_t)r * N - (int64_t)r * (r - 1) / 2));
-}
+// Each block takes the baseline rows i and N - 1 - i of a channel (i < N / 2, or the middle
+// row alone when N is odd): N - i + i + 1 = N + 1 elements for every block, so the blocks are
+// equal, and an element's (i, j) follows from its position in the pair without any search.
+// Row i starts at off(i) = i N - i (i - 1) / 2 within the channel.  Each thread issues kU
+// loads before it computes, to keep enough bytes in flight; blocks loop over channels.
+constexpr int kU = 4;
 
 template <typename AccT>
 __global__ void __launch_bounds__(kDumpThreads) dump_kernel(AccT* __restrict__ acc, const float2* __restrict__ g,
                                                             int N, int64_t P, int C, float inv_n,
                                                             float2* __restrict__ out, int reset) {
+    using Pair = std::conditional_t<sizeof(AccT) == 8, longlong2, float2>;
+    const int i0 = blockIdx.x, i1 = N - 1 - i0;
+    const int len0 = N - i0;                        // elements of row i0
+    const int len = i1 == i0 ? len0 : N + 1;        // elements of the pair
+    const int64_t off0 = (int64_t)i0 * N - (int64_t)i0 * (i0 - 1) / 2;
+    const int64_t off1 = (int64_t)i1 * N - (int64_t)i1 * (i1 - 1) / 2;
     for (int c = blockIdx.y; c < C; c += gridDim.y) {
-        AccT* a = acc + (size_t)c * P * 2;
+        Pair* a = reinterpret_cast<Pair*>(acc) + (size_t)c * P;
         float2* o = out + (size_t)c * P;
         const float2* gc = g ? g + (size_t)c * N : nullptr;
-        for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < P; b += (int64_t)gridDim.x * blockDim.x) {
-            AccT re, im;
-            if constexpr (sizeof(AccT) == 8) {
-                const longlong2 v = reinterpret_cast<const longlong2*>(a)[b];
-                re = v.x;
-                im = v.y;
-            } else {
-                const float2 v = reinterpret_cast<const float2*>(a)[b];
-                re = v.x;
-                im = v.y;
+        const float2 gi0 = gc ? gc[i0] : make_float2(1.f, 0.f);
+        const float2 gi1 = gc ? gc[i1] : make_float2(1.f, 0.f);
+        for (int e0 = 0; e0 < len; e0 += kDumpThreads * kU) {
+            Pair v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * kDumpThreads + (int)threadIdx.x;
+                if (e < len) v[u] = a[e < len0 ? off0 + e : off1 + (e - len0)];
             }
-            float2 w = make_float2((float)re * inv_n, (float)im * inv_n);
-            if (gc) {
-                int i, j;
-                baseline_ij(b, N, i, j);
-                w = cmulf_conj(cmulf(w, gc[i]), gc[j]);
-            }
-            o[b] = w;
-            if (reset) {
-                if constexpr (sizeof(AccT) == 8) reinterpret_cast<longlong2*>(a)[b] = make_longlong2(0, 0);
-                else reinterpret_cast<float2*>(a)[b] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int e = e0 + u * kDumpThreads + (int)threadIdx.x;
+                if (e >= len) continue;
+                const bool first = e < len0;
+                const int64_t b = first ? off0 + e : off1 + (e - len0);
+                float2 w = make_float2((float)v[u].x * inv_n, (float)v[u].y * inv_n);
+                if (gc) {
+                    const int j = first ? i0 + e : i1 + (e - len0);
+                    w = cmulf_conj(cmulf(w, first ? gi0 : gi1), gc[j]);
+                }
+                o[b] = w;
+                if (reset) {
+                    Pair z;
+                    z.x = 0;
+                    z.y = 0;
+                    a[b] = z;
+                }
             }
         }
     }
@@ -127,8 +134,11 @@ corr_status corr_dump(corr_plan plan, void* d_acc, int n_accum, const double* d_
         if (e != cudaSuccess) return cuda_error(e, "phasor launch");
     }
     const int64_t P = p->n_baselines;
-    const int64_t bx = (P + kDumpThreads - 1) / kDumpThreads;
-    const dim3 grid((unsigned)(bx < 1024 ? bx : 1024), (unsigned)(p->n_chan < 65535 ? p->n_chan : 65535));
+    // row pairs x channel groups: a few waves of blocks, each block looping over channels
+    const int pairs = (p->n_inputs + 1) / 2;
+    const int64_t want_y = ((int64_t)(p->n_sm > 0 ? p->n_sm : 148) * 64 + pairs - 1) / pairs;
+    const int gy = (int)std::min<int64_t>(std::min<int64_t>(want_y, p->n_chan), 65535);
+    const dim3 grid((unsigned)pairs, (unsigned)(gy > 0 ? gy : 1));
     const float inv_n = 1.0f / (float)n_accum;
     if (p->sample_bits == 32)
         dump_kernel<float><<<grid, kDumpThreads, 0, s>>>(static_cast<float*>(d_acc), g, p->n_inputs, P, p->n_chan,
