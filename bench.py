@@ -446,7 +446,7 @@ def run_dump(args):
     import torch
 
     from paper_0906_1887_gb300 import corr
-    n, c, t = 1024, 1536, 256
+    n, c, t = args.dump_inputs, 1536, 256
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     plan = corr.Plan(n, c, t, 8)
@@ -474,7 +474,7 @@ def run_dump(args):
         res["reset" if reset else "read_only"] = {"ms": ms, "algorithmic_bytes": by, "achieved": by / (ms / 1e3) / 1e9,
                                                   "frac": by / (ms / 1e3) / 1e9 / hbm}
     line = {"metric": "dump step GB/s (average + phase correction)", "value": res["reset"]["achieved"], "unit": "GB/s",
-            "workload": "dump1024: accumulators of one 1024-input x 1536-channel dump (12.9 GB int64) -> "
+            "workload": f"dump{n}: accumulators of one {n}-input x {c}-channel dump ({c * P * 16 / 1e9:.1f} GB int64) -> "
                         "float32 corrected visibilities, accumulators reset",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["reset"]["ms"],
             "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s", "frac": res["reset"]["frac"],
@@ -576,6 +576,8 @@ def main():
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
     ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx", "dump"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--dump-inputs", type=int, default=1024,
+                    help="inputs of the dump workload (1024 = the 1024-input array; smaller for a profiler capture)")
     ap.add_argument("--large-chans", type=int, default=1536,
                     help="channels of the large-array workload (fewer only for profiling captures)")
     args = ap.parse_args()

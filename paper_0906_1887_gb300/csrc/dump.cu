@@ -41,11 +41,12 @@ __device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {   // a * conj
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Each block takes the baseline rows i and N - 1 - i of a channel (i < N / 2, or the middle
-// row alone when N is odd): N - i + i + 1 = N + 1 elements for every block, so the blocks are
-// equal, and an element's (i, j) follows from its position in the pair without any search.
-// Row i starts at off(i) = i N - i (i - 1) / 2 within the channel.  Each thread issues kU
-// loads before it computes, to keep enough bytes in flight; blocks loop over channels.
+// Each block takes the baseline rows i and N - 1 - i (i < N / 2, or the middle row alone when
+// N is odd) of the channels c = blockIdx.y + m gridDim.y: N - i + i + 1 = N + 1 elements per
+// channel for every block, so the blocks are equal, and an element's (i, j) follows from its
+// position in the pair without any search.  Row i starts at off(i) = i N - i (i - 1) / 2
+// within a channel.  The block's (channel, element) pairs are numbered flat, so each thread
+// issues kU loads before it computes whatever N is (the host keeps the flat count < 2^31).
 constexpr int kU = 4;
 
 template <typename AccT>
@@ -58,37 +59,53 @@ __global__ void __launch_bounds__(kDumpThreads) dump_kernel(AccT* __restrict__ a
     const int len = i1 == i0 ? len0 : N + 1;        // elements of the pair
     const int64_t off0 = (int64_t)i0 * N - (int64_t)i0 * (i0 - 1) / 2;
     const int64_t off1 = (int64_t)i1 * N - (int64_t)i1 * (i1 - 1) / 2;
-    for (int c = blockIdx.y; c < C; c += gridDim.y) {
-        Pair* a = reinterpret_cast<Pair*>(acc) + (size_t)c * P;
-        float2* o = out + (size_t)c * P;
-        const float2* gc = g ? g + (size_t)c * N : nullptr;
-        const float2 gi0 = gc ? gc[i0] : make_float2(1.f, 0.f);
-        const float2 gi1 = gc ? gc[i1] : make_float2(1.f, 0.f);
-        for (int e0 = 0; e0 < len; e0 += kDumpThreads * kU) {
-            Pair v[kU];
+    const int nch = (C - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;   // channels of this block
+    const uint32_t total = (uint32_t)nch * (uint32_t)len;
+    Pair* const a = reinterpret_cast<Pair*>(acc);
+    for (uint32_t f0 = 0; f0 < total; f0 += kDumpThreads * kU) {
+        Pair v[kU];
+        int64_t at[kU];   // element index in the [C][P] arrays, -1 past the end
+        int ci[kU], ej[kU];
+        // (channel step m, element e) of the thread's first element by one division, the
+        // others by adding the block size and wrapping
+        const uint32_t fl0 = f0 + threadIdx.x;
+        uint32_t m = fl0 / (uint32_t)len;
+        int e = (int)(fl0 - m * (uint32_t)len);
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int e = e0 + u * kDumpThreads + (int)threadIdx.x;
-                if (e < len) v[u] = a[e < len0 ? off0 + e : off1 + (e - len0)];
+        for (int u = 0; u < kU; ++u) {
+            if (u > 0) {
+                e += kDumpThreads;
+                while (e >= len) {
+                    e -= len;
+                    ++m;
+                }
             }
+            at[u] = -1;
+            if (f0 + (uint32_t)(u * kDumpThreads) + threadIdx.x < total) {
+                const int c = (int)blockIdx.y + (int)m * (int)gridDim.y;
+                at[u] = (int64_t)c * P + (e < len0 ? off0 + e : off1 + (e - len0));
+                ci[u] = c;
+                ej[u] = e;
+                v[u] = a[at[u]];
+            }
+        }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int e = e0 + u * kDumpThreads + (int)threadIdx.x;
-                if (e >= len) continue;
-                const bool first = e < len0;
-                const int64_t b = first ? off0 + e : off1 + (e - len0);
-                float2 w = make_float2((float)v[u].x * inv_n, (float)v[u].y * inv_n);
-                if (gc) {
-                    const int j = first ? i0 + e : i1 + (e - len0);
-                    w = cmulf_conj(cmulf(w, first ? gi0 : gi1), gc[j]);
-                }
-                o[b] = w;
-                if (reset) {
-                    Pair z;
-                    z.x = 0;
-                    z.y = 0;
-                    a[b] = z;
-                }
+        for (int u = 0; u < kU; ++u) {
+            if (at[u] < 0) continue;
+            float2 w = make_float2((float)v[u].x * inv_n, (float)v[u].y * inv_n);
+            if (g) {
+                const bool first = ej[u] < len0;
+                const int i = first ? i0 : i1;
+                const int j = first ? i0 + ej[u] : i1 + (ej[u] - len0);
+                const float2* gc = g + (size_t)ci[u] * N;
+                w = cmulf_conj(cmulf(w, gc[i]), gc[j]);
+            }
+            out[at[u]] = w;
+            if (reset) {
+                Pair z;
+                z.x = 0;
+                z.y = 0;
+                a[at[u]] = z;
             }
         }
     }
@@ -137,8 +154,18 @@ corr_status corr_dump(corr_plan plan, void* d_acc, int n_accum, const double* d_
     // row pairs x channel groups: a few waves of blocks, each block looping over channels
     const int pairs = (p->n_inputs + 1) / 2;
     const int64_t want_y = ((int64_t)(p->n_sm > 0 ? p->n_sm : 148) * 64 + pairs - 1) / pairs;
-    const int gy = (int)std::min<int64_t>(std::min<int64_t>(want_y, p->n_chan), 65535);
-    const dim3 grid((unsigned)pairs, (unsigned)(gy > 0 ? gy : 1));
+    int gy = (int)std::min<int64_t>(std::min<int64_t>(want_y, p->n_chan), 65535);
+    if (gy < 1) gy = 1;
+    // each block numbers its (channel, element) pairs in 32 bits
+    const int64_t per_block = ((int64_t)p->n_chan + gy - 1) / gy * (int64_t)(p->n_inputs + 1);
+    if (per_block >= (int64_t{1} << 31)) {
+        gy = (int)std::min<int64_t>(65535, std::min<int64_t>(
+                 p->n_chan, ((int64_t)p->n_chan * (p->n_inputs + 1) + (int64_t{1} << 30) - 1) >> 30));
+        if (((int64_t)p->n_chan + gy - 1) / gy * (int64_t)(p->n_inputs + 1) >= (int64_t{1} << 31))
+            return set_error(CORR_EUNSUPPORTED, "corr_dump: %d channels x %d inputs is too large for one call",
+                             p->n_chan, p->n_inputs);
+    }
+    const dim3 grid((unsigned)pairs, (unsigned)gy);
     const float inv_n = 1.0f / (float)n_accum;
     if (p->sample_bits == 32)
         dump_kernel<float><<<grid, kDumpThreads, 0, s>>>(static_cast<float*>(d_acc), g, p->n_inputs, P, p->n_chan,
