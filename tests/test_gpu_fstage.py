@@ -74,6 +74,9 @@ CASES = [  # (kind, n_chan, n_inputs, n_frames): every transform length 8 .. 409
     ("c8", 256, 5, 2), ("c8", 1024, 33, 1), ("c8", 4096, 2, 2),
     ("c4", 8, 7, 3), ("c4", 64, 64, 2), ("c4", 128, 130, 1), ("c4", 2048, 3, 1),
     ("r8", 4, 2, 2), ("r8", 64, 64, 2), ("r8", 128, 9, 3), ("r8", 2048, 1, 1),
+    # L >= 512 with whole groups of 4 inputs: the 4-input vector loads (8 bytes for complex
+    # 8-bit, 4 for the 1-byte kinds) and L = 2048 with pairs
+    ("c8", 512, 8, 2), ("c8", 1024, 12, 2), ("c4", 1024, 20, 2), ("r8", 256, 8, 2), ("c8", 2048, 6, 1),
 ]
 
 
@@ -85,6 +88,31 @@ def test_fstage_matches_oracle(kind, n_chan, n_inputs, n_frames):
     ref = fstage.fstage(p, n_inputs, n_chan, n_frames, kind)
     assert got.shape == ref.shape
     _check_spectra(got, ref, L)
+
+
+@pytest.mark.parametrize("kind,n_chan,n_inputs", [("c8", 512, 8), ("c4", 1024, 8), ("c8", 128, 64)])
+def test_fstage_unaligned_samples(kind, n_chan, n_inputs):
+    # samples starting 2 bytes past an 8-byte boundary: the kernel falls back to one load per
+    # sample, with the same result
+    from paper_0906_1887_gb300 import corr
+    L = fstage.transform_length(n_chan, kind)
+    F = 2
+    p = _time_samples(55 + n_chan, F * L, n_inputs, kind)
+    raw = np.ascontiguousarray(p).view(np.uint8).reshape(-1)
+    buf = torch.zeros(raw.size + 16, dtype=torch.uint8, device="cuda")
+    buf[2:2 + raw.size].copy_(torch.from_numpy(raw.copy()))
+    x = buf[2:2 + raw.size]
+    assert x.data_ptr() % 8 == 2
+    fp = corr.FPlan(n_inputs, n_chan, KIND_ID[kind])
+    spec = fp.empty_spectra(F)
+    spec.fill_(float("nan"))
+    fp.run(x, spec, F)
+    torch.cuda.synchronize()
+    out = spec.cpu().numpy()
+    fp.close()
+    got = out[..., 0].astype(np.float64) + 1j * out[..., 1]
+    assert np.array_equal(got, _run_f(p, n_inputs, n_chan, F, kind))
+    _check_spectra(got, fstage.fstage(p, n_inputs, n_chan, F, kind), L)
 
 
 def test_fstage_tone_lands_in_its_channel():
