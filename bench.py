@@ -440,6 +440,55 @@ def run_fx(args):
     print(json.dumps(line), flush=True)
 
 
+def run_float(args):
+    """The float variant of the 64-input stream workload (float32 samples, no rounding) through
+    the BF16x3 tensor-core engine (bf16 hi/lo split, three products, fp32 accumulation) and the
+    FP32 CUDA-core engine.  20 dumps per step: 7.9 GB of samples, larger than L2."""
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    n, c, t, d = 64, 768, 1000, 20
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    plan = corr.Plan(n, c, t, 32)
+    P = plan.n_baselines
+    x = synth.torch_correlated_gaussian_f32(d, t, c, n, 16.0, 0.1, 2500, dev)
+    vis = plan.empty_vis(d, dev)
+    hbm, bf16, src = _peaks()
+    algo = d * (t * c * n * 8 + c * P * 8)   # float32 samples in, float32 visibilities out
+    res = {}
+    for name, engine in (("bf16x3", corr.ENGINE_BF16X3), ("fp32", corr.ENGINE_FP32)):
+        ws = plan.empty_workspace(engine, d, dev)
+        run = lambda: plan.run(x, vis, ws, engine=engine, n_dumps=d, stream=stream)   # noqa: E731
+        for _ in range(args.warmup):
+            run()
+        torch.cuda.synchronize()
+        assert plan.check_device() == 0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.steps):
+            run()
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        res[name] = ev[0].elapsed_time(ev[-1]) / args.steps
+        del ws
+    cm = P * c * t * d
+    ms = res["bf16x3"]
+    gbs = algo / (ms / 1e3) / 1e9
+    line = {"metric": "X-engine TeraCMAC/s (float samples, BF16x3)", "value": cm / (ms / 1e3) / 1e12,
+            "unit": "TeraCMAC/s",
+            "workload": "stream64_float: 64 inputs x 768 ch x 1000 samples/dump x 20 dumps, float32 "
+                        "(sigma 16, rho 0.1, no rounding)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "bf16x3/f32",
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "algorithmic_bytes": algo, "peak_source": src,
+                         "note": "samples in + visibilities out; the bf16 hi/lo planes are an intermediate"},
+            "fp32_path": {"ms_per_step": res["fp32"], "value": cm / (res["fp32"] / 1e3) / 1e12,
+                          "speedup_bf16x3_over_fp32": res["fp32"] / ms},
+            "l2": "inputs larger than L2 (7.9 GB per step)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_dump(args):
     """Dump step with phase correction (Fig. 1, Sec. 2) on one dump of the 1024-input array's
     accumulators: a pure HBM stream (int64 in, float32 out, zeros back when resetting)."""
@@ -574,7 +623,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--dumps", type=int, default=N_DUMPS,
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx", "dump"])
+    ap.add_argument("--workload", default="stream", choices=["stream", "large", "batch", "serve", "fx", "dump", "float"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--dump-inputs", type=int, default=1024,
                     help="inputs of the dump workload (1024 = the 1024-input array; smaller for a profiler capture)")
@@ -586,7 +635,8 @@ def main():
         reference_arm(args)
         return
     if args.workload != "stream":
-        {"large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx, "dump": run_dump}[args.workload](args)
+        {"large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx, "dump": run_dump,
+         "float": run_float}[args.workload](args)
         return
 
     import torch

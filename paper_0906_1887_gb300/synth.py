@@ -154,6 +154,25 @@ def torch_correlated_gaussian_packed8(n_dumps: int, n_time: int, n_chan: int, n_
     return out.view(torch.uint8)
 
 
+def torch_correlated_gaussian_f32(n_dumps: int, n_time: int, n_chan: int, n_inputs: int,
+                                  sigma: float, rho: float, seed: int, device):
+    """Device-side float variant of the same recipe (no rounding, no clipping): float32
+    ``[n_dumps][T][C][N][2]`` (re, im), generated one dump at a time."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((n_dumps, n_time, n_chan, n_inputs, 2), dtype=torch.float32, device=device)
+    a = float(np.sqrt(1.0 - rho))
+    b = float(np.sqrt(rho))
+    for d in range(n_dumps):
+        z = torch.randn((n_time, n_chan, n_inputs, 2), generator=g, device=device) * a
+        if rho > 0.0:
+            z += torch.randn((n_time, n_chan, 1, 2), generator=g, device=device) * b
+        out[d].copy_(z.mul_(sigma))
+        del z
+    return out
+
+
 def torch_uniform_packed4(n_dumps: int, n_time: int, n_chan: int, n_inputs: int, seed: int, device,
                           lo: int = -7, hi: int = 7):
     """Device-side uniform 4-bit generator: uint8 ``[n_dumps][T][C][N]`` (high nibble re, low im)."""
