@@ -106,13 +106,16 @@ corr_status corr_plan_destroy(corr_plan plan);
 corr_status corr_plan_info(corr_plan plan, int64_t *n_baselines, size_t *packed_bytes, size_t *vis_bytes);
 
 /*
- * Launch knob of the packed-sample tensor-core kernel for this plan (no counterpart in the
- * paper: it shapes the pipeline, not what it computes): op_stages = depth of the fp16
- * operand ring in shared memory, 0 = the default; a depth that leaves fewer than 3 stages
- * for the packed-sample ring is reduced to what fits.  Results are identical for every
- * setting.  CORR_EINVAL outside [0, 16].
+ * Launch knobs of the tensor-core kernel for this plan (no counterpart in the paper: they
+ * shape the pipeline, not what it computes).  op_stages = depth of the operand ring in shared
+ * memory, 0 = the default; a depth that leaves fewer than 3 stages for the sample ring is
+ * reduced to what fits.  float_planes (CORR_ENGINE_BF16X3 on float samples): 0 = the
+ * default, the tensor-core kernel loads the floats and splits them into bf16 hi + lo itself
+ * where it can (arrays of at most 64 inputs, an even count), needing no workspace; 1 = always
+ * split into hi/lo planes in the workspace first.  Results are identical for every setting.
+ * CORR_EINVAL when op_stages is outside [0, 16] or float_planes outside [0, 1].
  */
-corr_status corr_plan_set_tuning(corr_plan plan, int op_stages);
+corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes);
 
 /* Device workspace (bytes) corr_xengine_run_batch needs for `engine` and n_dumps
  * dumps.  0 means the engine needs none (d_workspace may be NULL). */

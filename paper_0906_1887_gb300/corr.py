@@ -32,7 +32,7 @@ SIGNATURES = {
     "corr_plan_create": (_c_int, [_P(_vp), _c_int, _c_int, _c_int, _c_int]),
     "corr_plan_destroy": (_c_int, [_vp]),
     "corr_plan_info": (_c_int, [_vp, _P(_c_i64), _P(_c_sz), _P(_c_sz)]),
-    "corr_plan_set_tuning": (_c_int, [_vp, _c_int]),
+    "corr_plan_set_tuning": (_c_int, [_vp, _c_int, _c_int]),
     "corr_workspace_size": (_c_int, [_vp, _c_int, _c_int, _P(_c_sz)]),
     "corr_unpack": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
     "corr_xengine_run": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
@@ -225,9 +225,11 @@ class Plan:
         check(lib().corr_dump_workspace_size(self._h, ctypes.byref(b)), "corr_dump_workspace_size")
         return b.value
 
-    def set_tuning(self, op_stages: int = 0):
-        """Operand ring depth of the packed-sample tensor-core kernel (results do not depend on it)."""
-        check(lib().corr_plan_set_tuning(self._h, op_stages), "corr_plan_set_tuning")
+    def set_tuning(self, op_stages: int = 0, float_planes: int = 0):
+        """Operand ring depth of the tensor-core kernel, and for BF16x3 on float samples whether the
+        hi/lo split goes through planes in memory (1) or happens in the kernel where it can (0);
+        results do not depend on either."""
+        check(lib().corr_plan_set_tuning(self._h, op_stages, float_planes), "corr_plan_set_tuning")
 
     def workspace_size(self, engine: int, n_dumps: int = 1) -> int:
         b = ctypes.c_size_t()

@@ -114,10 +114,13 @@ corr_status corr_plan_info(corr_plan plan, int64_t* n_bl, size_t* packed_bytes, 
     return CORR_OK;
 }
 
-corr_status corr_plan_set_tuning(corr_plan plan, int op_stages) {
+corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes) {
     if (!plan) return set_error(CORR_EINVAL, "corr_plan_set_tuning: plan is NULL");
     if (op_stages < 0 || op_stages > 16) return set_error(CORR_EINVAL, "op_stages=%d outside [0, 16]", op_stages);
+    if (float_planes < 0 || float_planes > 1)
+        return set_error(CORR_EINVAL, "float_planes=%d outside [0, 1]", float_planes);
     reinterpret_cast<Plan*>(plan)->tc_op_stages = op_stages;
+    reinterpret_cast<Plan*>(plan)->tc_float_planes = float_planes;
     return CORR_OK;
 }
 
@@ -134,8 +137,10 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t*
             *bytes = planes_bytes(*p, n_dumps);
             return CORR_OK;
         case CORR_ENGINE_BF16X3:
-            // hi and lo bf16 planes
-            *bytes = (size_t)n_dumps * p->n_chan * (size_t)p->nb * kBlockRows * (size_t)p->kp * 2 * 2;
+            // hi and lo bf16 planes, unless the tensor-core kernel splits the floats itself
+            *bytes = (!p->tc_float_planes && tc_rawf32_supported(*p))
+                         ? 0
+                         : (size_t)n_dumps * p->n_chan * (size_t)p->nb * kBlockRows * (size_t)p->kp * 2 * 2;
             return CORR_OK;
         default:
             return set_error(CORR_EINVAL, "unknown engine %d", engine);
@@ -185,10 +190,14 @@ corr_status corr_xengine_run_batch(corr_plan plan, const void* d_packed, int n_d
     } else if (engine == CORR_ENGINE_BF16X3) {
         if (p->sample_bits != 32)
             return set_error(CORR_EUNSUPPORTED, "CORR_ENGINE_BF16X3 takes float samples (sample_bits=32)");
-        char* hi = static_cast<char*>(d_workspace);
-        char* lo = hi + need / 2;
-        e = launch_unpack_bf16x2(*p, d_packed, n_dumps, hi, lo, s);
-        if (e == cudaSuccess) e = launch_xeng_tc(*p, hi, lo, n_dumps, d_vis, accumulate, s);
+        if (need == 0) {   // fused: TMA loads the floats, the converter warps split them
+            e = launch_xeng_tc_rawf32(*p, d_packed, n_dumps, d_vis, accumulate, s);
+        } else {
+            char* hi = static_cast<char*>(d_workspace);
+            char* lo = hi + need / 2;
+            e = launch_unpack_bf16x2(*p, d_packed, n_dumps, hi, lo, s);
+            if (e == cudaSuccess) e = launch_xeng_tc(*p, hi, lo, n_dumps, d_vis, accumulate, s);
+        }
     } else {
         return set_error(CORR_EINVAL, "unknown engine %d", engine);
     }

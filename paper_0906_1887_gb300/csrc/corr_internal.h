@@ -38,6 +38,7 @@ struct Plan {
     int n_sm = 0;
     int* d_status = nullptr; // [4] device status words
     int tc_op_stages = 0;     // operand ring depth of the packed-sample kernel (0: default)
+    int tc_float_planes = 0;  // BF16x3: 1 = hi/lo planes through memory even where the fused path applies
     // host-buffer pipeline (corr_xengine_run_host), created on first use
     char* pipe_dev = nullptr;   // 2 x (chunk inputs) + 2 x (chunk outputs) + workspace
     size_t pipe_bytes = 0;
@@ -89,6 +90,10 @@ struct TcTuning {
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };
 int tc_default_cpi(int n_inputs);
+// BF16x3 on float samples with the hi/lo split done in the tensor-core kernel (single-block arrays)
+bool tc_rawf32_supported(const Plan& p);
+cudaError_t launch_xeng_tc_rawf32(const Plan& p, const void* d_samples, int n_dumps, void* d_vis, int accumulate,
+                                  cudaStream_t s);
 // Fused dump mode: float32 [n_dumps][C][P][2] = V / n_accum * phasor_i conj(phasor_j) (phasor
 // float2 [C][N] or nullptr); every dump must fit one exact chunk.
 cudaError_t launch_xeng_tc_raw_dump(const Plan& p, const void* d_packed, int n_dumps, void* d_out, const void* phasor,

@@ -44,6 +44,7 @@
 // overlaps the MMAs of the next.  Every wait is bounded.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -72,18 +73,23 @@ constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 // slot and its destination are 16-byte aligned together and the bulk copies stay aligned.
 constexpr int kStageRowBytesF = 66 * 8;
 
-enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3 };
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRawF32 = 4 };
 
 template <int MODE>
 struct Cfg {
-    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4);
+    // kRawF32: float32 complex samples loaded by TMA and split into bf16 hi + lo by the converter
+    // warps (the BF16x3 products of the planes path, without the planes in memory)
+    static constexpr bool kFloat = MODE == kRawF32;
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || kFloat);
     static constexpr bool kBits8 = MODE == kRaw8;
-    static constexpr bool kSplit = (MODE == kPlanesBF16x3);
+    static constexpr bool kSplit = (MODE == kPlanesBF16x3 || kFloat);
     static constexpr int kEpiWarps = 4;     // one per tensor-memory lane quarter
     static constexpr int kConvWarps = 8;
     static constexpr int kThreads = 64 + 32 * kEpiWarps + (kRaw ? 32 * kConvWarps : 0);
-    static constexpr int kBps = kBits8 ? 2 : 1;                           // packed bytes per sample
+    static constexpr int kBps = kFloat ? 8 : (kBits8 ? 2 : 1);            // packed bytes per sample
     static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
+    // x coordinate of a 64-input block in the raw tensor map: bytes, or 8-byte complex floats
+    static constexpr int kMapX = kFloat ? kBlockInputs : kBlockInputs * kBps;
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
 };
 
@@ -311,6 +317,39 @@ __device__ __forceinline__ void convert_words4(const uint32_t (&w)[8], uint32_t 
     }
 }
 
+// One warp-sized slice of a float32 tile -> bf16 hi and lo operand tiles (hi = bf16(x),
+// lo = bf16(x - hi), both rounded to nearest, as the planes path splits).  A raw sample row
+// holds 128 words, (re, im) of 64 inputs, so word w of a row is operand row w; lane l takes
+// rows l + 32 kk (kk = 0..3) of samples 8q .. 8q + 7 and writes each row's 16-byte chunk q of
+// the hi tile and of the lo tile (kTileBytes further).  A quarter-warp's rows differ in
+// (row & 7), so its swizzled chunks fall in distinct banks.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b, uint32_t& lo) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+    return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+}
+
+__device__ __forceinline__ void convert_slice_f32(uint32_t raw_tile, uint32_t dst_hi, int q, int lane) {
+    constexpr uint32_t kRowBytes = kBlockInputs * 8;   // one sample row of the raw tile
+    const uint32_t src = raw_tile + (uint32_t)q * 8u * kRowBytes + 4u * (uint32_t)lane;
+    const uint32_t q16 = (uint32_t)q << 4;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t row = (uint32_t)lane + 32u * kk;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(ld_shared_u32(src + (uint32_t)e * kRowBytes + 128u * kk));
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) h[p] = bf16_pair(v[2 * p], v[2 * p + 1], l[p]);
+        const uint32_t at = dst_hi + (row >> 3) * 1024u + (row & 7u) * 128u + (q16 ^ ((row & 7u) << 4));
+        st_shared_v4(at, h[0], h[1], h[2], h[3]);
+        st_shared_v4(at + (uint32_t)kTileBytes, l[0], l[1], l[2], l[3]);
+    }
+}
+
 // Raw ring feed: packed tile [64 t][64 inputs] staged in shared memory (t rows PITCH bytes
 // apart), raw_lane = raw + the lane's byte offset.
 template <uint32_t PITCH>
@@ -400,7 +439,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         *abort_flag = 0;
         ptx::fence_mbar_init();
         for (int j = 0; j < prm.n_jobs; ++j) ptx::prefetch_tensormap(&prm.jobs[j].map);
-        if (C::kSplit) ptx::prefetch_tensormap(&prm.map_lo);
+        if (C::kSplit && !C::kRaw) ptx::prefetch_tensormap(&prm.map_lo);
     }
     if (warp == 1) {
         ptx::tmem_alloc(ptx::smem_u32(tmem_slot), prm.tmem_cols);
@@ -451,10 +490,10 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
                         // one box covers cpi adjacent channels (cpi x 64 inputs per sample row)
                         ptx::mbar_expect_tx(fb, (same ? (uint32_t)jb.cpi : 2u) * (uint32_t)C::kRawTileBytes);
-                        tma_load_4d(st, &jb.map, I * kBlockInputs * C::kBps, it.c0, kb * kTimeBlock, (int)it.d, fb);
+                        tma_load_4d(st, &jb.map, I * C::kMapX, it.c0, kb * kTimeBlock, (int)it.d, fb);
                         if (!same)
-                            tma_load_4d(st + C::kRawTileBytes, &jb.map, J * kBlockInputs * C::kBps, it.c0,
-                                        kb * kTimeBlock, (int)it.d, fb);
+                            tma_load_4d(st + C::kRawTileBytes, &jb.map, J * C::kMapX, it.c0, kb * kTimeBlock,
+                                        (int)it.d, fb);
                     } else {
                         const uint32_t st = ptx::smem_u32(ring + s * prm.op_stage_bytes);
                         const int64_t dc = it.d * jb.n_chan + it.c0;   // planes: one channel per item
@@ -877,6 +916,12 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 }
                 const uint32_t raw = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes) + lane_byte;
                 const uint32_t dst = ptx::smem_u32(ring + os * prm.op_stage_bytes);
+                if constexpr (C::kFloat) {
+                    // single-block arrays only (one tile, B = A): slice q of the tile per warp
+                    const uint32_t raw_tile = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes);
+                    for (int sl = cwarp; sl < kTimeBlock / 8; sl += C::kConvWarps)
+                        convert_slice_f32(raw_tile, dst, sl, lane);
+                } else {
                 const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
                 // all loads of the warp's slices (slices cwarp and cwarp + 8) are issued before
                 // the first conversion, so their shared-memory latencies overlap
@@ -904,6 +949,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         else convert_words4(w[v], out, 2 * part + (lane >> 4), cl);
                     }
                 }
+                }   // packed integers
                 fence_async_shared();   // generic-proxy writes -> visible to the tensor core
                 __syncwarp();
                 if (lane == 0) {
@@ -1080,7 +1126,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->bar_offset = prm->staging_offset + stage_space;
     const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
     auto kern = xeng_tc_kernel<MODE, MAXJ, false>;
-    if constexpr (C::kRaw && MAXJ == 1) {
+    if constexpr (C::kRaw && !C::kFloat && MAXJ == 1) {
         if (any_dump) kern = xeng_tc_kernel<MODE, MAXJ, true>;
     } else if (any_dump) {   // dump mode is built for single-job packed-sample launches only
         delete prm;
@@ -1179,6 +1225,35 @@ cudaError_t launch_raw_impl(const Plan& p, const void* d_packed, int n_dumps, vo
     return cudaSuccess;
 }
 }  // namespace
+
+bool tc_rawf32_supported(const Plan& p) {
+    // single-block arrays (the float raw stage and hi/lo operand tiles fill the ring), and a
+    // row of N complex floats a multiple of 16 bytes (TMA strides)
+    return p.sample_bits == 32 && p.n_inputs <= kBlockInputs && (p.n_inputs % 2) == 0;
+}
+
+cudaError_t launch_xeng_tc_rawf32(const Plan& p, const void* d_samples, int n_dumps, void* d_vis, int accumulate,
+                                  cudaStream_t s) {
+    if (!tc_rawf32_supported(p) || (reinterpret_cast<uintptr_t>(d_samples) & 15u)) return cudaErrorInvalidValue;
+    if ((int64_t)n_dumps * p.n_chan >= (int64_t{1} << 31)) return cudaErrorInvalidValue;   // 32-bit item indices
+    auto enc = get_encode();
+    if (!enc) return cudaErrorInvalidValue;
+    // [dump][time][chan][input] of 8-byte complex floats; box = 64 inputs x 1 channel x 64 samples
+    CUtensorMap m;
+    const cuuint64_t row = (cuuint64_t)p.n_inputs * 8;
+    cuuint64_t dims[4] = {(cuuint64_t)p.n_inputs, (cuuint64_t)p.n_chan, (cuuint64_t)p.n_time, (cuuint64_t)n_dumps};
+    cuuint64_t strides[3] = {row, row * p.n_chan, row * p.n_chan * p.n_time};
+    cuuint32_t box[4] = {(cuuint32_t)kBlockInputs, 1, (cuuint32_t)kTimeBlock, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(d_samples), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, 32, d_samples, d_vis, 1};
+    TcTuning tune;
+    tune.op_stages = p.tc_op_stages;
+    return launch_jobs<kRawF32, 1>(&sp, 1, &m, nullptr, accumulate, p.d_status, p.n_sm, tune, s);
+}
 
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s, const TcTuning* tune) {

@@ -66,6 +66,19 @@ def test_fused_ring_depths_bit_exact(op_stages, n, c, t, bits):
     assert np.array_equal(v, oracle.xcorr_int(p, n, c, t, bits))
 
 
+# BF16x3 on float samples: split into bf16 hi + lo inside the tensor-core kernel (single-block
+# arrays of an even number of inputs) or through hi/lo planes in memory -- the same splits and
+# the same products in the same order, so the same bits
+@pytest.mark.parametrize("n,c,t", [(2, 1, 1), (8, 3, 100), (34, 4, 130), (64, 5, 1000), (64, 2, 64), (33, 2, 70)])
+def test_bf16x3_split_in_kernel_matches_planes(n, c, t):
+    re, im = synth.correlated_gaussian(91 + n, t, c, n, 1.0, 0.3, as_float=True)
+    x = synth.packf32(re, im)
+    fused = run_engine(x, n, c, t, 32, BF16X3, tuning=(0, 0))[0]
+    planes = run_engine(x, n, c, t, 32, BF16X3, tuning=(0, 1))[0]
+    assert np.array_equal(fused, planes)
+    assert normwise_error(fused.astype(np.float64), oracle.xcorr_f64(x, n, c, t), n) <= 1e-2
+
+
 @pytest.mark.parametrize("n", [64, 192])
 def test_fused_dumps_and_accumulate(n):
     c, t, bits, d = 3, 200, 8, 3
