@@ -447,7 +447,8 @@ def run_float(args):
     import torch
 
     from paper_0906_1887_gb300 import corr, synth
-    n, c, t, d = 64, 768, 1000, 20
+    n, c, t = 64, 768, 1000
+    d = 20 if args.dumps == N_DUMPS else args.dumps   # fewer only for profiler captures
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     plan = corr.Plan(n, c, t, 32)
@@ -477,7 +478,7 @@ def run_float(args):
     gbs = algo / (ms / 1e3) / 1e9
     line = {"metric": "X-engine TeraCMAC/s (float samples, BF16x3)", "value": cm / (ms / 1e3) / 1e12,
             "unit": "TeraCMAC/s",
-            "workload": "stream64_float: 64 inputs x 768 ch x 1000 samples/dump x 20 dumps, float32 "
+            "workload": f"stream64_float: 64 inputs x 768 ch x 1000 samples/dump x {d} dumps, float32 "
                         "(sigma 16, rho 0.1, no rounding)",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "bf16x3/f32",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -485,7 +486,7 @@ def run_float(args):
                          "note": "samples in + visibilities out; the bf16 hi/lo planes are an intermediate"},
             "fp32_path": {"ms_per_step": res["fp32"], "value": cm / (res["fp32"] / 1e3) / 1e12,
                           "speedup_bf16x3_over_fp32": res["fp32"] / ms},
-            "l2": "inputs larger than L2 (7.9 GB per step)"}
+            "l2": f"inputs larger than L2 ({d * t * c * n * 8 / 1e9:.1f} GB per step)"}
     print(json.dumps(line), flush=True)
 
 
