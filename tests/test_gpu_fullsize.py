@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_0906_1887_gb300 import synth
-from _gpu_helpers import run_engine
+from _gpu_helpers import normwise_error, run_engine
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -33,3 +33,18 @@ def test_fullsize_sampled_channels(name, nsample):
     # properties that hold for every channel: autos real and non-negative
     auto_idx = [i * n - i * (i - 1) // 2 for i in range(n)]
     assert (v[:, auto_idx, 1] == 0).all() and (v[:, auto_idx, 0] >= 0).all()
+
+
+def test_fullsize_float_bf16x3_sampled_channels():
+    # the float variant of the 64-input stream (one dump): BF16x3 with the hi/lo split in the
+    # kernel, bit-identical to the planes path, and within 1e-2 normwise of the float64 oracle
+    n, c, t = 64, 768, 1000
+    re, im = synth.correlated_gaussian(2500, t, c, n, 16.0, 0.1, as_float=True)
+    x = synth.packf32(re, im)
+    del re, im
+    fused = run_engine(x, n, c, t, 32, 2, tuning=(0, 0))[0]
+    planes = run_engine(x, n, c, t, 32, 2, tuning=(0, 1))[0]
+    assert np.array_equal(fused, planes)
+    chans = np.random.default_rng(8).choice(c, size=6, replace=False)
+    ref = oracle.xcorr_f64(x, n, c, t, chans=chans)
+    assert normwise_error(fused[chans].astype(np.float64), ref, n) <= 1e-2
