@@ -131,7 +131,9 @@ Plan plan_of(const corr_job_desc& d, int device, int n_sm) {
 // Device bytes a job occupies while it runs: status, packed samples, visibilities, workspace.
 size_t footprint(const corr_job_desc& d, bool* raw) {
     Plan p = plan_of(d, 0, 0);
-    *raw = d.sample_bits != 32 && tc_raw_supported(p);
+    // samples the tensor-core kernel reads as they are: packed integers it can address with TMA,
+    // and float samples of single-block arrays (split into bf16 hi/lo inside the kernel)
+    *raw = d.sample_bits == 32 ? tc_rawf32_supported(p) : tc_raw_supported(p);
     size_t ws = 0;
     if (!*raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : planes_bytes(p, 1);
     return round_up(16) + round_up(packed_bytes(d)) + round_up(vis_bytes(d)) + round_up(ws);
@@ -176,7 +178,8 @@ cudaError_t issue(corr_server_s* S, Job& j) {
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         if (j.raw) {
-            e = launch_xeng_tc_raw(p, d_packed, 1, d_vis, 0, s);
+            e = j.desc.sample_bits == 32 ? launch_xeng_tc_rawf32(p, d_packed, 1, d_vis, 0, s)
+                                         : launch_xeng_tc_raw(p, d_packed, 1, d_vis, 0, s);
         } else if (j.desc.sample_bits == 32) {
             const size_t half = (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2;
             e = launch_unpack_bf16x2(p, d_packed, 1, d_ws, d_ws + half, s);
