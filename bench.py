@@ -350,10 +350,19 @@ def run_batch(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_each = e0.elapsed_time(e1) / args.steps
+    # algorithmic bytes of the step: packed samples in (2 B per complex sample) + int64 visibilities out
+    algo = sum(2 * n * c * t + 16 * (n * (n + 1) // 2) * c for n, c, t in sizes)
+    hbm, bf16, src = _peaks()
+    gbs = algo / (ms / 1e3) / 1e9
+    tflops = 8 * cm / (ms / 1e3) / 1e12   # 4 real MACs per CMAC
     line = {"metric": "X-engine TeraCMAC/s", "value": cm / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s",
             "workload": "batch40: 8 each of 16/32/64/128/256 dual-pol antennas, 64..1024 channels, "
                         "128..2048 samples, 8-bit Gaussian sigma 16, seed 4000",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "roofline": {"bound": "hbm", "kernel": "xeng_tc_kernel<raw8, job table>", "achieved": gbs,
+                         "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": algo,
+                         "peak_source": src, "tensor_tflops_algorithmic": tflops,
+                         "tensor_frac_of_measured_bf16_burst": tflops / bf16},
             "one_launch_per_job": {"ms_per_step": ms_each, "value": cm / (ms_each / 1e3) / 1e12},
             "batch": info, "autotune_seconds": tune_s, "cmacs_per_step": cm}
     print(json.dumps(line), flush=True)
