@@ -75,7 +75,10 @@ typedef enum {
      * samples. */
     CORR_ENGINE_FP32 = 1,
     /* Float samples on the tensor cores: x = h + l with h = bf16(x),
-     * l = bf16(x - h); V ~= h h^H + h l^H + l h^H with fp32 accumulation. */
+     * l = bf16(x - h); V ~= h h^H + h l^H + l h^H with fp32 accumulation.  For arrays of
+     * at most 64 inputs (an even count) the split happens inside the tensor-core kernel
+     * and needs no workspace; otherwise hi/lo planes go through the workspace.  Both give
+     * the same bits. */
     CORR_ENGINE_BF16X3 = 2
 } corr_engine;
 
