@@ -27,9 +27,11 @@
 //              interleaved row order; TMA loads 128-row x 64-sample tiles with 128-byte
 //              swizzle straight into the operand ring.
 //   raw     -- (4/8-bit samples) TMA loads the packed [time][chan][input] bytes of a
-//              64-input x 64-sample block and four converter warps turn them into the
+//              64-input x 64-sample block and eight converter warps turn them into the
 //              swizzled fp16 operand tiles in shared memory: the unpack/transpose step
-//              (Sec. 4) fused into the X kernel, so the samples cross HBM once.
+//              (Sec. 4) fused into the X kernel, so the samples cross HBM once.  Float
+//              samples of single-block arrays go the same way (8-byte complex floats in,
+//              bf16 hi and lo tiles out) instead of through planes.
 //
 // CTA roles (one CTA per SM, persistent over work items = (dump, channel, I, J)):
 //   warp 0       TMA producer
@@ -37,7 +39,8 @@
 //   warps 2..5   epilogue, one warp per tensor-memory lane quarter: tensor memory ->
 //                registers -> lane-pair combine -> int64 -> baseline order, stored from
 //                registers (single-block arrays) or staged in shared memory and bulk-copied
-//   warps 6..13  (raw only) converters: packed bytes -> fp16 K-major swizzled tiles
+//   warps 6..13  (raw only) converters: packed bytes -> fp16 (floats -> bf16 hi/lo) K-major
+//                swizzled tiles
 // Shared memory is carved at launch: when the array has a single 64-input block every
 // item is a diagonal tile (B = A), so stages hold one tile and the rings get deeper.
 // Tensor memory holds two accumulators (128 columns each) so the epilogue of one item
