@@ -774,7 +774,8 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    # the CPU oracle is timed on rank 0 at N = 1 only (a reported baseline, not part of the run)
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
     line = {
         "metric": "X-engine TeraCMAC/s", "value": value, "unit": "TeraCMAC/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -785,7 +786,8 @@ def main():
         "real_time_factor": rtf,
         "fp32_path": {"value": value32, "unit": "TeraCMAC/s", "ms_per_step": ms32, "speedup_tc_over_fp32": value / value32},
         "e2e": {"value": e2e_value, "unit": "TeraCMAC/s", "ms_per_step": ms_e2e,
-                "h2d_bytes_per_step": int(packed.numel()), "d2h_bytes_per_step": int(vis.numel() * vis.element_size()),
+                "h2d_bytes_per_step": int(packed.numel()) * world,
+                "d2h_bytes_per_step": int(vis.numel() * vis.element_size()) * world,
                 "api": "corr_xengine_run_host (pinned host buffers, chunked copy/compute overlap)",
                 "timing": "host wall clock around the synchronous call"},
         "roofline": roofline,
