@@ -172,16 +172,27 @@ corr_status corr_xengine_run_planes(corr_plan plan, const void *d_planes, int n_
  * Scratch: the unpacked sample planes (corr_unpack's layout, n_chan * ceil(N/64) * 128 *
  * Kp * 2 bytes) live in a fixed 64 MiB array inside the library; every GPU that loads the
  * library holds it until the process exits.  Larger dumps return CORR_EINVAL with a
- * message naming the size.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  The call itself calls no cudaMalloc, cudaFree or allocating
- * library routine.  All calls share the array and its contents persist between calls:
- * calls whose GPU work overlaps (other streams or host threads on the same device) race
- * and must be serialised by the caller.  Bounded-wait failures inside the kernels leave
- * the output incomplete and are not reported by this call.
+ * message naming the array's size in bytes (the check is made before any size product can
+ * overflow).  The first call on each device, and the first after that device's CUDA context
+ * changes (cudaDeviceReset), looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.  The call itself
+ * calls no cudaMalloc, cudaFree or allocating library routine.  All calls share the array and
+ * its contents persist between calls: calls whose GPU work overlaps (other streams or host
+ * threads on the same device) race and must be serialised by the caller.  A bounded wait
+ * inside the kernels that gives up leaves the output incomplete; it is recorded in a status
+ * block beside the array, which each call zeroes on its stream and corr_static_check reads.
  */
 corr_status corr_xengine_run_static(const void *d_packed, int n_inputs, int n_chan, int n_time,
                                     int sample_bits, void *d_vis, int accumulate, void *stream);
+
+/*
+ * Status of the last corr_xengine_run_static call on the current device, read and cleared
+ * (no counterpart in the paper; allocates nothing).  Synchronises `stream` (pass the stream
+ * of that call), copies the status block to the host, zeroes it, and sets *device_error to 0
+ * or to the code a kernel recorded when one of its bounded waits gave up (then returns
+ * CORR_ETIMEOUT).  CORR_EINVAL if device_error is NULL; CORR_ECUDA on a failed copy.
+ */
+corr_status corr_static_check(int *device_error, void *stream);
 
 /*
  * The X stage of n_dumps dumps held in HOST memory, end to end: the prototype streams
@@ -205,8 +216,8 @@ corr_status corr_xengine_run_host(corr_plan plan, const void *host_packed, int n
  *                    (DC to Nyquist, N_C + 1 channels) kept, the mirrored half dropped
  *                    (the paper transforms real input this way to keep power-of-two sizes).
  * The DFT is the forward, unnormalised X_k = sum_s x_s exp(-2 pi i k s / L); channel c is
- * bin c.  Computed in float32 on the GPU (Stockham radix-4/2 stages, twiddles rounded from
- * double); the relative L2 error of a frame's spectrum against an exact transform is a few
+ * bin c.  Computed in float32 on the GPU (Stockham stages of radix 16, the last of radix 8, 4
+ * or 2; twiddles rounded from double); the relative L2 error of a frame's spectrum against an exact transform is a few
  * times 2^-24 log2 L.
  *
  *   kind               packed time samples, [time][n_inputs], input index fastest (Sec. 3)

@@ -39,6 +39,7 @@ SIGNATURES = {
     "corr_xengine_run_batch": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_planes": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_static": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp]),
+    "corr_static_check": (_c_int, [_P(_c_int), _vp]),
     "corr_xengine_run_host": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int]),
     "corr_plan_check": (_c_int, [_vp, _P(_c_int)]),
     "corr_selftest_stall": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _P(_c_int)]),
