@@ -70,9 +70,9 @@ typedef enum {
      * sums stay below 2^24 within each flushed time chunk, so the int64 result is
      * bit-identical to the definition.  Not valid for float samples. */
     CORR_ENGINE_TC = 0,
-    /* CUDA-core FP32 X stage (the plain form).  Exact for integer samples (time
-     * chunks flushed to int64); fp32 arithmetic with two-level summation for float
-     * samples. */
+    /* CUDA-core FP32 X stage (the plain form), on the packed samples directly (no
+     * workspace).  Exact for integer samples (time chunks flushed to int64); fp32
+     * arithmetic with two-level summation for float samples. */
     CORR_ENGINE_FP32 = 1,
     /* Float samples on the tensor cores: x = h + l with h = bf16(x),
      * l = bf16(x - h); V ~= h h^H + h l^H + l h^H with fp32 accumulation.  For arrays of
@@ -120,8 +120,30 @@ corr_status corr_plan_info(corr_plan plan, int64_t *n_baselines, size_t *packed_
  */
 corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes);
 
-/* Device workspace (bytes) corr_xengine_run_batch needs for `engine` and n_dumps
- * dumps.  0 means the engine needs none (d_workspace may be NULL). */
+/*
+ * Operand feed of the tensor-core X stage for 4/8-bit samples (no counterpart in the paper; the
+ * results are identical for every setting).  The kernel either converts the packed samples
+ * itself (converter warps; the samples cross HBM once, but each 64-input block is converted once
+ * per tile it meets, about N/128 times per channel) or reads fp16 sample planes that the unpack
+ * kernel wrote into the workspace first (each block converted once; the planes cost HBM
+ * traffic).  operands:
+ *   CORR_OPERANDS_AUTO    planes for arrays of at least 256 inputs (4 blocks) when a workspace
+ *                         is given, and always where the packed rows are not 16-byte multiples;
+ *   CORR_OPERANDS_PACKED  always the fused conversion (CORR_EUNSUPPORTED where rows are not
+ *                         16-byte multiples);
+ *   CORR_OPERANDS_PLANES  always planes (the workspace is then required).
+ * items (plane feed): CORR_ITEMS_AUTO / CORR_ITEMS_WIDE = work items of block I against blocks
+ * J and J + 1 in one M = 128, N = 256 MMA (a quarter fewer operand loads per tile);
+ * CORR_ITEMS_TILES = one 64 x 64 input tile per item.  CORR_EINVAL on unknown values.
+ */
+enum { CORR_OPERANDS_AUTO = 0, CORR_OPERANDS_PACKED = 1, CORR_OPERANDS_PLANES = 2 };
+enum { CORR_ITEMS_AUTO = 0, CORR_ITEMS_TILES = 1, CORR_ITEMS_WIDE = 2 };
+corr_status corr_plan_set_operands(corr_plan plan, int operands, int items);
+
+/* Device workspace (bytes) corr_xengine_run_batch uses for `engine` and n_dumps dumps.  0 means
+ * the engine needs none (d_workspace may be NULL).  For CORR_ENGINE_TC on arrays whose packed
+ * rows are 16-byte multiples the workspace is optional unless CORR_OPERANDS_PLANES is set: a
+ * NULL workspace runs the fused conversion, a workspace of this size the plane feed. */
 corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t *bytes);
 
 /*
@@ -131,9 +153,11 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t 
  * blocks of 64 and Kp = n_time rounded up to a multiple of 64: row 2r holds the real
  * parts of input 64*nb + r and row 2r + 1 its imaginary parts, one element per time
  * sample, zero for padded inputs and samples.  Element type: fp16 for 4/8-bit
- * samples (exact), fp32 for float samples.  Size: corr_workspace_size(FP32 engine).
+ * samples (exact), fp32 for float samples.  Size: corr_planes_size.
  */
 corr_status corr_unpack(corr_plan plan, const void *d_packed, int n_dumps, void *d_planes, void *stream);
+/* Bytes of the sample planes of n_dumps dumps (corr_unpack's output). */
+corr_status corr_planes_size(corr_plan plan, int n_dumps, size_t *bytes);
 
 /*
  * The X stage of one dump: V = sum over the dump's n_time samples, in baseline order.
@@ -326,7 +350,13 @@ typedef struct corr_batch_s *corr_batch;   /* opaque, owned by the library */
 enum {
     CORR_BATCH_GRAPH = 1,       /* capture the launch(es) into a CUDA graph; corr_batch_run replays it */
     CORR_BATCH_AUTOTUNE = 2,    /* time candidate launch shapes on the batch's buffers, keep the fastest */
-    CORR_BATCH_ACCUMULATE = 4   /* add into the jobs' visibilities instead of overwriting them */
+    CORR_BATCH_ACCUMULATE = 4,  /* add into the jobs' visibilities instead of overwriting them */
+    CORR_BATCH_PLANES = 8       /* allow the plane operand path: the batch allocates fp16 sample planes
+                                   for its jobs of more than 64 inputs (n_chan x ceil(N/64) x 128 x
+                                   Kp x 2 bytes each); jobs of at least plane_min_nb 64-input blocks
+                                   are unpacked into them and the tensor-core kernel reads the planes
+                                   instead of converting packed samples itself (tuned, or 4 blocks
+                                   when not tuned).  Results are identical either way. */
 };
 
 typedef struct {
@@ -335,20 +365,32 @@ typedef struct {
     double cmacs;               /* algorithmic CMACs of one run: sum of P * n_chan * n_time */
     int op_stages, pair_cpi, order;   /* the launch shape in use (0: default) */
     float tune_ms;              /* the tuner's best time, ms (0 if not tuned) */
+    int plane_min_nb;           /* jobs of at least this many blocks read planes (0: none) */
+    size_t plane_bytes;         /* the batch's plane workspace */
+    int wide;                   /* plane jobs run wide work items (see CORR_ITEMS_WIDE) */
 } corr_batch_stats;
 
 /*
  * Build a batch over jobs[0..n_jobs) (the library copies the descriptors; the caller
  * keeps the buffers alive).  flags: CORR_BATCH_* bits.  With CORR_BATCH_AUTOTUNE the
  * library runs the batch several times on its own buffers (overwriting the
- * visibilities) and keeps the fastest launch shape for this set of job sizes; with a
- * non-NULL tune_cache path the choice is read from / appended to that JSON-lines file.
+ * visibilities) and keeps the fastest launch shape for this set of job sizes (operand-ring
+ * depth, channels per item of single-block arrays, item order and, with CORR_BATCH_PLANES,
+ * the operand path per array size); with a non-NULL tune_cache path the choice is read from
+ * / appended to that JSON-lines file, keyed by the job sizes and the library build.
  * AUTOTUNE with ACCUMULATE is rejected (tuning runs would add into the accumulators).
  * With CORR_BATCH_GRAPH the launches are captured into a CUDA graph once.  Allocates a
  * small device status block and a stream.
  */
 corr_status corr_batch_create(corr_batch *out, const corr_job *jobs, int n_jobs, int flags,
                               const char *tune_cache);
+/* Set the launch shape directly instead of tuning it: op_stages (0 = default, up to 16),
+ * pair_cpi (channels per work item of single-block arrays, 1 or 2), order (0: costliest jobs'
+ * items first, 1: the caller's order), plane_min_nb (jobs of at least this many 64-input blocks
+ * read fp16 planes; 0 = none; > 0 needs CORR_BATCH_PLANES), wide (plane jobs: 1 = wide work
+ * items, 0 = single tiles).  A captured graph is re-captured.  Results are identical for every
+ * shape.  Not concurrent with corr_batch_run. */
+corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide);
 /* Run the batch on `stream` (graph replay when captured).  Asynchronous. */
 corr_status corr_batch_run(corr_batch b, void *stream);
 corr_status corr_batch_info(corr_batch b, corr_batch_stats *stats);
@@ -385,12 +427,16 @@ typedef struct {
                                  CORR_ECUDA, or CORR_EBUSY (cancelled at shutdown) */
     double t_submit, t_start, t_done;   /* host monotonic seconds */
     float gpu_ms;             /* stream time from the job's first copy to its last */
-    void *d_vis;              /* device result while the job keeps it (host_vis == NULL) */
+    void *d_vis;              /* device result while the job keeps it (host_vis == NULL), or the
+                                 open stream's averaged dump this job produced (see below) */
+    int closed_interval;      /* open streams: 1 if this job ended a dump interval */
+    int64_t n_accum;          /* open streams, closing jobs: samples summed in the dump */
 } corr_job_result;
 
 typedef struct {
     int64_t submitted, completed, failed, rejected, cancelled, queued, running;
     size_t arena_bytes, bytes_in_use, peak_bytes;
+    int64_t open_streams;     /* streams with device state (corr_server_open_stream) */
 } corr_server_stats;
 
 enum { CORR_SERVER_START_PAUSED = 1 };   /* admit nothing until corr_server_resume */
@@ -416,6 +462,58 @@ corr_status corr_server_get_stats(corr_server s, corr_server_stats *st);
 /* Cancel queued jobs, wait up to drain_timeout_s for running ones (CORR_ETIMEOUT if some
  * are still running; the streams are then synchronised before memory is freed). */
 corr_status corr_server_destroy(corr_server s, double drain_timeout_s);
+/*
+ * ---- Per-stream device state: sample rings and accumulators kept on the device ----
+ *
+ * The correlator integrates: every batch of samples is added into accumulators, which are
+ * read out at the end of a dump interval, divided by the number of times they were updated
+ * and reset (Fig. 1).  corr_server_open_stream gives one input stream (a stream_tag) that state
+ * on the device, admitted once against the HBM budget instead of per job:
+ *   - a ring of ring_slots sample slots: job k of the stream is copied into slot k mod
+ *     ring_slots as soon as the X stage of job k - ring_slots has read that slot, so copies of
+ *     later jobs run ahead of the X stage of earlier ones;
+ *   - accumulators [n_chan][P][2] (int64 for 4/8-bit samples, float32 for float samples) that
+ *     every job of the stream adds into, in submission order (one CUDA stream per open stream);
+ *   - at every jobs_per_dump-th job the interval ends:
+ *       CORR_STREAM_DUMP_SUMS      the accumulated sums are copied to that job's host_vis (the
+ *                                  exact integer sums for 4/8-bit samples; host_vis must not be
+ *                                  NULL for such a job, CORR_EINVAL at submission otherwise) and
+ *                                  the next interval's first job overwrites them;
+ *       CORR_STREAM_DUMP_AVERAGED  the dump step (corr_dump) divides by the samples summed
+ *                                  (jobs_per_dump x n_time), applies the phase correction when
+ *                                  d_delays is given and writes float32 [n_chan][P][2] into a
+ *                                  device dump buffer (the next interval's first job overwrites
+ *                                  the accumulators, which resets them);
+ *                                  copied to the closing job's host_vis when it is not NULL, else
+ *                                  left there (corr_job_result.d_vis) until the stream's next
+ *                                  dump overwrites it.
+ * The stream's CUDA streams get a priority from its dump length (shorter dumps, tighter
+ * deadlines: higher priority), which orders kernels of different streams when the GPU is busy.
+ * Jobs submitted with that stream_tag must have the stream's shape (CORR_EINVAL otherwise); they
+ * need no arena space of their own and are issued as soon as they reach the mailbox, never held
+ * behind a job waiting for memory.  Results of such jobs other than the closing one carry no
+ * visibilities (host_vis is ignored).  CORR_EBUSY if the stream's state does not fit the arena's
+ * free space now; CORR_EINVAL if the tag is already open or the description is invalid.  d_delays
+ * (float64 [n_inputs], seconds) and d_freqs (float64 [n_chan], Hz) are device arrays the caller
+ * keeps alive while the stream is open (averaged mode only; NULL: averaging only).
+ */
+enum { CORR_STREAM_DUMP_SUMS = 0, CORR_STREAM_DUMP_AVERAGED = 1 };
+
+typedef struct {
+    int n_inputs, n_chan, n_time, sample_bits;   /* every job of the stream has this shape */
+    int ring_slots;           /* device sample slots, >= 1 */
+    int jobs_per_dump;        /* jobs accumulated into one dump interval, >= 1 */
+    int dump_mode;            /* CORR_STREAM_DUMP_SUMS or CORR_STREAM_DUMP_AVERAGED */
+    const double *d_delays;   /* averaged mode: per-input delays (device) or NULL */
+    const double *d_freqs;    /* averaged mode: channel frequencies (device), with d_delays */
+} corr_stream_desc;
+
+corr_status corr_server_open_stream(corr_server s, int stream_tag, const corr_stream_desc *desc);
+/* Stop taking jobs for the tag, wait up to drain_timeout_s for its jobs to finish (CORR_ETIMEOUT
+ * if some are still running; they are then waited for on the GPU before the state is freed), and
+ * return the stream's device state to the arena.  An interval left open is discarded. */
+corr_status corr_server_close_stream(corr_server s, int stream_tag, double drain_timeout_s);
+
 /* Page-locked host memory for job buffers (cudaMallocHost). */
 corr_status corr_host_alloc(void **ptr, size_t bytes);
 corr_status corr_host_free(void *ptr);

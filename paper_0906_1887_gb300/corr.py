@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libcorr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, PENDING, EUNSUPPORTED = range(8)
 ENGINE_TC, ENGINE_FP32, ENGINE_BF16X3 = 0, 1, 2
+OPERANDS_AUTO, OPERANDS_PACKED, OPERANDS_PLANES = 0, 1, 2
+ITEMS_AUTO, ITEMS_TILES, ITEMS_WIDE = 0, 1, 2
 F_COMPLEX8, F_COMPLEX4, F_REAL8 = 0, 1, 2
 STATUS_NAMES = {OK: "CORR_OK", EINVAL: "CORR_EINVAL", ENOMEM: "CORR_ENOMEM", ECUDA: "CORR_ECUDA",
                 EBUSY: "CORR_EBUSY", ETIMEOUT: "CORR_ETIMEOUT", PENDING: "CORR_PENDING",
@@ -33,8 +35,10 @@ SIGNATURES = {
     "corr_plan_destroy": (_c_int, [_vp]),
     "corr_plan_info": (_c_int, [_vp, _P(_c_i64), _P(_c_sz), _P(_c_sz)]),
     "corr_plan_set_tuning": (_c_int, [_vp, _c_int, _c_int]),
+    "corr_plan_set_operands": (_c_int, [_vp, _c_int, _c_int]),
     "corr_workspace_size": (_c_int, [_vp, _c_int, _c_int, _P(_c_sz)]),
     "corr_unpack": (_c_int, [_vp, _vp, _c_int, _vp, _vp]),
+    "corr_planes_size": (_c_int, [_vp, _c_int, _P(_c_sz)]),
     "corr_xengine_run": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_batch": (_c_int, [_vp, _vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
     "corr_xengine_run_planes": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _c_int, _vp]),
@@ -45,6 +49,7 @@ SIGNATURES = {
     "corr_selftest_stall": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _P(_c_int)]),
     "corr_batch_create": (_c_int, [_P(_vp), _vp, _c_int, _c_int, ctypes.c_char_p]),
     "corr_batch_run": (_c_int, [_vp, _vp]),
+    "corr_batch_set_shape": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int]),
     "corr_batch_info": (_c_int, [_vp, _vp]),
     "corr_batch_check": (_c_int, [_vp, _P(_c_int)]),
     "corr_batch_destroy": (_c_int, [_vp]),
@@ -57,6 +62,8 @@ SIGNATURES = {
     "corr_server_resume": (_c_int, [_vp]),
     "corr_server_get_stats": (_c_int, [_vp, _vp]),
     "corr_server_destroy": (_c_int, [_vp, ctypes.c_double]),
+    "corr_server_open_stream": (_c_int, [_vp, _c_int, _vp]),
+    "corr_server_close_stream": (_c_int, [_vp, _c_int, ctypes.c_double]),
     "corr_host_alloc": (_c_int, [_P(_vp), _c_sz]),
     "corr_host_free": (_c_int, [_vp]),
     "corr_dump_workspace_size": (_c_int, [_vp, _P(_c_sz)]),
@@ -232,9 +239,20 @@ class Plan:
         results do not depend on either."""
         check(lib().corr_plan_set_tuning(self._h, op_stages, float_planes), "corr_plan_set_tuning")
 
+    def set_operands(self, operands: int = OPERANDS_AUTO, items: int = ITEMS_AUTO):
+        """Operand feed of the tensor-core engine (packed samples or fp16 planes) and the plane
+        feed's work-item shape; results do not depend on either."""
+        check(lib().corr_plan_set_operands(self._h, operands, items), "corr_plan_set_operands")
+
     def workspace_size(self, engine: int, n_dumps: int = 1) -> int:
         b = ctypes.c_size_t()
         check(lib().corr_workspace_size(self._h, engine, n_dumps, ctypes.byref(b)), "corr_workspace_size")
+        return b.value
+
+    def planes_size(self, n_dumps: int = 1) -> int:
+        """Bytes of the sample planes corr_unpack writes for n_dumps dumps."""
+        b = ctypes.c_size_t()
+        check(lib().corr_planes_size(self._h, n_dumps, ctypes.byref(b)), "corr_planes_size")
         return b.value
 
     def unpack(self, packed, planes, n_dumps: int = 1, stream=None):
@@ -295,10 +313,11 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("n_jobs", ctypes.c_int), ("n_launches", ctypes.c_int), ("graph", ctypes.c_int),
                 ("tuned", ctypes.c_int), ("n_items", ctypes.c_int64), ("cmacs", ctypes.c_double),
                 ("op_stages", ctypes.c_int), ("pair_cpi", ctypes.c_int), ("order", ctypes.c_int),
-                ("tune_ms", ctypes.c_float)]
+                ("tune_ms", ctypes.c_float), ("plane_min_nb", ctypes.c_int), ("plane_bytes", ctypes.c_size_t),
+                ("wide", ctypes.c_int)]
 
 
-BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_ACCUMULATE = 1, 2, 4
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_ACCUMULATE, BATCH_PLANES = 1, 2, 4, 8
 
 
 class Batch:
@@ -319,6 +338,11 @@ class Batch:
 
     def run(self, stream=None):
         check(lib().corr_batch_run(self._h, _stream_handle(stream)), "corr_batch_run")
+
+    def set_shape(self, op_stages: int = 0, pair_cpi: int = 2, order: int = 0, plane_min_nb: int = 0, wide: int = 1):
+        """Launch shape chosen by the caller instead of the tuner (results do not depend on it)."""
+        check(lib().corr_batch_set_shape(self._h, op_stages, pair_cpi, order, plane_min_nb, wide),
+              "corr_batch_set_shape")
 
     def info(self) -> dict:
         st = BatchStats()
@@ -352,14 +376,24 @@ class ServerJob(ctypes.Structure):
 
 class JobResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_float), ("d_vis", ctypes.c_void_p)]
+                ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_float), ("d_vis", ctypes.c_void_p),
+                ("closed_interval", ctypes.c_int), ("n_accum", ctypes.c_int64)]
+
+
+class StreamDesc(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int), ("n_chan", ctypes.c_int), ("n_time", ctypes.c_int),
+                ("sample_bits", ctypes.c_int), ("ring_slots", ctypes.c_int), ("jobs_per_dump", ctypes.c_int),
+                ("dump_mode", ctypes.c_int), ("d_delays", ctypes.c_void_p), ("d_freqs", ctypes.c_void_p)]
+
+
+STREAM_DUMP_SUMS, STREAM_DUMP_AVERAGED = 0, 1
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rejected", ctypes.c_int64), ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("running", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
-                ("peak_bytes", ctypes.c_size_t)]
+                ("peak_bytes", ctypes.c_size_t), ("open_streams", ctypes.c_int64)]
 
 
 SERVER_START_PAUSED = 1
@@ -373,12 +407,30 @@ class Server:
         check(lib().corr_server_create(ctypes.byref(h), int(hbm_budget_bytes), n_streams, flags),
               "corr_server_create")
         self._h = h
+        self._keep_stream = {}
 
     def submit(self, n_inputs, n_chan, n_time, sample_bits, host_packed, host_vis=None, stream_tag=0) -> int:
         d = ServerJob(n_inputs, n_chan, n_time, sample_bits, _ptr(host_packed), _ptr(host_vis), stream_tag)
         jid = ctypes.c_uint64(0)
         check(lib().corr_submit(self._h, ctypes.byref(d), ctypes.byref(jid)), "corr_submit")
         return jid.value
+
+    def open_stream(self, stream_tag: int, n_inputs: int, n_chan: int, n_time: int, sample_bits: int,
+                    ring_slots: int = 4, jobs_per_dump: int = 1, dump_mode: int = STREAM_DUMP_SUMS,
+                    delays=None, freqs=None):
+        """Give stream_tag device state: a ring of sample slots and accumulators its jobs add into,
+        dumped every jobs_per_dump jobs (delays/freqs: float64 device tensors, averaged mode)."""
+        d = StreamDesc(n_inputs, n_chan, n_time, sample_bits, ring_slots, jobs_per_dump, dump_mode,
+                       _ptr(delays), _ptr(freqs))
+        self._keep_stream[stream_tag] = (delays, freqs)
+        check(lib().corr_server_open_stream(self._h, stream_tag, ctypes.byref(d)), "corr_server_open_stream")
+
+    def close_stream(self, stream_tag: int, drain_timeout_s: float = 30.0) -> int:
+        st = lib().corr_server_close_stream(self._h, stream_tag, float(drain_timeout_s))
+        if st == EINVAL:
+            check(st, "corr_server_close_stream")
+        self._keep_stream.pop(stream_tag, None)
+        return st
 
     def poll(self, job_id: int):
         r = JobResult()

@@ -1,5 +1,5 @@
 // Batched X stage: many uneven correlation jobs in one persistent tensor-core launch per
-// sample mode, optionally autotuned and captured in a CUDA graph.
+// sample mode and operand path, optionally autotuned and captured in a CUDA graph.
 //
 // The paper runs large batches per GPU call so that launch and transfer overhead vanish
 // (Sec. 4, Sec. 5: no gain beyond ~20 batches of samples).  Here the batch is across
@@ -7,11 +7,21 @@
 // flat list of work items walked by one grid of persistent CTAs, so small jobs no longer
 // pay a launch each and large ones no longer leave SMs idle at their tail.
 //
+// Operand path: the tensor-core kernel either converts packed samples itself (converter
+// warps, the samples cross HBM once) or reads fp16 sample planes that the unpack kernel wrote
+// first.  The first converts every 64-input block once per tile it meets, i.e. about nb/2
+// times per channel for an array of nb blocks; the second converts each block once and
+// spends HBM traffic on the planes instead.  Arrays of many blocks with long dumps are
+// compute-heavy and run faster from planes; with CORR_BATCH_PLANES the batch owns a plane
+// workspace and jobs of at least plane_min_nb blocks take that path.
+//
 // Autotuning: per job-set signature the tuner times each candidate launch shape
-// (operand-ring depth, channels per work item for single-block arrays, item order) on the
-// batch's own buffers and keeps the fastest; results are cached in memory and, when a
-// cache path is given, in a JSON-lines file.
+// (operand-ring depth, channels per work item for single-block arrays, item order, and with
+// planes allowed the block count from which jobs take the plane path) on the batch's own
+// buffers and keeps the fastest; results are cached in memory and, when a cache path is
+// given, in a JSON-lines file, keyed by the job sizes and this library's build.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -30,17 +40,24 @@ struct TuneChoice {
     int op_stages = 0;   // 0: default
     int pair_cpi = 2;    // channels per item for arrays of <= 64 inputs
     int order = 0;       // 0: items of the costliest jobs first; 1: jobs in the caller's order
+    int plane_min_nb = 0;   // jobs of at least this many 64-input blocks read fp16 planes (0: none)
+    int wide = 1;           // plane jobs: wide items (block I against J, J + 1 in one MMA)
     float ms = 0.f;
 };
+
+// The build this file was compiled in: tuning results of another build are not reused.
+constexpr const char* kBuildStamp = __DATE__ " " __TIME__;
 
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
 
 struct ModeGroup {
     int bits = 0;
+    bool planes = false;                  // jobs read fp16 planes the unpack kernel writes first
     std::vector<int> job_index;           // caller's job indices in this group
     std::vector<TcJobSpec> specs;         // launch order
     std::vector<CUtensorMap> maps;
+    std::vector<CUtensorMap> maps_wide;   // plane jobs with wide items
     TcTuning tune{};
 };
 
@@ -62,6 +79,10 @@ struct corr_batch_s {
     int64_t items = 0;
     corr::TuneChoice choice;
     bool tuned = false;
+    bool allow_planes = false;
+    char* d_planes = nullptr;             // plane workspace of the multi-block jobs
+    std::vector<size_t> plane_off;        // per job: offset in d_planes (SIZE_MAX: none)
+    size_t plane_bytes = 0;
 };
 
 namespace corr {
@@ -73,45 +94,82 @@ double job_cost_per_item(const corr_job& j, int cpi) {
     return (double)nkb * (nb == 1 ? cpi : 2);
 }
 
+int blocks_of(const corr_job& j) { return (j.n_inputs + kBlockInputs - 1) / kBlockInputs; }
+
+Plan plan_of_job(const corr_job& j, int n_sm) {
+    Plan p;
+    p.n_inputs = j.n_inputs;
+    p.n_chan = j.n_chan;
+    p.n_time = j.n_time;
+    p.sample_bits = j.sample_bits;
+    p.nb = blocks_of(j);
+    p.kp = (j.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    p.n_baselines = n_baselines(j.n_inputs);
+    p.n_sm = n_sm;
+    return p;
+}
+
+bool takes_planes(const corr_batch_s* b, const TuneChoice& ch, int k) {
+    return ch.plane_min_nb > 0 && b->d_planes && b->plane_off[k] != SIZE_MAX &&
+           blocks_of(b->jobs[k]) >= ch.plane_min_nb;
+}
+
 // (Re)build the launch groups for a tuning choice.
 bool build_groups(corr_batch_s* b, const TuneChoice& ch) {
     b->groups.clear();
     b->items = 0;
     for (int bits : {8, 4}) {
-        ModeGroup g;
-        g.bits = bits;
-        for (int k = 0; k < (int)b->jobs.size(); ++k)
-            if (b->jobs[k].sample_bits == bits) g.job_index.push_back(k);
-        if (g.job_index.empty()) continue;
-        auto cpi_of = [&](const corr_job& j) { return j.n_inputs <= kBlockInputs ? ch.pair_cpi : 1; };
-        if (ch.order == 0)
-            std::stable_sort(g.job_index.begin(), g.job_index.end(), [&](int x, int y) {
-                return job_cost_per_item(b->jobs[x], cpi_of(b->jobs[x])) >
-                       job_cost_per_item(b->jobs[y], cpi_of(b->jobs[y]));
-            });
-        for (int k : g.job_index) {
-            const corr_job& j = b->jobs[k];
-            TcJobSpec sp{j.n_inputs, j.n_chan, j.n_time, 1, j.sample_bits, j.packed, j.vis, cpi_of(j)};
-            CUtensorMap m;
-            if (!tc_make_raw_map(&m, sp)) return false;
-            g.specs.push_back(sp);
-            g.maps.push_back(m);
-            const int nb = (j.n_inputs + kBlockInputs - 1) / kBlockInputs;
-            b->items += (int64_t)((j.n_chan + sp.cpi - 1) / sp.cpi) * (nb * (nb + 1) / 2);
+        for (bool planes : {false, true}) {
+            ModeGroup g;
+            g.bits = bits;
+            g.planes = planes;
+            for (int k = 0; k < (int)b->jobs.size(); ++k)
+                if (b->jobs[k].sample_bits == bits && takes_planes(b, ch, k) == planes) g.job_index.push_back(k);
+            if (g.job_index.empty()) continue;
+            auto cpi_of = [&](const corr_job& j) { return !planes && j.n_inputs <= kBlockInputs ? ch.pair_cpi : 1; };
+            if (ch.order == 0)
+                std::stable_sort(g.job_index.begin(), g.job_index.end(), [&](int x, int y) {
+                    return job_cost_per_item(b->jobs[x], cpi_of(b->jobs[x])) >
+                           job_cost_per_item(b->jobs[y], cpi_of(b->jobs[y]));
+                });
+            for (int k : g.job_index) {
+                const corr_job& j = b->jobs[k];
+                const void* data = planes ? static_cast<const void*>(b->d_planes + b->plane_off[k]) : j.packed;
+                TcJobSpec sp{j.n_inputs, j.n_chan, j.n_time, 1, j.sample_bits, data, j.vis, cpi_of(j)};
+                CUtensorMap m, mw{};
+                if (!(planes ? tc_make_plane_map(&m, sp) : tc_make_raw_map(&m, sp))) return false;
+                const int nb = blocks_of(j);
+                if (planes && ch.wide && nb >= 2 && tc_make_plane_map_wide(&mw, sp)) sp.tw = 2;
+                g.specs.push_back(sp);
+                g.maps.push_back(m);
+                g.maps_wide.push_back(mw);
+                const int per_chan = sp.tw == 2 ? ((nb + 1) / 2) * ((nb + 2) / 2) : nb * (nb + 1) / 2;
+                b->items += (int64_t)((j.n_chan + sp.cpi - 1) / sp.cpi) * per_chan;
+            }
+            g.tune.op_stages = ch.op_stages;
+            b->groups.push_back(std::move(g));
         }
-        g.tune.op_stages = ch.op_stages;
-        b->groups.push_back(std::move(g));
     }
     return true;
 }
 
 cudaError_t launch_groups(corr_batch_s* b, cudaStream_t s) {
     for (auto& g : b->groups) {
+        if (g.planes)   // the unpack of every plane job first (each writes its own planes)
+            for (size_t i = 0; i < g.job_index.size(); ++i) {
+                const corr_job& j = b->jobs[g.job_index[i]];
+                const Plan p = plan_of_job(j, b->n_sm);
+                cudaError_t e = launch_unpack_fp16(p, j.packed, 1, const_cast<void*>(g.specs[i].data), s);
+                if (e != cudaSuccess) return e;
+            }
         // at most kMaxJobs jobs per launch
         for (size_t k0 = 0; k0 < g.specs.size(); k0 += kMaxJobsPerLaunch) {
             const int n = (int)std::min(g.specs.size() - k0, (size_t)kMaxJobsPerLaunch);
-            cudaError_t e = launch_xeng_tc_raw_jobs(g.specs.data() + k0, g.maps.data() + k0, n, b->accumulate,
-                                                    b->d_status, b->n_sm, g.tune, s);
+            cudaError_t e = g.planes ? launch_xeng_tc_plane_jobs(g.specs.data() + k0, g.maps.data() + k0, n,
+                                                                 b->accumulate, b->d_status, b->n_sm, g.tune, s,
+                                                                 g.maps_wide.data() + k0)
+                                     : launch_xeng_tc_raw_jobs(g.specs.data() + k0, g.maps.data() + k0, n,
+                                                               b->accumulate, b->d_status, b->n_sm, g.tune, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -120,6 +178,7 @@ cudaError_t launch_groups(corr_batch_s* b, cudaStream_t s) {
 
 std::string signature(const corr_batch_s* b) {
     std::vector<std::string> parts;
+    parts.push_back(std::string("build ") + kBuildStamp + (b->allow_planes ? " planes" : " raw"));
     for (const auto& j : b->jobs) {
         char buf[96];
         snprintf(buf, sizeof(buf), "%d:%d:%d:%d", j.sample_bits, j.n_inputs, j.n_chan, j.n_time);
@@ -149,6 +208,8 @@ void load_cache_file(const char* path) {
         if ((p = strstr(k1, "\"op_stages\": "))) c.op_stages = atoi(p + 13);
         if ((p = strstr(k1, "\"pair_cpi\": "))) c.pair_cpi = atoi(p + 12);
         if ((p = strstr(k1, "\"order\": "))) c.order = atoi(p + 9);
+        if ((p = strstr(k1, "\"plane_min_nb\": "))) c.plane_min_nb = atoi(p + 16);
+        if ((p = strstr(k1, "\"wide\": "))) c.wide = atoi(p + 8);
         if ((p = strstr(k1, "\"ms\": "))) c.ms = (float)atof(p + 6);
         if (c.pair_cpi != 1 && c.pair_cpi != 2) continue;
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -161,8 +222,10 @@ void append_cache_file(const char* path, const std::string& key, const TuneChoic
     if (!path || !*path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"op_stages\": %d, \"pair_cpi\": %d, \"order\": %d, \"ms\": %.6f}\n", key.c_str(),
-            c.op_stages, c.pair_cpi, c.order, c.ms);
+    fprintf(f,
+            "{\"key\": \"%s\", \"op_stages\": %d, \"pair_cpi\": %d, \"order\": %d, \"plane_min_nb\": %d, "
+            "\"wide\": %d, \"ms\": %.6f}\n",
+            key.c_str(), c.op_stages, c.pair_cpi, c.order, c.plane_min_nb, c.wide, c.ms);
     fclose(f);
 }
 
@@ -207,17 +270,29 @@ corr_status autotune(corr_batch_s* b, const char* cache_path) {
         }
     }
     bool any_small = false;
-    for (const auto& j : b->jobs) any_small = any_small || j.n_inputs <= kBlockInputs;
+    int max_nb = 1;
+    for (const auto& j : b->jobs) {
+        any_small = any_small || j.n_inputs <= kBlockInputs;
+        max_nb = std::max(max_nb, blocks_of(j));
+    }
+    std::vector<int> plane_opts{0};
+    if (b->d_planes)
+        for (int nb : {2, 4, 8, 16})
+            if (nb <= max_nb) plane_opts.push_back(nb);
     std::vector<TuneChoice> cands;
     for (int order : {0, 1})
         for (int cpi : any_small ? std::vector<int>{2, 1} : std::vector<int>{2})
-            for (int ops : {3, 4, 5}) {
-                TuneChoice c;
-                c.op_stages = ops;
-                c.pair_cpi = cpi;
-                c.order = order;
-                cands.push_back(c);
-            }
+            for (int ops : {3, 4, 5})
+                for (int pm : plane_opts)
+                    for (int wide : pm ? std::vector<int>{1, 0} : std::vector<int>{1}) {
+                        TuneChoice c;
+                        c.op_stages = ops;
+                        c.pair_cpi = cpi;
+                        c.order = order;
+                        c.plane_min_nb = pm;
+                        c.wide = wide;
+                        cands.push_back(c);
+                    }
     TuneChoice best;
     float best_ms = 1e30f;
     cudaStream_t s = b->own_stream;
@@ -240,6 +315,22 @@ corr_status autotune(corr_batch_s* b, const char* cache_path) {
     }
     append_cache_file(cache_path, key, best);
     return build_groups(b, best) ? CORR_OK : set_error(CORR_EINVAL, "tensor map encoding failed");
+}
+
+// Capture the batch's launches into a CUDA graph (one eager run first sets the kernels'
+// shared-memory attributes outside the capture).
+cudaError_t capture_graph(corr_batch_s* b) {
+    cudaError_t e = launch_groups(b, b->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->own_stream);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->own_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t el = launch_groups(b, b->own_stream);
+        e = cudaStreamEndCapture(b->own_stream, &b->g);
+        if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gx, b->g, 0);
+    if (e == cudaSuccess) b->graph = true;
+    return e;
 }
 
 }  // namespace
@@ -281,6 +372,26 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
         corr_batch_destroy(b);
         return cuda_error(e, "corr_batch_create");
     }
+    // plane workspace: one set of fp16 planes per multi-block job, owned by the batch
+    b->plane_off.assign(n_jobs, SIZE_MAX);
+    if (flags & CORR_BATCH_PLANES) {
+        b->allow_planes = true;
+        size_t total = 0;
+        for (int k = 0; k < n_jobs; ++k) {
+            const Plan p = plan_of_job(b->jobs[k], b->n_sm);
+            if (p.nb < 2) continue;
+            b->plane_off[k] = total;
+            total += (planes_bytes(p, 1) + 255) / 256 * 256;
+        }
+        if (total) {
+            e = cudaMalloc((void**)&b->d_planes, total);
+            if (e != cudaSuccess) {
+                corr_batch_destroy(b);
+                return set_error(CORR_ENOMEM, "cudaMalloc(%zu) of the batch's plane workspace failed", total);
+            }
+            b->plane_bytes = total;
+        }
+    }
     corr_status st = CORR_OK;
     if ((flags & CORR_BATCH_AUTOTUNE) && (flags & CORR_BATCH_ACCUMULATE)) {
         corr_batch_destroy(b);
@@ -289,31 +400,53 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
     }
     if (flags & CORR_BATCH_AUTOTUNE) {
         st = autotune(b, tune_cache);
-    } else if (!build_groups(b, TuneChoice{})) {
-        st = set_error(CORR_EINVAL, "tensor map encoding failed");
+    } else {
+        TuneChoice def;
+        if (b->d_planes) def.plane_min_nb = 4;   // untuned: arrays of 256 inputs and more read planes
+        b->choice = def;
+        if (!build_groups(b, def)) st = set_error(CORR_EINVAL, "tensor map encoding failed");
     }
     if (st != CORR_OK) {
         corr_batch_destroy(b);
         return st;
     }
     if (flags & CORR_BATCH_GRAPH) {
-        // one eager run sets the kernels' shared-memory attributes outside the capture
-        e = launch_groups(b, b->own_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->own_stream);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->own_stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t el = launch_groups(b, b->own_stream);
-            e = cudaStreamEndCapture(b->own_stream, &b->g);
-            if (el != cudaSuccess) e = el;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gx, b->g, 0);
+        e = capture_graph(b);
         if (e != cudaSuccess) {
             corr_batch_destroy(b);
             return cuda_error(e, "CUDA graph capture of the batch");
         }
-        b->graph = true;
     }
     *out = b;
+    return CORR_OK;
+}
+
+corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide) {
+    if (!b) return set_error(CORR_EINVAL, "corr_batch_set_shape: NULL batch");
+    if (op_stages < 0 || op_stages > 16 || (pair_cpi != 1 && pair_cpi != 2) || (order != 0 && order != 1) ||
+        plane_min_nb < 0 || (wide != 0 && wide != 1))
+        return set_error(CORR_EINVAL, "corr_batch_set_shape: op_stages in [0, 16], pair_cpi 1 or 2, order 0 or 1, "
+                                      "plane_min_nb >= 0, wide 0 or 1");
+    if (plane_min_nb > 0 && !b->d_planes)
+        return set_error(CORR_EINVAL, "plane_min_nb > 0 needs a batch created with CORR_BATCH_PLANES");
+    TuneChoice c;
+    c.op_stages = op_stages;
+    c.pair_cpi = pair_cpi;
+    c.order = order;
+    c.plane_min_nb = plane_min_nb;
+    c.wide = wide;
+    if (!build_groups(b, c)) return set_error(CORR_EINVAL, "tensor map encoding failed");
+    b->choice = c;
+    b->tuned = false;
+    if (b->graph) {
+        if (b->gx) cudaGraphExecDestroy(b->gx);
+        if (b->g) cudaGraphDestroy(b->g);
+        b->gx = nullptr;
+        b->g = nullptr;
+        b->graph = false;
+        const cudaError_t e = capture_graph(b);
+        if (e != cudaSuccess) return cuda_error(e, "CUDA graph capture of the batch");
+    }
     return CORR_OK;
 }
 
@@ -340,6 +473,9 @@ corr_status corr_batch_info(corr_batch b, corr_batch_stats* st) {
     st->pair_cpi = b->choice.pair_cpi;
     st->order = b->choice.order;
     st->tune_ms = b->choice.ms;
+    st->plane_min_nb = b->choice.plane_min_nb;
+    st->wide = b->choice.wide;
+    st->plane_bytes = b->plane_bytes;
     return CORR_OK;
 }
 
@@ -361,6 +497,7 @@ corr_status corr_batch_destroy(corr_batch b) {
     if (b->g) cudaGraphDestroy(b->g);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     if (b->d_status) cudaFree(b->d_status);
+    if (b->d_planes) cudaFree(b->d_planes);
     delete b;
     return CORR_OK;
 }

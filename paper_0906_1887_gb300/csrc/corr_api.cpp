@@ -124,17 +124,33 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
     return CORR_OK;
 }
 
+corr_status corr_plan_set_operands(corr_plan plan, int operands, int items) {
+    if (!plan) return set_error(CORR_EINVAL, "corr_plan_set_operands: plan is NULL");
+    if (operands < CORR_OPERANDS_AUTO || operands > CORR_OPERANDS_PLANES)
+        return set_error(CORR_EINVAL, "operands=%d is not a CORR_OPERANDS_* value", operands);
+    if (items < CORR_ITEMS_AUTO || items > CORR_ITEMS_WIDE)
+        return set_error(CORR_EINVAL, "items=%d is not a CORR_ITEMS_* value", items);
+    Plan* p = reinterpret_cast<Plan*>(plan);
+    if (operands == CORR_OPERANDS_PACKED && !tc_raw_supported(*p))
+        return set_error(CORR_EUNSUPPORTED, "packed rows of %d inputs are not 16-byte multiples: planes only",
+                         p->n_inputs);
+    p->tc_operands = operands;
+    p->tc_items = items;
+    return CORR_OK;
+}
+
 corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t* bytes) {
     if (!plan || !bytes) return set_error(CORR_EINVAL, "corr_workspace_size: NULL argument");
     if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
     const Plan* p = reinterpret_cast<const Plan*>(plan);
     switch (engine) {
         case CORR_ENGINE_TC:
-            // packed samples feed the tensor-core kernel directly when TMA can address them
-            *bytes = tc_raw_supported(*p) ? 0 : planes_bytes(*p, n_dumps);
+            // fp16 planes when the kernel reads planes (required where TMA cannot address the
+            // packed rows; optional otherwise: without a workspace it converts packed samples)
+            *bytes = tc_use_planes(*p) ? planes_bytes(*p, n_dumps) : 0;
             return CORR_OK;
         case CORR_ENGINE_FP32:
-            *bytes = planes_bytes(*p, n_dumps);
+            *bytes = 0;   // reads the packed samples directly
             return CORR_OK;
         case CORR_ENGINE_BF16X3:
             // hi and lo bf16 planes, unless the tensor-core kernel splits the floats itself
@@ -145,6 +161,13 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t*
         default:
             return set_error(CORR_EINVAL, "unknown engine %d", engine);
     }
+}
+
+corr_status corr_planes_size(corr_plan plan, int n_dumps, size_t* bytes) {
+    if (!plan || !bytes) return set_error(CORR_EINVAL, "corr_planes_size: NULL argument");
+    if (n_dumps < 1) return set_error(CORR_EINVAL, "n_dumps=%d must be >= 1", n_dumps);
+    *bytes = planes_bytes(*reinterpret_cast<const Plan*>(plan), n_dumps);
+    return CORR_OK;
 }
 
 corr_status corr_unpack(corr_plan plan, const void* d_packed, int n_dumps, void* d_planes, void* stream) {
@@ -172,21 +195,24 @@ corr_status corr_xengine_run_batch(corr_plan plan, const void* d_packed, int n_d
     size_t need = 0;
     corr_status st = corr_workspace_size(plan, engine, n_dumps, &need);
     if (st != CORR_OK) return st;
-    if (need && !d_workspace) return set_error(CORR_EINVAL, "engine %d needs %zu bytes of workspace", engine, need);
+    // the tensor-core engine's planes are optional where the kernel can read the packed rows
+    // itself (the automatic choice), so a NULL workspace takes the fused path there
+    const bool tc_fused_ok = engine == CORR_ENGINE_TC && p->sample_bits != 32 && tc_raw_supported(*p) &&
+                             p->tc_operands != 2;
+    if (need && !d_workspace && !tc_fused_ok)
+        return set_error(CORR_EINVAL, "engine %d needs %zu bytes of workspace", engine, need);
     cudaError_t e = cudaSuccess;
     if (engine == CORR_ENGINE_TC) {
         if (p->sample_bits == 32)
             return set_error(CORR_EUNSUPPORTED, "float samples run on CORR_ENGINE_BF16X3 or CORR_ENGINE_FP32");
-        if (tc_raw_supported(*p)) {
+        if (!d_workspace || !tc_use_planes(*p)) {
             e = launch_xeng_tc_raw(*p, d_packed, n_dumps, d_vis, accumulate, s);
         } else {
             e = launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
             if (e == cudaSuccess) e = launch_xeng_tc(*p, d_workspace, nullptr, n_dumps, d_vis, accumulate, s);
         }
     } else if (engine == CORR_ENGINE_FP32) {
-        e = p->sample_bits == 32 ? launch_unpack_f32(*p, d_packed, n_dumps, d_workspace, s)
-                                 : launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
-        if (e == cudaSuccess) e = launch_xeng_fp32(*p, d_workspace, n_dumps, d_vis, accumulate, s);
+        e = launch_xeng_fp32_packed(*p, d_packed, n_dumps, d_vis, accumulate, s);
     } else if (engine == CORR_ENGINE_BF16X3) {
         if (p->sample_bits != 32)
             return set_error(CORR_EUNSUPPORTED, "CORR_ENGINE_BF16X3 takes float samples (sample_bits=32)");

@@ -39,6 +39,8 @@ struct Plan {
     int* d_status = nullptr; // [4] device status words
     int tc_op_stages = 0;     // operand ring depth of the packed-sample kernel (0: default)
     int tc_float_planes = 0;  // BF16x3: 1 = hi/lo planes through memory even where the fused path applies
+    int tc_operands = 0;      // 4/8-bit, tensor cores: 0 auto, 1 packed samples (fused converters), 2 fp16 planes
+    int tc_items = 0;         // plane path: 0 auto (wide), 1 single tiles, 2 wide items
     // host-buffer pipeline (corr_xengine_run_host), created on first use
     char* pipe_dev = nullptr;   // 2 x (chunk inputs) + 2 x (chunk outputs) + workspace
     size_t pipe_bytes = 0;
@@ -64,10 +66,19 @@ cudaError_t launch_unpack_bf16x2(const Plan& p, const void* d_packed, int n_dump
                                  void* d_lo, cudaStream_t s);
 cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, void* d_vis,
                              int accumulate, cudaStream_t s);
+// FP32 engine on the packed samples themselves (4/8-bit or float32), no planes
+cudaError_t launch_xeng_fp32_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                                    cudaStream_t s);
 cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_planes_lo, int n_dumps,
                            void* d_vis, int accumulate, cudaStream_t s);
 // Fused path: packed 4/8-bit samples straight into the tensor-core kernel (no planes).
 bool tc_raw_supported(const Plan& p);
+// Whether the tensor-core X stage of 4/8-bit samples reads fp16 planes (written by the unpack
+// kernel into the workspace) rather than converting the packed samples itself: always when the
+// packed rows are not TMA-addressable; otherwise as the plan's knob says, by default for arrays
+// of at least kPlaneMinBlocks 64-input blocks, whose tiles re-read every block nb / 2 times.
+constexpr int kPlaneMinBlocks = 4;
+bool tc_use_planes(const Plan& p);
 bool tc_raw_supported(int n_inputs, int sample_bits);
 struct TcTuning;
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
@@ -82,6 +93,7 @@ struct TcJobSpec {
     int out_mode = 0;   // 1: dump mode, float32 [n_dumps][C][P][2] of V / n_accum * phasor_i conj(phasor_j)
     const void* phasor = nullptr;   // float2 [C][N] (device) or nullptr
     float inv_n = 1.0f;
+    int tw = 1;         // plane path: 2 = wide items (block I against blocks J, J + 1 in one MMA)
 };
 // Launch-shape knobs the autotuner chooses (0 = default).
 struct TcTuning {
@@ -101,6 +113,14 @@ cudaError_t launch_xeng_tc_raw_dump(const Plan& p, const void* d_packed, int n_d
 // Per-input phasors exp(+2 pi i nu_c tau_n) as float2 [C][N], formed in double precision.
 cudaError_t launch_phasors(const Plan& p, const double* d_delays, const double* d_freqs, void* d_g, cudaStream_t s);
 bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp);
+// Jobs whose samples the unpack kernel already turned into fp16 planes (TcJobSpec::data = the
+// planes, [n_dumps][C][NB][128][Kp]); one channel per work item.
+bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp);
+// the same planes in boxes of two adjacent blocks, for wide items (TcJobSpec::tw = 2)
+bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp);
+cudaError_t launch_xeng_tc_plane_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
+                                      int* status, int n_sm, const TcTuning& tune, cudaStream_t s,
+                                      const CUtensorMap* maps_wide = nullptr);
 // All jobs of one launch share a sample mode (4 or 8 bits) and must be TMA-addressable.
 cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
                                     int* status, int n_sm, const TcTuning& tune, cudaStream_t s);

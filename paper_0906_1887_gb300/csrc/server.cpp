@@ -2,18 +2,24 @@
 // footprint into a device arena, run asynchronously, polled by id.
 //
 // The paper's prototype overlaps staging of the next batch in host memory with the
-// CMAC of the previous one on the GPU (Sec. 5, Table 3 notes).  Here a dispatcher thread
-// takes jobs from a mailbox in arrival order, admits each when its device footprint
-// (packed samples + visibilities + any workspace) fits the free space of a fixed arena
-// allocated once at start-up, and issues on one of n_streams CUDA streams: the
-// host-to-device copy of the samples, the X-stage kernel, the readback of the kernel's
-// status words and, if the caller gave a host buffer, the device-to-host copy of the
-// visibilities.  Copies of one job overlap the kernels of others on the other streams.
-// A completion thread retires jobs as their events complete, frees their arena blocks
-// and wakes waiters.  All host waits are bounded; the kernels' own waits are bounded and
-// report through the status words.
+// CMAC of the previous one on the GPU (Sec. 5, Table 3 notes), and integrates: batches are
+// added into accumulators that are read out, divided by the update count and reset at each
+// dump (Fig. 1).  Here a dispatcher thread takes jobs from a mailbox in arrival order.  A job
+// of an input stream opened with corr_server_open_stream uses that stream's device state,
+// admitted once: a ring of sample slots and accumulators that its jobs add into, dumped
+// every jobs_per_dump jobs; such jobs are issued as soon as they arrive, on the stream's own
+// pair of CUDA streams (copy-in of job k into its ring slot waits only for the X stage of job
+// k - ring_slots).  Any other job is admitted when its device footprint (packed samples +
+// visibilities + any workspace) fits the free space of a fixed arena allocated once at
+// start-up, and is issued on one of n_streams CUDA streams: the host-to-device copy of the
+// samples, the X-stage kernel, the readback of the kernel's status words and, if the caller
+// gave a host buffer, the device-to-host copy of the visibilities.  Copies of one job overlap
+// the kernels of others.  A completion thread retires jobs as their events complete, frees
+// their arena blocks and wakes waiters.  All host waits are bounded; the kernels' own waits
+// are bounded and report through the status words.
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -89,6 +95,8 @@ private:
 
 enum JobState { kQueued, kRunning, kDone, kFailed, kCancelled };
 
+struct StreamState;
+
 struct Job {
     uint64_t id = 0;
     corr_job_desc desc{};
@@ -103,6 +111,29 @@ struct Job {
     int* h_status = nullptr;   // pinned host copy of the kernel status words
     float gpu_ms = 0.f;
     void* d_vis = nullptr;     // device result while the job keeps it
+    bool stream_job = false;   // runs on an open stream's device state
+    int64_t seq = 0;           // index of the job within its open stream
+    bool closes = false;       // ends a dump interval of its open stream
+    int64_t n_accum = 0;       // samples summed in that dump
+    StreamState* st = nullptr;  // the open stream's state (stream jobs)
+};
+
+// Device state of one open input stream (corr_server_open_stream).
+struct StreamState {
+    corr_stream_desc d{};
+    size_t off = 0, bytes = 0;           // arena block
+    size_t slot_bytes = 0;               // one ring slot (packed samples of one job)
+    char* slots = nullptr;               // [ring_slots] sample slots
+    int* status = nullptr;               // [ring_slots][4] kernel status words
+    char* acc = nullptr;                 // accumulators [C][P][2]
+    char* ws = nullptr;                  // sample planes when the kernel cannot read the packed layout
+    char* dumpbuf = nullptr;             // averaged mode: float32 [C][P][2]
+    char* phasor = nullptr;              // averaged mode with delays: float2 [C][N]
+    bool raw = false;
+    cudaStream_t copy_s = nullptr, comp_s = nullptr;
+    std::vector<cudaEvent_t> slot_full, slot_free;
+    int64_t n_submitted = 0, n_retired = 0;
+    bool closing = false;
 };
 
 size_t packed_bytes(const corr_job_desc& d) {
@@ -131,12 +162,46 @@ Plan plan_of(const corr_job_desc& d, int device, int n_sm) {
 // Device bytes a job occupies while it runs: status, packed samples, visibilities, workspace.
 size_t footprint(const corr_job_desc& d, bool* raw) {
     Plan p = plan_of(d, 0, 0);
-    // samples the tensor-core kernel reads as they are: packed integers it can address with TMA,
-    // and float samples of single-block arrays (split into bf16 hi/lo inside the kernel)
-    *raw = d.sample_bits == 32 ? tc_rawf32_supported(p) : tc_raw_supported(p);
+    // samples the tensor-core kernel reads as they are: packed integers it can address with TMA
+    // (unless the array is large enough for the plane feed to be faster), and float samples of
+    // single-block arrays (split into bf16 hi/lo inside the kernel)
+    *raw = d.sample_bits == 32 ? tc_rawf32_supported(p) : !tc_use_planes(p);
     size_t ws = 0;
     if (!*raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : planes_bytes(p, 1);
     return round_up(16) + round_up(packed_bytes(d)) + round_up(vis_bytes(d)) + round_up(ws);
+}
+
+corr_job_desc shape_of(const corr_stream_desc& sd) {
+    corr_job_desc d{};
+    d.n_inputs = sd.n_inputs;
+    d.n_chan = sd.n_chan;
+    d.n_time = sd.n_time;
+    d.sample_bits = sd.sample_bits;
+    return d;
+}
+
+// Carve an open stream's arena block: status words, ring slots, accumulators, workspace,
+// dump buffer and phasors.  Returns the bytes needed; with base != nullptr fills the pointers.
+size_t stream_layout(StreamState& st, char* base) {
+    const corr_job_desc d = shape_of(st.d);
+    Plan p = plan_of(d, 0, 0);
+    size_t ws = 0;
+    if (!st.raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : planes_bytes(p, 1);
+    const bool avg = st.d.dump_mode == CORR_STREAM_DUMP_AVERAGED;
+    st.slot_bytes = round_up(packed_bytes(d));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* ptr = base ? base + off : nullptr;
+        off += round_up(bytes);
+        return ptr;
+    };
+    st.status = reinterpret_cast<int*>(take((size_t)st.d.ring_slots * 16));
+    st.slots = take(st.slot_bytes * (size_t)st.d.ring_slots);
+    st.acc = take(vis_bytes(d));
+    st.ws = ws ? take(ws) : nullptr;
+    st.dumpbuf = avg ? take((size_t)n_baselines(d.n_inputs) * d.n_chan * 8) : nullptr;
+    st.phasor = (avg && st.d.d_delays) ? take((size_t)d.n_chan * d.n_inputs * 8) : nullptr;
+    return off;
 }
 
 }  // namespace
@@ -157,10 +222,27 @@ struct corr_server_s {
     bool stop = false, paused = false;
     std::thread dispatcher, completer;
     corr_server_stats stats{};
+    std::map<int, corr::StreamState*> open_streams;   // by stream_tag
 };
 
 namespace corr {
 namespace {
+
+// The X stage of one job into d_vis: packed samples straight into the tensor-core kernel
+// when it can read them, else through sample planes in d_ws.
+cudaError_t run_x(const Plan& p, const corr_job_desc& d, bool raw, const char* d_packed, void* d_vis, char* d_ws,
+                  int accumulate, cudaStream_t s) {
+    if (raw)
+        return d.sample_bits == 32 ? launch_xeng_tc_rawf32(p, d_packed, 1, d_vis, accumulate, s)
+                                   : launch_xeng_tc_raw(p, d_packed, 1, d_vis, accumulate, s);
+    if (d.sample_bits == 32) {
+        const size_t half = (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2;
+        cudaError_t e = launch_unpack_bf16x2(p, d_packed, 1, d_ws, d_ws + half, s);
+        return e == cudaSuccess ? launch_xeng_tc(p, d_ws, d_ws + half, 1, d_vis, accumulate, s) : e;
+    }
+    cudaError_t e = launch_unpack_fp16(p, d_packed, 1, d_ws, s);
+    return e == cudaSuccess ? launch_xeng_tc(p, d_ws, nullptr, 1, d_vis, accumulate, s) : e;
+}
 
 // Issue one admitted job on its stream (called with the lock released).
 cudaError_t issue(corr_server_s* S, Job& j) {
@@ -176,19 +258,7 @@ cudaError_t issue(corr_server_s* S, Job& j) {
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 16, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc),
                                               cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        if (j.raw) {
-            e = j.desc.sample_bits == 32 ? launch_xeng_tc_rawf32(p, d_packed, 1, d_vis, 0, s)
-                                         : launch_xeng_tc_raw(p, d_packed, 1, d_vis, 0, s);
-        } else if (j.desc.sample_bits == 32) {
-            const size_t half = (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2;
-            e = launch_unpack_bf16x2(p, d_packed, 1, d_ws, d_ws + half, s);
-            if (e == cudaSuccess) e = launch_xeng_tc(p, d_ws, d_ws + half, 1, d_vis, 0, s);
-        } else {
-            e = launch_unpack_fp16(p, d_packed, 1, d_ws, s);
-            if (e == cudaSuccess) e = launch_xeng_tc(p, d_ws, nullptr, 1, d_vis, 0, s);
-        }
-    }
+    if (e == cudaSuccess) e = run_x(p, j.desc, j.raw, d_packed, d_vis, d_ws, 0, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_status, d_status, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && j.desc.host_vis)
         e = cudaMemcpyAsync(j.desc.host_vis, d_vis, vis_bytes(j.desc), cudaMemcpyDeviceToHost, s);
@@ -196,46 +266,128 @@ cudaError_t issue(corr_server_s* S, Job& j) {
     return e;
 }
 
+// Issue job `seq` of an open stream (called with the lock released; jobs of one stream are
+// issued in submission order by the single dispatcher thread).  The copy stream fills ring
+// slot seq mod R once the X stage of job seq - R has read it; the compute stream runs the X
+// stage into the stream's accumulators and, for the job that ends an interval, the dump.
+cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
+    const int R = st.d.ring_slots;
+    const int slot = (int)(j.seq % R);
+    char* d_packed = st.slots + (size_t)slot * st.slot_bytes;
+    int* d_status = st.status + 4 * slot;
+    Plan p = plan_of(j.desc, S->device, S->n_sm);
+    p.d_status = d_status;
+    const bool sums = st.d.dump_mode == CORR_STREAM_DUMP_SUMS;
+    // an interval's first job overwrites the accumulators (the previous interval's dump, issued
+    // earlier on the same stream, has read them): that is the reset of Fig. 1, with no extra pass
+    const int accumulate = j.seq % st.d.jobs_per_dump == 0 ? 0 : 1;
+    cudaError_t e = cudaSuccess;
+    if (j.seq >= R) e = cudaStreamWaitEvent(st.copy_s, st.slot_free[slot], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st.copy_s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc), cudaMemcpyHostToDevice, st.copy_s);
+    if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[slot], st.copy_s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[slot], 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 16, st.comp_s);
+    if (e == cudaSuccess) e = run_x(p, j.desc, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
+    if (e == cudaSuccess) e = cudaEventRecord(st.slot_free[slot], st.comp_s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_status, d_status, 16, cudaMemcpyDeviceToHost, st.comp_s);
+    if (e == cudaSuccess && j.closes) {
+        if (sums) {
+            e = cudaMemcpyAsync(j.desc.host_vis, st.acc, vis_bytes(j.desc), cudaMemcpyDeviceToHost, st.comp_s);
+        } else {
+            // Fig. 1: read out and divide by the update count (the next job's overwrite resets)
+            const corr_status cs = corr_dump(reinterpret_cast<corr_plan>(&p), st.acc, (int)j.n_accum, st.d.d_delays,
+                                             st.d.d_freqs, st.phasor, st.dumpbuf, 0, st.comp_s);
+            if (cs != CORR_OK) e = cudaErrorLaunchFailure;
+            if (e == cudaSuccess && j.desc.host_vis)
+                e = cudaMemcpyAsync(j.desc.host_vis, st.dumpbuf, (size_t)p.n_baselines * p.n_chan * 8,
+                                    cudaMemcpyDeviceToHost, st.comp_s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(j.ev_done, st.comp_s);
+    return e;
+}
+
+// The next job the dispatcher may issue: the first job of an open stream in the mailbox (they
+// need no arena space), or the first other job if it fits the arena's free space (the others
+// wait behind it in arrival order).  Called with the lock held.
+bool pick_next(corr_server_s* S, std::deque<uint64_t>::iterator* pick) {
+    bool arena_head_seen = false;
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        const Job& j = S->jobs[*it];
+        if (j.stream_job) {
+            *pick = it;
+            return true;
+        }
+        if (!arena_head_seen) {
+            arena_head_seen = true;
+            if (S->arena->fits(j.bytes)) {
+                *pick = it;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
 void dispatcher_loop(corr_server_s* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lock(S->mu);
     while (true) {
+        std::deque<uint64_t>::iterator pick;
+        bool have = false;
         S->cv_dispatch.wait_for(lock, std::chrono::milliseconds(50), [&] {
             if (S->stop) return true;
             if (S->paused || S->queue.empty()) return false;
-            auto it = S->jobs.find(S->queue.front());
-            return it != S->jobs.end() && S->arena->fits(it->second.bytes);
+            have = pick_next(S, &pick);
+            return have;
         });
         if (S->stop) break;
-        if (S->paused || S->queue.empty()) continue;
-        const uint64_t id = S->queue.front();
+        if (!have) continue;
+        const uint64_t id = *pick;
         Job& j = S->jobs[id];
-        size_t off;
-        if (!S->arena->alloc(j.bytes, &off)) continue;   // head of line waits for memory (FIFO admission)
-        S->queue.pop_front();
-        j.off = off;
-        j.holds_arena = true;
-        j.stream = S->next_stream;
-        S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
-        j.state = kRunning;
-        j.t_start = now_s();
-        j.d_vis = S->d_base + off + round_up(16) + round_up(packed_bytes(j.desc));   // layout of issue()
-        S->stats.bytes_in_use = S->arena->used();
-        S->stats.peak_bytes = S->arena->peak();
-        lock.unlock();
-        cudaError_t e = issue(S, j);
-        lock.lock();
+        cudaError_t e = cudaSuccess;
+        if (j.stream_job) {
+            S->queue.erase(pick);
+            j.state = kRunning;
+            j.t_start = now_s();
+            StreamState* st = j.st;
+            lock.unlock();
+            e = issue_stream(S, j, *st);
+            lock.lock();
+        } else {
+            size_t off;
+            if (!S->arena->alloc(j.bytes, &off)) continue;   // cannot happen: fits() held under the lock
+            S->queue.erase(pick);
+            j.off = off;
+            j.holds_arena = true;
+            j.stream = S->next_stream;
+            S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+            j.state = kRunning;
+            j.t_start = now_s();
+            j.d_vis = S->d_base + off + round_up(16) + round_up(packed_bytes(j.desc));   // layout of issue()
+            S->stats.bytes_in_use = S->arena->used();
+            S->stats.peak_bytes = S->arena->peak();
+            lock.unlock();
+            e = issue(S, j);
+            lock.lock();
+        }
         // the completion thread sees the job only once its events are recorded
         if (e == cudaSuccess) S->running.push_back(id);
         if (e != cudaSuccess) {
             // nothing of this job is queued behind a failed call that we can rely on; mark it
             // failed once its stream has drained the calls that were accepted
-            cudaStreamSynchronize(S->streams[j.stream]);
+            cudaStreamSynchronize(j.stream_job ? j.st->comp_s : S->streams[j.stream]);
+            if (j.stream_job) cudaStreamSynchronize(j.st->copy_s);
             j.state = kFailed;
             j.final_status = CORR_ECUDA;
             j.t_done = now_s();
-            S->arena->release(j.off, j.bytes);
-            j.holds_arena = false;
+            if (j.holds_arena) {
+                S->arena->release(j.off, j.bytes);
+                j.holds_arena = false;
+            }
+            if (j.stream_job) j.st->n_retired++;
             S->stats.failed++;
             S->cv_done.notify_all();
         }
@@ -268,9 +420,16 @@ void completer_loop(corr_server_s* S) {
             }
             if (j.state == kDone) S->stats.completed++;
             else S->stats.failed++;
-            // results copied to the host free their device block now; device-resident
-            // results stay until corr_release
-            if (j.desc.host_vis || j.state != kDone) {
+            if (j.stream_job) {
+                // an averaged dump left on the device stays in the stream's dump buffer
+                j.d_vis = (j.state == kDone && j.closes && !j.desc.host_vis &&
+                           j.st->d.dump_mode == CORR_STREAM_DUMP_AVERAGED)
+                              ? j.st->dumpbuf
+                              : nullptr;
+                j.st->n_retired++;
+            } else if (j.desc.host_vis || j.state != kDone) {
+                // results copied to the host free their device block now; device-resident
+                // results stay until corr_release
                 S->arena->release(j.off, j.bytes);
                 j.holds_arena = false;
                 j.d_vis = nullptr;
@@ -291,6 +450,21 @@ void completer_loop(corr_server_s* S) {
     }
 }
 
+// Destroy an open stream's streams and events (its work must be finished) and give its block
+// back to the arena (lock held by the caller, or the server's threads stopped).
+void free_stream_state(corr_server_s* S, StreamState* st) {
+    if (st->copy_s) cudaStreamSynchronize(st->copy_s);
+    if (st->comp_s) cudaStreamSynchronize(st->comp_s);
+    for (auto ev : st->slot_full)
+        if (ev) cudaEventDestroy(ev);
+    for (auto ev : st->slot_free)
+        if (ev) cudaEventDestroy(ev);
+    if (st->copy_s) cudaStreamDestroy(st->copy_s);
+    if (st->comp_s) cudaStreamDestroy(st->comp_s);
+    if (st->bytes) S->arena->release(st->off, st->bytes);
+    delete st;
+}
+
 void fill_result(const Job& j, corr_job_result* r) {
     r->status = j.state == kQueued || j.state == kRunning ? CORR_PENDING : j.final_status;
     r->t_submit = j.t_submit;
@@ -298,6 +472,8 @@ void fill_result(const Job& j, corr_job_result* r) {
     r->t_done = j.t_done;
     r->gpu_ms = j.gpu_ms;
     r->d_vis = j.d_vis;
+    r->closed_interval = j.stream_job && j.closes ? 1 : 0;
+    r->n_accum = j.stream_job && j.closes ? j.n_accum : 0;
 }
 
 }  // namespace
@@ -355,13 +531,34 @@ corr_status corr_submit(corr_server S, const corr_job_desc* d, uint64_t* job_id)
     if (!d->host_packed) return set_error(CORR_EINVAL, "host_packed is NULL");
     Job j;
     j.desc = *d;
-    j.bytes = footprint(*d, &j.raw);
     std::unique_lock<std::mutex> lock(S->mu);
     if (S->stop) return set_error(CORR_EBUSY, "server is shutting down");
-    if (j.bytes > S->arena->size()) {
-        S->stats.rejected++;
-        return set_error(CORR_EBUSY, "job needs %zu device bytes, more than the %zu-byte HBM budget", j.bytes,
-                         S->arena->size());
+    auto sit = S->open_streams.find(d->stream_tag);
+    StreamState* st = sit == S->open_streams.end() ? nullptr : sit->second;
+    if (st) {
+        // a job of an open stream: its shape is the stream's, its place is the next ring slot
+        if (st->closing) return set_error(CORR_EINVAL, "stream %d is closing", d->stream_tag);
+        if (d->n_inputs != st->d.n_inputs || d->n_chan != st->d.n_chan || d->n_time != st->d.n_time ||
+            d->sample_bits != st->d.sample_bits)
+            return set_error(CORR_EINVAL, "job shape differs from the shape stream %d was opened with",
+                             d->stream_tag);
+        j.stream_job = true;
+        j.st = st;
+        j.seq = st->n_submitted;
+        j.closes = (j.seq + 1) % st->d.jobs_per_dump == 0;
+        j.n_accum = j.closes ? (int64_t)st->d.jobs_per_dump * st->d.n_time : 0;
+        j.raw = st->raw;
+        j.bytes = 0;
+        if (j.closes && st->d.dump_mode == CORR_STREAM_DUMP_SUMS && !d->host_vis)
+            return set_error(CORR_EINVAL, "job %lld of stream %d ends a dump interval: host_vis must receive the sums",
+                             (long long)j.seq, d->stream_tag);
+    } else {
+        j.bytes = footprint(*d, &j.raw);
+        if (j.bytes > S->arena->size()) {
+            S->stats.rejected++;
+            return set_error(CORR_EBUSY, "job needs %zu device bytes, more than the %zu-byte HBM budget", j.bytes,
+                             S->arena->size());
+        }
     }
     cudaError_t e = cudaEventCreate(&j.ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&j.ev_done);
@@ -372,6 +569,7 @@ corr_status corr_submit(corr_server S, const corr_job_desc* d, uint64_t* job_id)
         return cuda_error(e, "corr_submit");
     }
     memset(j.h_status, 0, 16);
+    if (st) st->n_submitted++;
     j.id = S->next_id++;
     j.t_submit = now_s();
     *job_id = j.id;
@@ -441,10 +639,11 @@ corr_status corr_fetch(corr_server S, uint64_t job_id, void* host_vis) {
         const Job& j = it->second;
         if (j.state != kDone) return set_error(j.state == kFailed ? j.final_status : CORR_PENDING,
                                                "job %llu has no result", (unsigned long long)job_id);
-        if (!j.holds_arena) return set_error(CORR_EINVAL, "job %llu did not keep its result on the device",
-                                             (unsigned long long)job_id);
+        if (!j.d_vis) return set_error(CORR_EINVAL, "job %llu did not keep its result on the device",
+                                       (unsigned long long)job_id);
         src = j.d_vis;
-        bytes = vis_bytes(j.desc);
+        // an open stream's averaged dump is float32; any other kept result is the job's visibilities
+        bytes = j.stream_job ? (size_t)n_baselines(j.desc.n_inputs) * j.desc.n_chan * 8 : vis_bytes(j.desc);
     }
     // the block stays reserved until corr_release, which the caller must not race with this copy
     cudaError_t e = cudaMemcpy(host_vis, src, bytes, cudaMemcpyDeviceToHost);
@@ -468,6 +667,7 @@ corr_status corr_server_get_stats(corr_server S, corr_server_stats* st) {
     st->running = (int64_t)S->running.size();
     st->bytes_in_use = S->arena->used();
     st->peak_bytes = S->arena->peak();
+    st->open_streams = (int64_t)S->open_streams.size();
     return CORR_OK;
 }
 
@@ -494,6 +694,10 @@ corr_status corr_server_destroy(corr_server S, double drain_timeout_s) {
     // the streams must be idle before the arena goes away: wait for them (the kernels'
     // own waits are bounded, so this returns)
     for (auto st : S->streams) cudaStreamSynchronize(st);
+    for (auto& kv : S->open_streams) {
+        cudaStreamSynchronize(kv.second->copy_s);
+        cudaStreamSynchronize(kv.second->comp_s);
+    }
     S->dispatcher.join();
     S->completer.join();
     for (auto& kv : S->jobs) {
@@ -501,10 +705,135 @@ corr_status corr_server_destroy(corr_server S, double drain_timeout_s) {
         if (kv.second.ev_done) cudaEventDestroy(kv.second.ev_done);
         if (kv.second.h_status) cudaFreeHost(kv.second.h_status);
     }
+    for (auto& kv : S->open_streams) free_stream_state(S, kv.second);
+    S->open_streams.clear();
     for (auto st : S->streams) cudaStreamDestroy(st);
     cudaFree(S->d_base);
     delete S->arena;
     delete S;
+    return result;
+}
+
+corr_status corr_server_open_stream(corr_server S, int stream_tag, const corr_stream_desc* d) {
+    if (!S || !d) return set_error(CORR_EINVAL, "corr_server_open_stream: NULL argument");
+    if (d->sample_bits != 4 && d->sample_bits != 8 && d->sample_bits != 32)
+        return set_error(CORR_EINVAL, "sample_bits=%d must be 4, 8 or 32", d->sample_bits);
+    if (d->n_inputs < 1 || d->n_inputs > kMaxInputs || d->n_chan < 1 || d->n_time < 1)
+        return set_error(CORR_EINVAL, "bad stream sizes N=%d C=%d T=%d", d->n_inputs, d->n_chan, d->n_time);
+    if (d->ring_slots < 1 || d->ring_slots > 64) return set_error(CORR_EINVAL, "ring_slots=%d outside [1, 64]", d->ring_slots);
+    if (d->jobs_per_dump < 1) return set_error(CORR_EINVAL, "jobs_per_dump=%d must be >= 1", d->jobs_per_dump);
+    if (d->dump_mode != CORR_STREAM_DUMP_SUMS && d->dump_mode != CORR_STREAM_DUMP_AVERAGED)
+        return set_error(CORR_EINVAL, "unknown dump_mode %d", d->dump_mode);
+    if (d->dump_mode == CORR_STREAM_DUMP_AVERAGED && (int64_t)d->jobs_per_dump * d->n_time > INT32_MAX)
+        return set_error(CORR_EINVAL, "an averaged dump sums more than 2^31 samples");
+    if (d->d_delays && !d->d_freqs) return set_error(CORR_EINVAL, "delays need channel frequencies");
+    if ((double)n_baselines(d->n_inputs) * d->n_chan * 16.0 > 4.0e15) return set_error(CORR_EINVAL, "stream too large");
+    StreamState* st = new (std::nothrow) StreamState();
+    if (!st) return set_error(CORR_ENOMEM, "host allocation failed");
+    st->d = *d;
+    if (st->d.dump_mode != CORR_STREAM_DUMP_AVERAGED) {
+        st->d.d_delays = nullptr;
+        st->d.d_freqs = nullptr;
+    }
+    const Plan p = plan_of(shape_of(*d), 0, 0);
+    st->raw = d->sample_bits == 32 ? tc_rawf32_supported(p) : !tc_use_planes(p);
+    const size_t need = stream_layout(*st, nullptr);
+    std::unique_lock<std::mutex> lock(S->mu);
+    if (S->stop) {
+        delete st;
+        return set_error(CORR_EBUSY, "server is shutting down");
+    }
+    if (S->open_streams.count(stream_tag)) {
+        delete st;
+        return set_error(CORR_EINVAL, "stream %d is already open", stream_tag);
+    }
+    size_t off = 0;
+    if (need > S->arena->size() || !S->arena->alloc(need, &off)) {
+        const size_t arena = S->arena->size();
+        delete st;
+        return set_error(CORR_EBUSY, "stream %d needs %zu device bytes (ring, accumulators, dump); the %zu-byte "
+                                     "arena has not that much free now", stream_tag, need, arena);
+    }
+    st->off = off;
+    st->bytes = need;
+    stream_layout(*st, S->d_base + off);
+    // deadline-aware priority: a job must be correlated within its own sample time, so streams
+    // with shorter dumps get the higher priority when the GPU picks the next kernel to run
+    int lo_prio = 0, hi_prio = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    int prio = lo_prio;
+    if (e == cudaSuccess && hi_prio < lo_prio) {
+        // 1024 samples or more: the lowest; each halving of the sample time one step higher
+        int steps = 0;
+        for (int t = d->n_time; t < 1024 && steps < lo_prio - hi_prio; t *= 2) ++steps;
+        prio = lo_prio - steps;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st->copy_s, cudaStreamNonBlocking, prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st->comp_s, cudaStreamNonBlocking, prio);
+    st->slot_full.assign(d->ring_slots, nullptr);
+    st->slot_free.assign(d->ring_slots, nullptr);
+    for (int k = 0; k < d->ring_slots && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&st->slot_full[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->slot_free[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        free_stream_state(S, st);
+        return cuda_error(e, "corr_server_open_stream");
+    }
+    S->open_streams[stream_tag] = st;
+    S->stats.bytes_in_use = S->arena->used();
+    S->stats.peak_bytes = S->arena->peak();
+    return CORR_OK;
+}
+
+corr_status corr_server_close_stream(corr_server S, int stream_tag, double drain_timeout_s) {
+    if (!S) return set_error(CORR_EINVAL, "corr_server_close_stream: NULL server");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->open_streams.find(stream_tag);
+    if (it == S->open_streams.end()) return set_error(CORR_EINVAL, "stream %d is not open", stream_tag);
+    StreamState* st = it->second;
+    st->closing = true;
+    corr_status result = CORR_OK;
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(drain_timeout_s > 0 ? drain_timeout_s : 0));
+    S->cv_done.wait_until(lock, deadline, [&] { return st->n_retired == st->n_submitted; });
+    if (st->n_retired != st->n_submitted) {
+        result = set_error(CORR_ETIMEOUT, "stream %d: %lld jobs unfinished after %.1f s", stream_tag,
+                           (long long)(st->n_submitted - st->n_retired), drain_timeout_s);
+        // jobs not yet issued never will be; issued ones are waited for on the GPU
+        for (auto q = S->queue.begin(); q != S->queue.end();) {
+            Job& j = S->jobs[*q];
+            if (j.stream_job && j.st == st) {
+                j.state = kCancelled;
+                j.final_status = CORR_EBUSY;
+                st->n_retired++;
+                S->stats.cancelled++;
+                q = S->queue.erase(q);
+            } else {
+                ++q;
+            }
+        }
+        lock.unlock();
+        cudaStreamSynchronize(st->copy_s);
+        cudaStreamSynchronize(st->comp_s);
+        lock.lock();
+        // the completion thread retires the issued jobs once their events are complete
+        S->cv_done.wait_for(lock, std::chrono::seconds(10), [&] { return st->n_retired == st->n_submitted; });
+        if (st->n_retired != st->n_submitted) {
+            S->open_streams.erase(stream_tag);   // jobs still reference the state: keep it alive
+            return result;
+        }
+    }
+    S->open_streams.erase(stream_tag);
+    // finished jobs keep no pointer into the state except their dump result, which goes now
+    for (auto& kv : S->jobs)
+        if (kv.second.st == st) {
+            kv.second.st = nullptr;
+            kv.second.d_vis = nullptr;
+        }
+    free_stream_state(S, st);
+    S->stats.bytes_in_use = S->arena->used();
+    S->cv_dispatch.notify_all();
     return result;
 }
 

@@ -221,4 +221,225 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
     return cudaGetLastError();
 }
 
+// ---- FP32 CUDA-core engine reading the packed samples directly ----------------------------
+//
+// The plain form as run by corr_xengine_run: no unpack pass, and no products below the
+// diagonal.  A 64 x 64 tile of input pairs is split into 4 x 4 sub-blocks of contiguous inputs
+// (16 x 16 of them); a thread owns one sub-block: rows 4gi .. 4gi+3, columns 4gj .. 4gj+3, 16
+// complex accumulators.  Off-diagonal tiles (I < J) use 256 threads, one per sub-block; diagonal
+// tiles (I = J) only need the 136 sub-blocks with gi <= gj and run in 160-thread blocks (136
+// working, the rest only load), so the 64-input stream computes 2176 products per 2080 baselines
+// instead of 4096.  Each 32-sample chunk of the tile's one or two 64-input blocks is loaded with
+// consecutive threads on consecutive inputs (coalesced), converted to float2 (re, im) and stored
+// in shared memory with two pad slots after every four inputs: a thread's four inputs are then
+// two 16-byte loads, and the 16 sub-block columns of a warp hit distinct bank groups in pairs.
+// Exactness for integer samples as in the plane-fed engine above: 64-sample fp32 partials
+// (|Re| <= 2^21), int32 totals over segments of at most 32768 samples, int64 output.
+namespace {
+
+constexpr int kDChunk = 32;            // samples per shared-memory chunk
+constexpr int kDRow = 64 + 32;         // float2 slots per sample row (inputs + pads)
+constexpr int kDiagThreads = 160;      // 136 sub-blocks with gi <= gj, rounded to whole warps
+constexpr int kOffThreads = 256;
+
+__device__ __forceinline__ int dslot(int i) { return i + 2 * (i >> 2); }
+
+template <int BITS>
+__device__ __forceinline__ float2 load_packed(const unsigned char* __restrict__ p, int64_t idx) {
+    if constexpr (BITS == 4) {
+        const int b = p[idx];
+        return make_float2((float)((int)((unsigned)b << 24) >> 28), (float)((int)((unsigned)b << 28) >> 28));
+    } else if constexpr (BITS == 8) {
+        const unsigned short v = reinterpret_cast<const unsigned short*>(p)[idx];
+        return make_float2((float)(signed char)(v & 0xFF), (float)(signed char)(v >> 8));
+    } else {
+        return reinterpret_cast<const float2*>(p)[idx];
+    }
+}
+
+// strictly-upper tile index -> (I, J), I < J < nb, row-major
+__device__ __forceinline__ void off_tile(int tile, int nb, int& I, int& J) {
+    int i = 0, rem = tile;
+    while (rem >= nb - 1 - i) {
+        rem -= nb - 1 - i;
+        ++i;
+    }
+    I = i;
+    J = i + 1 + rem;
+}
+
+template <int BITS, bool DIAG>
+__global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 2)
+    xeng_fp32_packed_kernel(const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
+                            int64_t n_items, void* __restrict__ vis, int accumulate) {
+    constexpr bool kInt = BITS != 32;
+    constexpr int kThreads = DIAG ? kDiagThreads : kOffThreads;
+    constexpr int kBlocks = DIAG ? 1 : 2;            // 64-input blocks per tile
+    __shared__ __align__(16) float2 s[kBlocks][kDChunk * kDRow];
+    const int tid = threadIdx.x;
+    int gi, gj;
+    bool active = true;
+    if (DIAG) {
+        // tid -> the tid-th sub-block (gi <= gj) in row-major order
+        int g = 0, rem = tid;
+        while (g < 16 && rem >= 16 - g) {
+            rem -= 16 - g;
+            ++g;
+        }
+        active = g < 16;
+        gi = active ? g : 0;
+        gj = active ? g + rem : 0;
+    } else {
+        gi = tid >> 4;
+        gj = tid & 15;
+    }
+    const float2* sa = s[0];
+    const float2* sb = s[kBlocks - 1];
+    const int64_t P = (int64_t)n_inputs * (n_inputs + 1) / 2;
+    const int n_off = nb * (nb - 1) / 2;
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int I, J;
+        int64_t dc;
+        if (DIAG) {
+            I = J = (int)(item % nb);
+            dc = item / nb;
+        } else {
+            off_tile((int)(item % n_off), nb, I, J);
+            dc = item / n_off;
+        }
+        const int64_t d = dc / n_chan;
+        const int c = (int)(dc % n_chan);
+        constexpr int kSegment = 32768;
+        for (int s0 = 0; s0 < n_time; s0 += kSegment) {
+            const int s1 = min(n_time, s0 + kSegment);
+            float pr[4][4], pi[4][4];
+            typename std::conditional<kInt, int, float>::type tr[4][4], ti[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    pr[a][b] = pi[a][b] = 0.f;
+                    tr[a][b] = ti[a][b] = 0;
+                }
+            int chunk = 0;
+            for (int t0 = s0; t0 < s1; t0 += kDChunk) {
+                // load + convert this chunk of the tile's blocks (zero past the last input/sample)
+                for (int k = tid; k < kBlocks * kDChunk * 64; k += kThreads) {
+                    const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
+                    const int t = rest >> 6, i = rest & 63;
+                    const int ig = (blk ? J : I) * 64 + i;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (t0 + t < s1 && ig < n_inputs)
+                        v = load_packed<BITS>(packed, ((d * n_time + t0 + t) * n_chan + c) * (int64_t)n_inputs + ig);
+                    s[blk][t * kDRow + dslot(i)] = v;
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll 2
+                    for (int t = 0; t < kDChunk; ++t) {
+                        const float4 a01 = *reinterpret_cast<const float4*>(sa + t * kDRow + 6 * gi);
+                        const float4 a23 = *reinterpret_cast<const float4*>(sa + t * kDRow + 6 * gi + 2);
+                        const float4 b01 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj);
+                        const float4 b23 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj + 2);
+                        const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
+                        const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
+#pragma unroll
+                        for (int x = 0; x < 4; ++x)
+#pragma unroll
+                            for (int y = 0; y < 4; ++y) {
+                                // x_i conj(x_j): re = ar br + ai bi, im = ai br - ar bi
+                                pr[x][y] = fmaf(ar[x], br[y], pr[x][y]);
+                                pr[x][y] = fmaf(ai[x], bi[y], pr[x][y]);
+                                pi[x][y] = fmaf(ai[x], br[y], pi[x][y]);
+                                pi[x][y] = fmaf(-ar[x], bi[y], pi[x][y]);
+                            }
+                    }
+                }
+                __syncthreads();
+                if (++chunk == 2 || t0 + kDChunk >= s1) {   // flush every 64 samples
+                    chunk = 0;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            if constexpr (kInt) {
+                                tr[a][b] += __float2int_rn(pr[a][b]);   // exact: |partial| <= 2^21
+                                ti[a][b] += __float2int_rn(pi[a][b]);
+                            } else {
+                                tr[a][b] += pr[a][b];
+                                ti[a][b] += pi[a][b];
+                            }
+                            pr[a][b] = pi[a][b] = 0.f;
+                        }
+                }
+            }
+            if (!active) continue;
+            const bool add = accumulate || s0 > 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int i = I * 64 + 4 * gi + a;
+                if (i >= n_inputs) continue;
+                const int64_t row = dc * P + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int j = J * 64 + 4 * gj + b;
+                    if (j < i || j >= n_inputs) continue;
+                    if constexpr (kInt) {
+                        longlong2* dst = reinterpret_cast<longlong2*>(vis) + row + j;
+                        longlong2 v = make_longlong2(tr[a][b], ti[a][b]);
+                        if (add) {
+                            const longlong2 o = *dst;
+                            v.x += o.x;
+                            v.y += o.y;
+                        }
+                        *dst = v;
+                    } else {
+                        float2* dst = reinterpret_cast<float2*>(vis) + row + j;
+                        float2 v = make_float2(tr[a][b], ti[a][b]);
+                        if (add) {
+                            const float2 o = *dst;
+                            v.x += o.x;
+                            v.y += o.y;
+                        }
+                        *dst = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int BITS>
+cudaError_t launch_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                          cudaStream_t s) {
+    const auto* src = static_cast<const unsigned char*>(d_packed);
+    const int64_t diag_items = (int64_t)n_dumps * p.n_chan * p.nb;
+    const int64_t off_items = (int64_t)n_dumps * p.n_chan * (p.nb * (p.nb - 1) / 2);
+    if (diag_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 3;
+        const int grid = (int)(diag_items < cap ? diag_items : cap);
+        xeng_fp32_packed_kernel<BITS, true><<<grid, kDiagThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb,
+                                                                          diag_items, d_vis, accumulate);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (off_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 2;
+        const int grid = (int)(off_items < cap ? off_items : cap);
+        xeng_fp32_packed_kernel<BITS, false><<<grid, kOffThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb,
+                                                                          off_items, d_vis, accumulate);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_xeng_fp32_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                                    cudaStream_t s) {
+    if (p.sample_bits == 4) return launch_packed<4>(p, d_packed, n_dumps, d_vis, accumulate, s);
+    if (p.sample_bits == 8) return launch_packed<8>(p, d_packed, n_dumps, d_vis, accumulate, s);
+    return launch_packed<32>(p, d_packed, n_dumps, d_vis, accumulate, s);
+}
+
 }  // namespace corr

@@ -55,6 +55,7 @@
 #include <new>
 
 #include "corr_internal.h"
+#include "sample_convert.cuh"
 #include "tc_ptx.cuh"
 
 namespace corr {
@@ -102,13 +103,15 @@ constexpr int kMaxJobs = kMaxJobsPerLaunch;   // jobs one launch packs (kernel-p
 // sizes, output and the flat index of its first work item.
 struct TcJob {
     CUtensorMap map;
+    CUtensorMap map_wide;   // plane path, wide items: boxes of two blocks (256 rows)
     void* vis;
     int64_t item_begin;  // first flat item of this job
     int n_inputs;
     int n_chan;
     int nb;              // 64-input blocks
     int kp;              // samples per dump rounded up to 64
-    int n_tiles;         // nb (nb + 1) / 2 upper-triangle blocks
+    int n_tiles;         // work items per channel group: nb (nb + 1) / 2 tiles, or S(nb) wide items
+    int tw;              // 2: wide items (block I against blocks J0, J0 + 1, one N = 256 MMA); 1: tiles
     int cpi;             // channels per work item (2: adjacent channel pair, single-block arrays)
     int n_groups;        // channel groups per dump = ceil(n_chan / cpi)
     int chunk_kb;        // 64-sample blocks per exactly-flushed chunk
@@ -154,8 +157,10 @@ struct TcLaunch {
 // index only moves forward.
 struct ItemCtx {
     int j;
-    int I, J;
+    int I, J;            // J: the first B block (wide items: J and J + 1 when nsub = 2)
     bool same;
+    bool wide;
+    int nsub;            // accumulators of the item: channels (cpi) or B blocks (wide)
     int64_t d;           // dump within the job
     int c0;              // first channel of the item
 };
@@ -170,6 +175,22 @@ __device__ __forceinline__ void tile_coords(int tile, int nb, int& I, int& J) {
     while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= tile) ++i;
     I = i;
     J = i + (tile - (i * nb - i * (i - 1) / 2));
+}
+
+// Wide items: row I holds the items J0 = I, I + 2, ... < nb, so the rows of lengths nb .. 1
+// start at S(nb) - S(nb - I) with S(m) = floor((m + 1) / 2) floor((m + 2) / 2).  The row is
+// the smallest m = nb - I with S(m) >= S(nb) - item, from S(m) ~ (m + 1.5)^2 / 4 in float and
+// corrected exactly.
+__device__ __forceinline__ int pairs_upto(int m) { return ((m + 1) >> 1) * ((m + 2) >> 1); }
+
+__device__ __forceinline__ void wide_coords(int tile, int nb, int& I, int& J0) {
+    const int R = pairs_upto(nb) - tile;
+    int m = (int)(2.0f * sqrtf((float)R) - 1.5f);
+    m = max(0, min(m, nb));
+    while (m > 0 && pairs_upto(m - 1) >= R) --m;
+    while (pairs_upto(m) < R) ++m;
+    I = nb - m;
+    J0 = I + 2 * (tile - (pairs_upto(nb) - pairs_upto(m)));
 }
 
 __device__ __forceinline__ uint32_t fast_div(uint32_t n, uint32_t m, int s) {
@@ -187,7 +208,14 @@ __device__ __forceinline__ void decode_item(const TcLaunch<MAXJ>& L, int64_t ite
     it.j = j;
     it.d = d;
     it.c0 = (int)(dg - d * (uint32_t)jb.n_groups) * jb.cpi;
-    tile_coords(tile, jb.nb, it.I, it.J);
+    it.wide = jb.tw == 2;
+    if (it.wide) {
+        wide_coords(tile, jb.nb, it.I, it.J);
+        it.nsub = min(2, jb.nb - it.J);
+    } else {
+        tile_coords(tile, jb.nb, it.I, it.J);
+        it.nsub = jb.cpi;
+    }
     it.same = it.I == it.J;
 }
 
@@ -196,20 +224,8 @@ __device__ __forceinline__ void record_error(int* status, volatile int* abort, i
     if (atomicCAS(status, 0, code) == 0) status[1] = detail;
 }
 
-// Two samples (t, t+1) taken from byte lane `sel` of words a, b -> half2 of the signed
-// values.  fp16(1024 + u) has bit pattern 0x6400 | u for 0 <= u < 1024; `flip` both inserts
-// the 0x64 exponent bytes and turns the two's-complement byte into u = x + offset
-// ((r & 0x00FF00FF) ^ flip is a single LOP3), and `bias` = 1024 + offset removes it again.
-__device__ __forceinline__ uint32_t pair_to_half2(uint32_t a, uint32_t b, uint32_t sel, uint32_t flip,
-                                                  __half2 bias) {
-    uint32_t r = (__byte_perm(a, b, sel) & 0x00FF00FFu) ^ flip;
-    __half2 h = __hsub2(*reinterpret_cast<__half2*>(&r), bias);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-
-__device__ __forceinline__ uint32_t lane_selector(int k) {
-    return (uint32_t)(k | (k << 4) | ((k + 4) << 8) | ((k + 4) << 12));
-}
+using conv::lane_selector;
+using conv::pair_to_half2;
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
@@ -282,8 +298,8 @@ __device__ __forceinline__ ConvLane conv_lane4(int l) {
 // w[e] = bytes 4l .. 4l+3 (re, im of inputs 2l, 2l+1) of sample 8q + e; the slice is the 8
 // samples of group q, written as four 16-byte swizzled row chunks.
 __device__ __forceinline__ void convert_words8(const uint32_t (&w)[8], uint32_t dst, int q, const ConvLane& cl) {
-    const __half2 bias = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));  // 1152
-    const uint32_t flip = 0x64806480u;   // exponent bytes 0x64, sign bit of each sample byte flipped
+    const __half2 bias = conv::bias8();
+    const uint32_t flip = conv::kFlip8;   // exponent bytes 0x64, sign bit of each sample byte flipped
     const uint32_t q16 = (uint32_t)q << 4;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
@@ -297,8 +313,8 @@ __device__ __forceinline__ void convert_words8(const uint32_t (&w)[8], uint32_t 
 // Packed 4-bit words (high nibble re, low nibble im): lane l holds w[e] = inputs 4m .. 4m+3
 // (m = l & 15) of sample 8q + e, q = 2s + (l >> 4) for slice s.
 __device__ __forceinline__ void convert_words4(const uint32_t (&w)[8], uint32_t dst, int q, const ConvLane& cl) {
-    const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
-    const uint32_t flip = 0x64086408u;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
+    const __half2 bias = conv::bias4();
+    const uint32_t flip = conv::kFlip4;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -441,7 +457,10 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         ptx::mbar_init(bar_drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
-        for (int j = 0; j < prm.n_jobs; ++j) ptx::prefetch_tensormap(&prm.jobs[j].map);
+        for (int j = 0; j < prm.n_jobs; ++j) {
+            ptx::prefetch_tensormap(&prm.jobs[j].map);
+            if (!C::kRaw && prm.jobs[j].tw == 2) ptx::prefetch_tensormap(&prm.jobs[j].map_wide);
+        }
         if (C::kSplit && !C::kRaw) ptx::prefetch_tensormap(&prm.map_lo);
     }
     if (warp == 1) {
@@ -503,12 +522,21 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         const int rowA = (int)((dc * jb.nb + I) * kBlockRows);
                         const int rowB = (int)((dc * jb.nb + J) * kBlockRows);
                         const uint32_t bo = (uint32_t)prm.b_offset;
-                        ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)(C::kTilesPerOperand * kTileBytes));
-                        ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
-                        if (!same) ptx::tma_load_2d(st + bo, &jb.map, kb * kTimeBlock, rowB, fb);
-                        if (C::kSplit) {
-                            ptx::tma_load_2d(st + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowA, fb);
-                            if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowB, fb);
+                        if (it.wide) {
+                            // B = blocks J (, J + 1) in one box at b_offset; A = block I, or on the
+                            // diagonal the first half of the B box itself
+                            const uint32_t nB = (uint32_t)it.nsub;
+                            ptx::mbar_expect_tx(fb, (nB + (same ? 0u : 1u)) * (uint32_t)kTileBytes);
+                            if (!same) ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
+                            ptx::tma_load_2d(st + bo, nB == 2 ? &jb.map_wide : &jb.map, kb * kTimeBlock, rowB, fb);
+                        } else {
+                            ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)(C::kTilesPerOperand * kTileBytes));
+                            ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
+                            if (!same) ptx::tma_load_2d(st + bo, &jb.map, kb * kTimeBlock, rowB, fb);
+                            if (C::kSplit) {
+                                ptx::tma_load_2d(st + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowA, fb);
+                                if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowB, fb);
+                            }
                         }
                     }
                     ++n_slots;
@@ -536,6 +564,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = ptx::idesc_f16(128, 128, C::kSplit);
+            constexpr uint32_t idesc_wide = ptx::idesc_f16(128, 256, C::kSplit);
             constexpr uint32_t desc_hi = ptx::sw128_desc_hi();
             const uint32_t desc_lo_ring = ptx::sw128_desc_lo(ptx::smem_u32(ring));
             const uint32_t stage16 = (uint32_t)prm.op_stage_bytes >> 4;
@@ -573,7 +602,16 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         // 16 KB tile, +2 per 16-sample step along the swizzled rows
                         const uint32_t a0 = desc_lo_ring + (uint32_t)s * stage16;
                         const uint32_t acc0 = kb > kb0 ? 1u : 0u;
-                        if constexpr (C::kSplit) {
+                        if (!C::kRaw && !C::kSplit && it.wide) {
+                            // one M = 128, N = 256 MMA covers tiles (I, J) and (I, J + 1); on the
+                            // diagonal A is the first half of the B box
+                            const uint32_t b0 = a0 + boff16;
+                            const uint32_t aw = same ? b0 : a0;
+                            const uint32_t id = it.nsub == 2 ? idesc_wide : idesc;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                ptx::mma_f16_lo(dset, aw + 2u * k, b0 + 2u * k, desc_hi, id, (k > 0) | acc0);
+                        } else if constexpr (C::kSplit) {
                             const uint32_t b0 = same ? a0 : a0 + boff16;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
@@ -659,9 +697,13 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 }
                 ptx::tc_fence_after();
                 const bool add = prm.accumulate || kb0 > 0;
-                for (int ch = 0; ch < jb.cpi; ++ch) {
-                const bool ch_ok = row_ok && (it.c0 + ch) < jb.n_chan;
-                const int64_t chan_base = (it.d * jb.n_chan + it.c0 + ch) * P;
+                for (int ch = 0; ch < it.nsub; ++ch) {
+                // sub-accumulator ch: channel c0 + ch of a channel-pair item, or tile (I, J + ch)
+                // of a wide item
+                const int Jx = it.wide ? J + ch : J;
+                const int cx = it.wide ? it.c0 : it.c0 + ch;
+                const bool ch_ok = row_ok && cx < jb.n_chan;
+                const int64_t chan_base = (it.d * jb.n_chan + cx) * P;
                 const int64_t row_base = chan_base + row_off;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) +
                                        (uint32_t)(abuf * (int)(prm.tmem_cols / 2) + ch * 128);
@@ -676,13 +718,13 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 float2 gi = make_float2(1.f, 0.f);
                 uint32_t phs = 0;
                 if constexpr (DUMP) {
-                    if (jb.phasor && (it.c0 + ch) < jb.n_chan) {   // warp-uniform: every lane stages
-                        gch = jb.phasor + (size_t)(it.c0 + ch) * n_in;
+                    if (jb.phasor && cx < jb.n_chan) {   // warp-uniform: every lane stages
+                        gch = jb.phasor + (size_t)cx * n_in;
                         if (row_ok) gi = gch[i];
                         if (prm.staged) {
                             phs = staging_q + 16u * (uint32_t)kStageRowBytesF;
                             for (int u = lane; u < kBlockInputs; u += 32) {
-                                const int j = J * kBlockInputs + u;
+                                const int j = Jx * kBlockInputs + u;
                                 const float2 g = j < n_in ? gch[j] : make_float2(1.f, 0.f);
                                 st_shared_v2_f32(phs + 8u * (uint32_t)u, g.x, g.y);
                             }
@@ -708,7 +750,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         own0[k] = odd ? v[2 * k + 16] : v[2 * k];
                         own1[k] = odd ? v[2 * k + 17] : v[2 * k + 1];
                     }
-                    const int j0 = J * kBlockInputs + 16 * m + (odd ? 8 : 0);
+                    const int j0 = Jx * kBlockInputs + 16 * m + (odd ? 8 : 0);
                     if constexpr (kIntOut && DUMP) {
                         // dump mode: rr + ii and ir - ri in fp32 (each term exact, the sum rounded
                         // once), scaled by 1 / n_accum and rotated by phasor_i conj(phasor_j)
@@ -722,7 +764,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             const float ii = __uint_as_float(odd ? own1[k] : oth1[k]);
                             float2 w = make_float2((rr + ii) * jb.inv_n, (ir - ri) * jb.inv_n);
                             if (gch && j < n_in) {
-                                const float2 gj = prm.staged ? ld_shared_v2_f32(phs + 8u * (uint32_t)(j - J * kBlockInputs))
+                                const float2 gj = prm.staged ? ld_shared_v2_f32(phs + 8u * (uint32_t)(j - Jx * kBlockInputs))
                                                              : gch[j];
                                 const float2 t = make_float2(w.x * gi.x - w.y * gi.y, w.x * gi.y + w.y * gi.x);
                                 w = make_float2(t.x * gj.x + t.y * gj.y, t.y * gj.x - t.x * gj.y);
@@ -731,9 +773,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         }
                         if (prm.staged) {
                             // slot (j - J0) + s of row lane/2, s = parity of the row's element J0
-                            const int s_r = (int)((chan_base + row_off + J * kBlockInputs) & 1);
+                            const int s_r = (int)((chan_base + row_off + Jx * kBlockInputs) & 1);
                             const uint32_t rowp = staging_q + (uint32_t)(lane >> 1) * kStageRowBytesF +
-                                                  (uint32_t)(j0 - J * kBlockInputs + s_r) * 8u;
+                                                  (uint32_t)(j0 - Jx * kBlockInputs + s_r) * 8u;
 #pragma unroll
                             for (int k = 0; k < 8; ++k) st_shared_v2_f32(rowp + 8u * (uint32_t)k, wv[k].x, wv[k].y);
                         } else {
@@ -773,7 +815,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             // row lane/2 of this warp's staging rows, slots j - J0; odd lanes
                             // write their slots rotated by 4 so a quarter-warp never shares banks
                             const uint32_t rowp = staging_q + (uint32_t)(lane >> 1) * kStageRowBytes +
-                                                  (uint32_t)(j0 - J * kBlockInputs) * 16u;
+                                                  (uint32_t)(j0 - Jx * kBlockInputs) * 16u;
 #pragma unroll
                             for (int kk = 0; kk < 8; ++kk) {
                                 const int k_even = kk, k_odd = (kk + 4) & 7;
@@ -825,27 +867,27 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     __syncwarp();
                     if (lane < 16) {
                         const int ir_ = I * kBlockInputs + 16 * q + lane;
-                        const int j_lo = max(J * kBlockInputs, ir_);
-                        const int j_hi = min(J * kBlockInputs + kBlockInputs, n_in);
-                        if (ir_ < n_in && j_lo < j_hi && (it.c0 + ch) < jb.n_chan) {
+                        const int j_lo = max(Jx * kBlockInputs, ir_);
+                        const int j_hi = min(Jx * kBlockInputs + kBlockInputs, n_in);
+                        if (ir_ < n_in && j_lo < j_hi && cx < jb.n_chan) {
                             const int64_t rstart = chan_base + (int64_t)ir_ * n_in - (int64_t)ir_ * (ir_ - 1) / 2 - ir_;
-                            const int s_r = (int)((rstart + J * kBlockInputs) & 1);
+                            const int s_r = (int)((rstart + Jx * kBlockInputs) & 1);
                             const uint32_t row_src = staging_q + (uint32_t)lane * kStageRowBytesF;
                             float2* vis2 = reinterpret_cast<float2*>(jb.vis);
                             int j = j_lo;
                             if ((rstart + j) & 1) {
                                 vis2[rstart + j] =
-                                    ld_shared_v2_f32(row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u);
+                                    ld_shared_v2_f32(row_src + (uint32_t)(j - Jx * kBlockInputs + s_r) * 8u);
                                 ++j;
                             }
                             const int body = (j_hi - j) & ~1;
                             if (body > 0)
-                                bulk_store(vis2 + rstart + j, row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u,
+                                bulk_store(vis2 + rstart + j, row_src + (uint32_t)(j - Jx * kBlockInputs + s_r) * 8u,
                                            (uint32_t)body * 8u);
                             j += body;
                             if (j < j_hi)
                                 vis2[rstart + j] =
-                                    ld_shared_v2_f32(row_src + (uint32_t)(j - J * kBlockInputs + s_r) * 8u);
+                                    ld_shared_v2_f32(row_src + (uint32_t)(j - Jx * kBlockInputs + s_r) * 8u);
                         }
                         bulk_commit();
                     }
@@ -856,13 +898,13 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     __syncwarp();
                     if (lane < 16) {
                         const int ir_ = I * kBlockInputs + 16 * q + lane;
-                        const int j_lo = max(J * kBlockInputs, ir_);
-                        const int j_hi = min(J * kBlockInputs + kBlockInputs, n_in);
-                        if (ir_ < n_in && j_lo < j_hi && (it.c0 + ch) < jb.n_chan) {
+                        const int j_lo = max(Jx * kBlockInputs, ir_);
+                        const int j_hi = min(Jx * kBlockInputs + kBlockInputs, n_in);
+                        if (ir_ < n_in && j_lo < j_hi && cx < jb.n_chan) {
                             const int64_t b0 = chan_base + (int64_t)ir_ * n_in - (int64_t)ir_ * (ir_ - 1) / 2 +
                                                (j_lo - ir_);
                             const uint32_t src = staging_q + (uint32_t)lane * kStageRowBytes +
-                                                 (uint32_t)(j_lo - J * kBlockInputs) * 16u;
+                                                 (uint32_t)(j_lo - Jx * kBlockInputs) * 16u;
                             void* dst = reinterpret_cast<longlong2*>(jb.vis) + b0;
                             const uint32_t bytes = (uint32_t)(j_hi - j_lo) * 16u;
                             if (add) bulk_add_u64(dst, src, bytes);
@@ -871,7 +913,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         bulk_commit();
                     }
                 }
-                }  // channels of the item
+                }  // sub-accumulators of the item
                 // accumulator drained (the loads completed at tcgen05.wait::ld): hand the
                 // tensor-memory buffer back to the MMA warp
                 ptx::tc_fence_before();
@@ -993,13 +1035,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D map over plane rows: dim0 = Kp samples (fp16/bf16), dim1 = all 128-row blocks.
-bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CUtensorMapDataType dt) {
+// 2-D map over plane rows: dim0 = Kp samples (fp16/bf16), dim1 = all 128-row blocks; boxes of
+// one block (128 rows) or, for wide items, of two adjacent blocks (256 rows).
+bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CUtensorMapDataType dt,
+                    int box_rows = kBlockRows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTimeBlock, (cuuint32_t)kBlockRows};
+    cuuint32_t box[2] = {(cuuint32_t)kTimeBlock, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1033,9 +1077,13 @@ void fast_div_make(uint32_t d, uint32_t& m, int& s) {
     s = l;
 }
 
+// S(m) = floor((m + 1) / 2) floor((m + 2) / 2): wide items of an array of m blocks
+int wide_items(int m) { return ((m + 1) / 2) * ((m + 2) / 2); }
+
 template <int MODE, int MAXJ>
 cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* maps, const CUtensorMap* map_lo,
-                        int accumulate, int* status, int n_sm, const TcTuning& tune, cudaStream_t s) {
+                        int accumulate, int* status, int n_sm, const TcTuning& tune, cudaStream_t s,
+                        const CUtensorMap* maps_wide = nullptr) {
     using C = Cfg<MODE>;
     if (n_jobs < 1 || n_jobs > MAXJ) return cudaErrorInvalidValue;
     static_assert(sizeof(TcLaunch<MAXJ>) <= 32000, "kernel parameters exceed the launch limit");
@@ -1054,12 +1102,15 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         const TcJobSpec& sp = specs[j];
         TcJob& jb = prm->jobs[j];
         jb.map = maps[j];
+        // wide items only where the MMA feed reads fp16 planes (two blocks per TMA box)
+        jb.tw = (MODE == kPlanesF16 && sp.tw == 2 && maps_wide) ? 2 : 1;
+        if (jb.tw == 2) jb.map_wide = maps_wide[j];
         jb.vis = sp.vis;
         jb.n_inputs = sp.n_inputs;
         jb.n_chan = sp.n_chan;
         jb.nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
         jb.kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
-        jb.n_tiles = jb.nb * (jb.nb + 1) / 2;
+        jb.n_tiles = jb.tw == 2 ? wide_items(jb.nb) : jb.nb * (jb.nb + 1) / 2;
         jb.cpi = sp.cpi;
         jb.n_groups = (sp.n_chan + jb.cpi - 1) / jb.cpi;
         // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
@@ -1082,10 +1133,11 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         fast_div_make((uint32_t)jb.n_tiles, jb.tiles_m, jb.tiles_s);
         fast_div_make((uint32_t)jb.n_groups, jb.groups_m, jb.groups_s);
         items += job_items;
-        const int tiles = jb.nb == 1 ? jb.cpi : 2;    // operand tiles one stage needs
+        // operand tiles one stage needs: A + a two-block B box for wide items
+        const int tiles = jb.tw == 2 ? 3 : (jb.nb == 1 ? jb.cpi : 2);
         op_tiles = tiles > op_tiles ? tiles : op_tiles;
         raw_tiles = tiles > raw_tiles ? tiles : raw_tiles;
-        any_pair = any_pair || jb.cpi == 2;
+        any_pair = any_pair || jb.cpi == 2 || jb.tw == 2;   // two 256-column accumulator sets
     }
     prm->n_items = items;
     prm->tmem_cols = any_pair ? 512u : 256u;
@@ -1161,7 +1213,21 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
         return launch_jobs<kPlanesBF16x3, 1>(&sp, 1, &mh, &ml, accumulate, p.d_status, p.n_sm, tune, s);
     }
     if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16)) return cudaErrorInvalidValue;
+    // wide items (one N = 256 MMA over blocks J, J + 1) unless the plan asks for single tiles
+    CUtensorMap mw;
+    if (p.nb >= 2 && p.tc_items != 1 && make_plane_map(&mw, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                                       2 * kBlockRows)) {
+        sp.tw = 2;
+        return launch_jobs<kPlanesF16, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s, &mw);
+    }
     return launch_jobs<kPlanesF16, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s);
+}
+
+bool tc_use_planes(const Plan& p) {
+    if (!tc_raw_supported(p)) return true;
+    if (p.tc_operands == 1) return false;
+    if (p.tc_operands == 2) return true;
+    return p.nb >= kPlaneMinBlocks;
 }
 
 bool tc_raw_supported(int n_inputs, int sample_bits) {
@@ -1195,6 +1261,36 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
     if (n_jobs > kMaxJobs) return cudaErrorInvalidValue;
     if (bits == 8) return launch_jobs<kRaw8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
     return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
+}
+
+bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp) {
+    const int nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
+    const int kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    const int64_t rows = (int64_t)sp.n_dumps * sp.n_chan * nb * kBlockRows;
+    if (rows >= (int64_t{1} << 31)) return false;   // TMA row coordinates are int32
+    return make_plane_map(map, sp.data, kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+}
+
+bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp) {
+    const int nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
+    const int kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    const int64_t rows = (int64_t)sp.n_dumps * sp.n_chan * nb * kBlockRows;
+    if (rows >= (int64_t{1} << 31) || rows < 2 * kBlockRows) return false;
+    return make_plane_map(map, sp.data, kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2 * kBlockRows);
+}
+
+cudaError_t launch_xeng_tc_plane_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
+                                      int* status, int n_sm, const TcTuning& tune, cudaStream_t s,
+                                      const CUtensorMap* maps_wide) {
+    if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+    for (int j = 0; j < n_jobs; ++j)
+        if ((specs[j].sample_bits != 4 && specs[j].sample_bits != 8) || specs[j].cpi != 1 ||
+            (specs[j].tw == 2 && !maps_wide))
+            return cudaErrorInvalidValue;
+    if (n_jobs == 1)
+        return launch_jobs<kPlanesF16, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s, maps_wide);
+    return launch_jobs<kPlanesF16, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s,
+                                             maps_wide);
 }
 
 namespace {

@@ -4,12 +4,15 @@ import numpy as np
 from paper_0906_1887_gb300 import synth
 
 
-def run_engine(packed, n, c, t, bits, engine, n_dumps=1, accumulate=False, vis_init=None, tuning=None):
+def run_engine(packed, n, c, t, bits, engine, n_dumps=1, accumulate=False, vis_init=None, tuning=None,
+               operands=None):
     import torch
     from paper_0906_1887_gb300 import corr
     plan = corr.Plan(n, c, t, bits)
     if tuning is not None:
         plan.set_tuning(*tuning)
+    if operands is not None:
+        plan.set_operands(*operands)
     dev = torch.device("cuda:0")
     x = torch.from_numpy(np.ascontiguousarray(packed).view(np.uint8).reshape(-1)).to(dev)
     vis = plan.empty_vis(n_dumps, dev)

@@ -94,3 +94,37 @@ def test_batch_rejects_unaddressable_rows():
     with pytest.raises(corr.CorrError) as e:
         corr.Batch([(17, 4, 10, 8, x, v)])
     assert e.value.status == corr.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batch_plane_path_every_shape_bit_exact(jobs, graph):
+    # the plane operand path (unpack kernel + plane-fed tensor-core kernel) for multi-block jobs,
+    # mixed with the packed-sample path for the others, in every shape the tuner can choose
+    from paper_0906_1887_gb300 import corr
+    b = corr.Batch(_descs(jobs), flags=corr.BATCH_PLANES | (corr.BATCH_GRAPH if graph else 0))
+    info = b.info()
+    assert info["plane_bytes"] > 0 and info["plane_min_nb"] == 4
+    for plane_min_nb, order, ops, wide in [(0, 0, 0, 1), (2, 0, 3, 1), (4, 1, 5, 0), (8, 0, 4, 1), (2, 1, 0, 0)]:
+        b.set_shape(ops, 2, order, plane_min_nb, wide)
+        for j in jobs:
+            j["vis"].fill_(-5)
+        b.run()
+        torch.cuda.synchronize()
+        assert b.check_device() == 0
+        _check(jobs)
+    b.close()
+
+
+def test_batch_autotune_with_planes(jobs):
+    from paper_0906_1887_gb300 import corr
+    b = corr.Batch(_descs(jobs), flags=corr.BATCH_AUTOTUNE | corr.BATCH_PLANES)
+    info = b.info()
+    assert info["tuned"] == 1 and info["plane_min_nb"] in (0, 2, 4, 8) and info["wide"] in (0, 1)
+    for j in jobs:
+        j["vis"].fill_(-5)
+    b.run()
+    torch.cuda.synchronize()
+    _check(jobs)
+    with pytest.raises(corr.CorrError):
+        corr.Batch(_descs(jobs)).set_shape(0, 2, 0, 2, 1)   # planes need CORR_BATCH_PLANES
+    b.close()

@@ -80,6 +80,25 @@ def test_bf16x3_split_in_kernel_matches_planes(n, c, t):
     check_bf16x3(fused, x, n, c, t)
 
 
+# multi-block arrays through both operand feeds and both item shapes of the plane feed: odd and
+# even block counts (wide items end a row with a single tile when nb - I is odd), ragged last
+# blocks, 4- and 8-bit samples, chunk flushes past 1024 samples, several dumps and accumulate
+FEED_CASES = [(128, 2, 100, 8), (192, 3, 130, 8), (256, 2, 64, 4), (320, 1, 1100, 8), (136, 2, 70, 8),
+              (200, 2, 129, 8), (448, 1, 65, 4), (512, 1, 2100, 8), (72, 3, 300, 8), (1000, 1, 64, 8)]
+FEEDS = [(1, 0), (2, 1), (2, 2)]   # (operands, items): packed; planes + single tiles; planes + wide items
+
+
+@pytest.mark.parametrize("feed", FEEDS)
+@pytest.mark.parametrize("n,c,t,bits", FEED_CASES)
+def test_operand_feeds_and_item_shapes_bit_exact(feed, n, c, t, bits):
+    p = np.concatenate([int_case(9000 + n + t + k, n, c, t, bits) for k in range(2)])
+    ref = np.stack([oracle.xcorr_int(p[k * t:(k + 1) * t], n, c, t, bits) for k in range(2)])
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=2, operands=feed)
+    assert np.array_equal(v, ref)
+    v = run_engine(p, n, c, t, bits, TC, n_dumps=2, accumulate=True, vis_init=ref, operands=feed)
+    assert np.array_equal(v, 2 * ref)
+
+
 @pytest.mark.parametrize("n", [64, 192])
 def test_fused_dumps_and_accumulate(n):
     c, t, bits, d = 3, 200, 8, 3
@@ -155,7 +174,7 @@ def test_plane_path_tc_and_fp32(n, c, t, bits):
     ref = oracle.xcorr_int(p, n, c, t, bits)
     plan = corr.Plan(n, c, t, bits)
     x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
-    planes = torch.empty(plan.workspace_size(FP32), dtype=torch.uint8, device="cuda")
+    planes = torch.empty(plan.planes_size(), dtype=torch.uint8, device="cuda")
     plan.unpack(x, planes)
     for engine in (TC, FP32):
         vis = plan.empty_vis(1, "cuda")
@@ -184,25 +203,28 @@ def test_host_pipeline_end_to_end(n, bits, chunk):
     plan.close()
 
 
-def test_unpack_planes_match_oracle_unpack():
+# (n, bits): rows that are whole 16-byte pieces take the vectorised unpack (64, 80, 96, 136 x 2 B;
+# 64, 80, 112 x 1 B, several with a ragged last block), the others the general one
+@pytest.mark.parametrize("n,bits,t", [(70, 4, 100), (70, 8, 100), (64, 8, 100), (136, 8, 130), (96, 8, 64),
+                                      (64, 4, 65), (80, 4, 200), (112, 4, 33), (8, 8, 64), (16, 4, 1)])
+def test_unpack_planes_match_oracle_unpack(n, bits, t):
     from paper_0906_1887_gb300 import corr
-    for bits in (4, 8):
-        n, c, t = 70, 3, 100
-        p = int_case(5 + bits, n, c, t, bits)
-        plan = corr.Plan(n, c, t, bits)
-        x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
-        planes = torch.empty(plan.workspace_size(FP32) // 2, dtype=torch.float16, device="cuda")
-        plan.unpack(x, planes)
-        torch.cuda.synchronize()
-        nb, kp = (n + 63) // 64, (t + 63) // 64 * 64
-        got = planes.cpu().float().numpy().reshape(c, nb, 128, kp)
-        re, im = oracle.unpack(p, n, c, t, bits)                 # [T][C][N]
-        want = np.zeros((c, nb, 128, kp), np.float32)
-        for i in range(n):                                       # row 2r: re, row 2r + 1: im
-            want[:, i // 64, 2 * (i % 64), :t] = re[:, :, i].T
-            want[:, i // 64, 2 * (i % 64) + 1, :t] = im[:, :, i].T
-        assert np.array_equal(got, want)
-        plan.close()
+    c = 3
+    p = int_case(5 + bits + n, n, c, t, bits)
+    plan = corr.Plan(n, c, t, bits)
+    x = torch.from_numpy(p.reshape(-1).view(np.uint8)).cuda()
+    planes = torch.full((plan.planes_size() // 2,), float("nan"), dtype=torch.float16, device="cuda")
+    plan.unpack(x, planes)
+    torch.cuda.synchronize()
+    nb, kp = (n + 63) // 64, (t + 63) // 64 * 64
+    got = planes.cpu().float().numpy().reshape(c, nb, 128, kp)
+    re, im = oracle.unpack(p, n, c, t, bits)                 # [T][C][N]
+    want = np.zeros((c, nb, 128, kp), np.float32)
+    for i in range(n):                                       # row 2r: re, row 2r + 1: im
+        want[:, i // 64, 2 * (i % 64), :t] = re[:, :, i].T
+        want[:, i // 64, 2 * (i % 64) + 1, :t] = im[:, :, i].T
+    assert np.array_equal(got, want)                         # padding included: no NaN left
+    plan.close()
 
 
 def test_float_engines_error_vs_float64():

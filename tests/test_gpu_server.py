@@ -125,3 +125,107 @@ def test_shutdown_cancels_queued_jobs():
     t0 = time.time()
     assert srv.close(drain_timeout_s=5.0) == corr.OK     # nothing was running: prompt return
     assert time.time() - t0 < 5
+
+
+# ---- open streams: device sample rings and accumulators (Fig. 1) ----
+
+def _stream_jobs(seed, k, n, c, t, bits):
+    lo, hi = (-8, 7) if bits == 4 else (-128, 127)
+    packs = []
+    for m in range(k):
+        re, im = synth.uniform_ints(seed + m, t, c, n, lo, hi)
+        packs.append(np.ascontiguousarray(synth.pack(re, im, bits)))
+    return packs
+
+
+@pytest.mark.parametrize("n,c,t,bits,ring", [(64, 12, 300, 8, 2), (96, 5, 130, 4, 3), (40, 6, 100, 8, 1)])
+def test_open_stream_sums_equal_oracle_over_concatenated_samples(n, c, t, bits, ring):
+    # additivity: the k jobs of one interval sum to the correlation of their concatenated samples
+    from paper_0906_1887_gb300 import corr
+    k = 5
+    packs = _stream_jobs(4000 + n, 2 * k, n, c, t, bits)
+    host_in = [torch.from_numpy(p.reshape(-1).view(np.uint8)).pin_memory() for p in packs]
+    P = n * (n + 1) // 2
+    outs = [torch.full((c, P, 2), -1, dtype=torch.int64).pin_memory() for _ in range(2)]
+    srv = corr.Server(256 * MiB, n_streams=2)
+    srv.open_stream(7, n, c, t, bits, ring_slots=ring, jobs_per_dump=k)
+    assert srv.stats()["open_streams"] == 1
+    ids = []
+    for m in range(2 * k):
+        closes = (m + 1) % k == 0
+        ids.append(srv.submit(n, c, t, bits, host_in[m], outs[m // k] if closes else None, stream_tag=7))
+    for m, jid in enumerate(ids):
+        st, r = srv.wait(jid, 60.0)
+        assert st == corr.OK, (m, st, corr.last_error())
+        assert r.closed_interval == int((m + 1) % k == 0)
+        if r.closed_interval:
+            assert r.n_accum == k * t
+        srv.release(jid)
+    for iv in range(2):
+        allp = np.concatenate([packs[iv * k + m].reshape(t, c, -1) for m in range(k)])   # [k t][C][...]
+        ref = oracle.xcorr_int(allp, n, c, k * t, bits)
+        assert np.array_equal(outs[iv].numpy(), ref), iv
+    assert srv.close_stream(7) == corr.OK
+    s = srv.stats()
+    assert s["open_streams"] == 0 and s["bytes_in_use"] == 0 and s["completed"] == 2 * k
+    srv.close()
+
+
+def test_open_stream_averaged_dump_with_phase_correction():
+    from oracle import dump as odump
+    from paper_0906_1887_gb300 import corr
+    n, c, t, bits, k = 64, 8, 256, 8, 3
+    packs = _stream_jobs(4500, k, n, c, t, bits)
+    rng = np.random.default_rng(9)
+    tau = rng.normal(0, 1e-6, n)
+    nu = 1.5e8 + 1e4 * np.arange(c)
+    d_tau = torch.from_numpy(tau).cuda()
+    d_nu = torch.from_numpy(nu).cuda()
+    srv = corr.Server(128 * MiB, n_streams=2)
+    srv.open_stream(3, n, c, t, bits, ring_slots=2, jobs_per_dump=k, dump_mode=corr.STREAM_DUMP_AVERAGED,
+                    delays=d_tau, freqs=d_nu)
+    P = n * (n + 1) // 2
+    out = torch.zeros((c, P, 2), dtype=torch.float32).pin_memory()
+    # host buffers stay alive (and unchanged) until their jobs finish
+    host_in = [torch.from_numpy(p.reshape(-1).view(np.uint8)).pin_memory() for p in packs]
+    ids = [srv.submit(n, c, t, bits, host_in[m], out if m == k - 1 else None, stream_tag=3) for m in range(k)]
+    for jid in ids:
+        st, r = srv.wait(jid, 60.0)
+        assert st == corr.OK, corr.last_error()
+    allp = np.concatenate([p.reshape(t, c, -1) for p in packs])
+    want = odump.dump_corrected(oracle.xcorr_int(allp, n, c, k * t, bits), k * t, tau, nu)
+    got = out.numpy().astype(np.float64)
+    mag = np.hypot(want[..., 0], want[..., 1])
+    assert np.all(np.hypot(*(got - want).transpose(2, 0, 1)) <= 8 * 2.0 ** -24 * mag + 1e-30)
+    # the same stream keeps going: the dump reset the accumulators, so the next interval is fresh
+    ids2 = [srv.submit(n, c, t, bits, host_in[m], out if m == k - 1 else None, stream_tag=3) for m in range(k)]
+    for jid in ids2:
+        assert srv.wait(jid, 60.0)[0] == corr.OK
+    got2 = out.numpy().astype(np.float64)
+    assert np.all(np.hypot(*(got2 - want).transpose(2, 0, 1)) <= 8 * 2.0 ** -24 * mag + 1e-30)
+    srv.close()
+
+
+def test_open_stream_rejections():
+    from paper_0906_1887_gb300 import corr
+    srv = corr.Server(8 * MiB, n_streams=2)
+    with pytest.raises(corr.CorrError) as e:      # state larger than the arena
+        srv.open_stream(1, 1024, 64, 256, 8, ring_slots=2, jobs_per_dump=4)
+    assert e.value.status == corr.EBUSY
+    srv.open_stream(2, 16, 4, 64, 8, ring_slots=2, jobs_per_dump=2)
+    with pytest.raises(corr.CorrError):           # tag already open
+        srv.open_stream(2, 16, 4, 64, 8)
+    j = _job(5, 16, 4, 64, 8)
+    with pytest.raises(corr.CorrError):           # shape differs from the stream's
+        srv.submit(16, 4, 65, 8, j["host_in"], None, stream_tag=2)
+    a = srv.submit(16, 4, 64, 8, j["host_in"], None, stream_tag=2)
+    with pytest.raises(corr.CorrError):           # the interval's last job needs host_vis for the sums
+        srv.submit(16, 4, 64, 8, j["host_in"], None, stream_tag=2)
+    b = srv.submit(16, 4, 64, 8, j["host_in"], j["host_out"], stream_tag=2)
+    assert srv.wait(a, 30.0)[0] == corr.OK and srv.wait(b, 30.0)[0] == corr.OK
+    assert np.array_equal(j["host_out"].numpy(), 2 * j["ref"])
+    # a job of another tag still goes through the arena meanwhile
+    c_ = srv.submit(16, 4, 64, 8, j["host_in"], j["host_out"], stream_tag=9)
+    assert srv.wait(c_, 30.0)[0] == corr.OK and np.array_equal(j["host_out"].numpy(), j["ref"])
+    assert srv.close_stream(2) == corr.OK
+    srv.close()

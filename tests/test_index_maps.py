@@ -103,3 +103,41 @@ def test_dump_row_pairs_cover_every_baseline_once():
             assert np.all(b == np.array([off(ii, n) for ii in i]) + (j - i))
             np.add.at(seen, b, 1)
         assert np.all(seen == 1), n
+
+
+def _pairs_upto(m):
+    """S(m) = sum over k = 1..m of ceil(k / 2): items of m consecutive block rows of lengths 1..m."""
+    return ((m + 1) >> 1) * ((m + 2) >> 1)
+
+
+def _wide_coords(tile, nb):
+    """The kernel's decode of a wide work item: row I holds the items J0 = I, I + 2, ... < nb."""
+    R = _pairs_upto(nb) - tile
+    m = int(np.float32(2.0) * np.sqrt(np.float32(R)) - np.float32(1.5))
+    m = max(0, min(m, nb))
+    while m > 0 and _pairs_upto(m - 1) >= R:
+        m -= 1
+    while _pairs_upto(m) < R:
+        m += 1
+    I = nb - m
+    return I, I + 2 * (tile - (_pairs_upto(nb) - _pairs_upto(m)))
+
+
+def test_wide_item_decode_covers_every_tile_once():
+    # wide items (block I against blocks J0 and J0 + 1 in one N = 256 MMA): every upper-triangle
+    # tile of every array up to 128 blocks belongs to exactly one item, items of a row are
+    # consecutive, and the second block exists unless J0 is the last block
+    for nb in range(1, 129):
+        seen = {}
+        n_items = _pairs_upto(nb)
+        assert n_items == sum((nb - i + 1) // 2 for i in range(nb))
+        prev = (-1, -1)
+        for tile in range(n_items):
+            I, J0 = _wide_coords(tile, nb)
+            assert 0 <= I <= J0 < nb and (J0 - I) % 2 == 0
+            assert (I, J0) > prev
+            prev = (I, J0)
+            for J in range(J0, min(J0 + 2, nb)):
+                assert (I, J) not in seen
+                seen[(I, J)] = tile
+        assert len(seen) == nb * (nb + 1) // 2
