@@ -621,6 +621,49 @@ def run_float(args):
     return out
 
 
+def run_shape(args):
+    """One X stage of a given shape (--shape N,C,T,BITS) through the library's API, with a chosen
+    engine (--engine tc|fp32) and, for the tensor cores, operand feed (--feed auto|packed|planes)
+    and item shape (--items auto|tiles|wide): the launch a profiler capture of one kernel needs."""
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    n, c, t, bits = (int(v) for v in args.shape.split(","))
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    plan = corr.Plan(n, c, t, bits)
+    engine = {"tc": corr.ENGINE_TC, "fp32": corr.ENGINE_FP32}[args.engine]
+    plan.set_operands({"auto": corr.OPERANDS_AUTO, "packed": corr.OPERANDS_PACKED, "planes": corr.OPERANDS_PLANES}[args.feed],
+                      {"auto": corr.ITEMS_AUTO, "tiles": corr.ITEMS_TILES, "wide": corr.ITEMS_WIDE}[args.items])
+    if bits == 4:
+        x = synth.torch_uniform_packed4(1, t, c, n, 7000, dev)
+    elif bits == 8:
+        x = synth.torch_correlated_gaussian_packed8(1, t, c, n, 16.0, 0.0, 7000, dev)
+    else:
+        x = synth.torch_correlated_gaussian_f32(1, t, c, n, 16.0, 0.0, 7000, dev)
+    # the library takes raw pointers: the buffer must hold one dump of this shape
+    if x.numel() * x.element_size() != plan.info()[1]:
+        raise ValueError("sample buffer does not match the plan's packed size")
+    vis = plan.empty_vis(1, dev)
+    ws = plan.empty_workspace(engine, 1, dev) if args.feed != "packed" else None
+    run = lambda: plan.run(x, vis, ws, engine=engine, stream=stream)   # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    ms = _event_ms(run, args.steps, stream)
+    P = plan.n_baselines
+    hbm, bf16, src = _peaks()
+    by = t * c * n * {4: 1, 8: 2, 32: 8}[bits] + (8 if bits == 32 else 16) * P * c
+    out = {"workload": f"shape {n} inputs x {c} channels x {t} samples, {bits}-bit, engine {args.engine}, "
+                       f"feed {args.feed}, items {args.items}",
+           "value": P * c * t / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s", "ms": ms, "steps": args.steps,
+           "tensor_tflops_algorithmic": 8.0 * P * c * t / (ms / 1e3) / 1e12,
+           "hbm_frac": by / (ms / 1e3) / 1e9 / hbm, "algorithmic_bytes": by}
+    plan.close()
+    return out
+
+
 def run_dump(args):
     """Dump step with phase correction (Fig. 1, Sec. 2) on one dump of the 1024-input array's
     accumulators: a pure HBM stream (int64 in, float32 out, zeros back when resetting)."""
@@ -790,7 +833,11 @@ def main():
     ap.add_argument("--dumps", type=int, default=N_DUMPS,
                     help="dumps per step (default: the full 200-dump job; smaller only for profiler captures)")
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "mwa32t", "large", "batch", "serve", "fx", "dump", "float"])
+                    choices=["stream", "mwa32t", "large", "batch", "serve", "fx", "dump", "float", "shape"])
+    ap.add_argument("--shape", default="512,128,2048,8", help="shape workload: N,C,T,BITS")
+    ap.add_argument("--engine", default="tc", choices=["tc", "fp32"], help="shape workload: X engine")
+    ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes"], help="shape workload: operand feed")
+    ap.add_argument("--items", default="auto", choices=["auto", "tiles", "wide"], help="shape workload: item shape")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--no-configs", action="store_true", help="the headline workload only")
     ap.add_argument("--dump-inputs", type=int, default=1024,
@@ -974,7 +1021,7 @@ def main():
 
 
 WORKLOADS = {"mwa32t": run_mwa32t, "large": run_large, "batch": run_batch, "serve": run_serve, "fx": run_fx,
-             "dump": run_dump, "float": run_float}
+             "dump": run_dump, "float": run_float, "shape": run_shape}
 CONFIG_KEYS = {"mwa32t": "mwa32t_4bit", "large": "large1024_8bit", "batch": "batch40", "float": "float_stream",
                "fx": "fx_chain", "serve": "serve"}
 

@@ -132,9 +132,11 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
  *   CORR_OPERANDS_PACKED  always the fused conversion (CORR_EUNSUPPORTED where rows are not
  *                         16-byte multiples);
  *   CORR_OPERANDS_PLANES  always planes (the workspace is then required).
- * items (plane feed): CORR_ITEMS_AUTO / CORR_ITEMS_WIDE = work items of block I against blocks
- * J and J + 1 in one M = 128, N = 256 MMA (a quarter fewer operand loads per tile);
- * CORR_ITEMS_TILES = one 64 x 64 input tile per item.  CORR_EINVAL on unknown values.
+ * items (plane feed): CORR_ITEMS_WIDE = work items of block I against blocks J and J + 1 in one
+ * M = 128, N = 256 MMA (a quarter fewer operand loads per tile); CORR_ITEMS_TILES = one 64 x 64
+ * input tile per item; CORR_ITEMS_AUTO = wide, except single tiles for accumulating dumps of
+ * fewer than 1024 samples (bound by their read-modify-write of the output).  CORR_EINVAL on
+ * unknown values.
  */
 enum { CORR_OPERANDS_AUTO = 0, CORR_OPERANDS_PACKED = 1, CORR_OPERANDS_PLANES = 2 };
 enum { CORR_ITEMS_AUTO = 0, CORR_ITEMS_TILES = 1, CORR_ITEMS_WIDE = 2 };

@@ -101,7 +101,7 @@ struct TcTuning {
     uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };
-int tc_default_cpi(int n_inputs);
+int tc_default_cpi(int n_inputs, int64_t channels, int n_sm);   // channels = dumps x n_chan of the launch
 // BF16x3 on float samples with the hi/lo split done in the tensor-core kernel (single-block arrays)
 bool tc_rawf32_supported(const Plan& p);
 cudaError_t launch_xeng_tc_rawf32(const Plan& p, const void* d_samples, int n_dumps, void* d_vis, int accumulate,

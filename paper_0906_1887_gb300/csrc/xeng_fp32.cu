@@ -233,11 +233,11 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
 // consecutive threads on consecutive inputs (coalesced), converted to float2 (re, im) and stored
 // in shared memory with two pad slots after every four inputs: a thread's four inputs are then
 // two 16-byte loads, and the 16 sub-block columns of a warp hit distinct bank groups in pairs.
-// Exactness for integer samples as in the plane-fed engine above: 64-sample fp32 partials
-// (|Re| <= 2^21), int32 totals over segments of at most 32768 samples, int64 output.
+// Exactness for integer samples as in the plane-fed engine above: one fp32 partial per 64-sample
+// chunk (|Re| <= 2^21), int32 totals over segments of at most 32768 samples, int64 output.
 namespace {
 
-constexpr int kDChunk = 32;            // samples per shared-memory chunk
+constexpr int kDChunk = 64;            // samples per shared-memory chunk (one fp32 partial each)
 constexpr int kDRow = 64 + 32;         // float2 slots per sample row (inputs + pads)
 constexpr int kDiagThreads = 160;      // 136 sub-blocks with gi <= gj, rounded to whole warps
 constexpr int kOffThreads = 256;
@@ -268,14 +268,112 @@ __device__ __forceinline__ void off_tile(int tile, int nb, int& I, int& J) {
     J = i + 1 + rem;
 }
 
+// A chunk of kDChunk samples of the tile's kBlocks 64-input blocks -> float2 rows in shared
+// memory.  Vector form (packed rows of whole 16-byte pieces): every thread issues up to four
+// 16-byte loads before converting any, so their latencies overlap; a piece holds 8 (8-bit),
+// 16 (4-bit) or 2 (float) inputs of one sample.
+template <int BITS, int NBLK, int NT>
+__device__ __forceinline__ void load_chunk_vec(const unsigned char* __restrict__ packed,
+                                               float2 (*s)[kDChunk * kDRow], int tid, int64_t d, int c, int n_chan,
+                                               int n_time, int n_inputs, int t0, int s1, int I, int J) {
+    constexpr int kBps = BITS == 4 ? 1 : (BITS == 8 ? 2 : 8);
+    constexpr int kPieces = 64 * kBps / 16;             // 16-byte pieces per block row
+    constexpr int kPerPiece = 16 / kBps;                // inputs per piece
+    constexpr int kTotal = NBLK * kDChunk * kPieces;
+    const int64_t row_bytes = (int64_t)n_inputs * kBps;
+    for (int base = tid; base < kTotal; base += 4 * NT) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + u * NT;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (k < kTotal) {
+                const int blk = k / (kDChunk * kPieces), rest = k % (kDChunk * kPieces);
+                const int t = rest / kPieces, piece = rest % kPieces;
+                const int i0 = (blk ? J : I) * 64 + piece * kPerPiece;
+                if (t0 + t < s1 && i0 < n_inputs)
+                    v[u] = *reinterpret_cast<const uint4*>(
+                        packed + ((d * n_time + t0 + t) * n_chan + c) * row_bytes + (int64_t)i0 * kBps);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + u * NT;
+            if (k >= kTotal) break;
+            const int blk = k / (kDChunk * kPieces), rest = k % (kDChunk * kPieces);
+            const int t = rest / kPieces, piece = rest % kPieces;
+            float2* row = s[blk] + t * kDRow;
+            const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            if constexpr (BITS == 8) {
+                // 8 inputs: bytes (re, im) pairs; two groups of four contiguous slots
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const uint32_t a = w[2 * g], b = w[2 * g + 1];
+                    float4* dst = reinterpret_cast<float4*>(row + dslot(piece * 8 + 4 * g));
+                    dst[0] = make_float4((float)(signed char)(a & 0xFF), (float)(signed char)((a >> 8) & 0xFF),
+                                         (float)(signed char)((a >> 16) & 0xFF), (float)(signed char)(a >> 24));
+                    dst[1] = make_float4((float)(signed char)(b & 0xFF), (float)(signed char)((b >> 8) & 0xFF),
+                                         (float)(signed char)((b >> 16) & 0xFF), (float)(signed char)(b >> 24));
+                }
+            } else if constexpr (BITS == 4) {
+                // 16 inputs: one byte each, high nibble re, low nibble im; four groups of four
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const uint32_t a = w[g];
+                    float4* dst = reinterpret_cast<float4*>(row + dslot(piece * 16 + 4 * g));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t b0 = (a >> (16 * h)) & 0xFF, b1 = (a >> (16 * h + 8)) & 0xFF;
+                        dst[h] = make_float4((float)((int)(b0 << 24) >> 28), (float)((int)(b0 << 28) >> 28),
+                                             (float)((int)(b1 << 24) >> 28), (float)((int)(b1 << 28) >> 28));
+                    }
+                }
+            } else {
+                // 2 inputs of (re, im) float32: contiguous slots (an even input starts a slot pair)
+                *reinterpret_cast<uint4*>(row + dslot(piece * 2)) = v[u];
+            }
+        }
+    }
+}
+
+// Element-wise form for packed rows that are not whole 16-byte pieces, four loads in flight.
+template <int BITS, int NBLK, int NT>
+__device__ __forceinline__ void load_chunk_scalar(const unsigned char* __restrict__ packed,
+                                                  float2 (*s)[kDChunk * kDRow], int tid, int64_t d, int c, int n_chan,
+                                                  int n_time, int n_inputs, int t0, int s1, int I, int J) {
+    constexpr int kTotal = NBLK * kDChunk * 64;
+    for (int base = tid; base < kTotal; base += 4 * NT) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + u * NT;
+            v[u] = make_float2(0.f, 0.f);
+            if (k < kTotal) {
+                const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
+                const int t = rest >> 6, ig = (blk ? J : I) * 64 + (rest & 63);
+                if (t0 + t < s1 && ig < n_inputs)
+                    v[u] = load_packed<BITS>(packed, ((d * n_time + t0 + t) * n_chan + c) * (int64_t)n_inputs + ig);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + u * NT;
+            if (k >= kTotal) break;
+            const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
+            s[blk][(rest >> 6) * kDRow + dslot(rest & 63)] = v[u];
+        }
+    }
+}
+
 template <int BITS, bool DIAG>
 __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 2)
     xeng_fp32_packed_kernel(const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
-                            int64_t n_items, void* __restrict__ vis, int accumulate) {
+                            int64_t n_items, void* __restrict__ vis, int accumulate, int vec) {
     constexpr bool kInt = BITS != 32;
     constexpr int kThreads = DIAG ? kDiagThreads : kOffThreads;
     constexpr int kBlocks = DIAG ? 1 : 2;            // 64-input blocks per tile
-    __shared__ __align__(16) float2 s[kBlocks][kDChunk * kDRow];
+    extern __shared__ __align__(16) float2 s_dyn[];   // [kBlocks][kDChunk * kDRow]
+    float2 (*s)[kDChunk * kDRow] = reinterpret_cast<float2 (*)[kDChunk * kDRow]>(s_dyn);
     const int tid = threadIdx.x;
     int gi, gj;
     bool active = true;
@@ -322,17 +420,13 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
                     pr[a][b] = pi[a][b] = 0.f;
                     tr[a][b] = ti[a][b] = 0;
                 }
-            int chunk = 0;
             for (int t0 = s0; t0 < s1; t0 += kDChunk) {
                 // load + convert this chunk of the tile's blocks (zero past the last input/sample)
-                for (int k = tid; k < kBlocks * kDChunk * 64; k += kThreads) {
-                    const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
-                    const int t = rest >> 6, i = rest & 63;
-                    const int ig = (blk ? J : I) * 64 + i;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (t0 + t < s1 && ig < n_inputs)
-                        v = load_packed<BITS>(packed, ((d * n_time + t0 + t) * n_chan + c) * (int64_t)n_inputs + ig);
-                    s[blk][t * kDRow + dslot(i)] = v;
+                if (vec) {
+                    load_chunk_vec<BITS, kBlocks, kThreads>(packed, s, tid, d, c, n_chan, n_time, n_inputs, t0, s1, I, J);
+                } else {
+                    load_chunk_scalar<BITS, kBlocks, kThreads>(packed, s, tid, d, c, n_chan, n_time, n_inputs, t0, s1, I,
+                                                               J);
                 }
                 __syncthreads();
                 if (active) {
@@ -357,8 +451,7 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
                     }
                 }
                 __syncthreads();
-                if (++chunk == 2 || t0 + kDChunk >= s1) {   // flush every 64 samples
-                    chunk = 0;
+                {   // flush every chunk of 64 samples
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -414,21 +507,32 @@ template <int BITS>
 cudaError_t launch_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                           cudaStream_t s) {
     const auto* src = static_cast<const unsigned char*>(d_packed);
+    // 16-byte loads when every packed row (and so every block's piece) starts 16-byte aligned
+    const int bps = BITS == 4 ? 1 : (BITS == 8 ? 2 : 8);
+    const int vec = ((int64_t)p.n_inputs * bps) % 16 == 0 && (reinterpret_cast<uintptr_t>(d_packed) & 15u) == 0;
     const int64_t diag_items = (int64_t)n_dumps * p.n_chan * p.nb;
     const int64_t off_items = (int64_t)n_dumps * p.n_chan * (p.nb * (p.nb - 1) / 2);
+    const int smem_diag = kDChunk * kDRow * (int)sizeof(float2);     // 48 KB
+    const int smem_off = 2 * smem_diag;                                // 96 KB
+    cudaError_t e = cudaFuncSetAttribute(xeng_fp32_packed_kernel<BITS, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_diag);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xeng_fp32_packed_kernel<BITS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_off);
+    if (e != cudaSuccess) return e;
     if (diag_items > 0) {
         const int64_t cap = (int64_t)p.n_sm * 3;
         const int grid = (int)(diag_items < cap ? diag_items : cap);
-        xeng_fp32_packed_kernel<BITS, true><<<grid, kDiagThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb,
-                                                                          diag_items, d_vis, accumulate);
+        xeng_fp32_packed_kernel<BITS, true><<<grid, kDiagThreads, smem_diag, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, diag_items, d_vis, accumulate, vec);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (off_items > 0) {
         const int64_t cap = (int64_t)p.n_sm * 2;
         const int grid = (int)(off_items < cap ? off_items : cap);
-        xeng_fp32_packed_kernel<BITS, false><<<grid, kOffThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb,
-                                                                          off_items, d_vis, accumulate);
+        xeng_fp32_packed_kernel<BITS, false><<<grid, kOffThreads, smem_off, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, off_items, d_vis, accumulate, vec);
     }
     return cudaGetLastError();
 }

@@ -49,3 +49,29 @@ def test_fullsize_float_bf16x3_sampled_channels():
     chans = np.random.default_rng(8).choice(c, size=6, replace=False)
     err, _ = check_bf16x3(fused[chans], x, n, c, t, chans=chans)
     assert err <= 1e-4
+
+
+def test_headline_full_launch_sampled_dumps():
+    # the benchmark's whole job in its own launch configuration: 200 dumps of 64 inputs x 768
+    # channels x 1000 samples through one fused launch, inputs from the same seeded device
+    # generator; 24 seeded (dump, channel) pairs recomputed by the oracle from the same bytes
+    from paper_0906_1887_gb300 import corr
+    n, c, t, d = 64, 768, 1000, 200
+    dev = torch.device("cuda:0")
+    packed = synth.torch_correlated_gaussian_packed8(d, t, c, n, 16.0, 0.1, 2000, dev)
+    plan = corr.Plan(n, c, t, 8)
+    vis = plan.empty_vis(d, dev)
+    vis.fill_(-9)
+    plan.run(packed, vis, plan.empty_workspace(corr.ENGINE_TC, d, dev), engine=corr.ENGINE_TC, n_dumps=d)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    rng = np.random.default_rng(11)
+    picks = [(int(rng.integers(0, d)), int(rng.integers(0, c))) for _ in range(24)]
+    for dd, ch in picks:
+        one = packed[dd, :, ch:ch + 1].contiguous().cpu().numpy()          # [T][1][N][2] bytes
+        ref = oracle.xcorr_int(one, n, 1, t, 8)[0]
+        assert np.array_equal(vis[dd, ch].cpu().numpy(), ref), (dd, ch)
+    auto_idx = torch.tensor([i * n - i * (i - 1) // 2 for i in range(n)], device=dev)
+    autos = vis.index_select(2, auto_idx)
+    assert bool((autos[..., 1] == 0).all()) and bool((autos[..., 0] >= 0).all())
+    plan.close()

@@ -42,6 +42,8 @@ CASES = [  # (n, c, t, bits): ragged inputs, tails, several tiles, chunk boundar
     # shapes whose packed rows are 16-byte multiples take the fused packed-sample path
     (8, 2, 100, 8), (16, 3, 64, 4), (32, 2, 1000, 8), (96, 2, 130, 8), (96, 1, 77, 4), (128, 2, 256, 4),
     (192, 1, 65, 8), (200, 1, 100, 8), (64, 3, 2049, 8), (48, 2, 300, 4),
+    # single-block arrays with enough channels for channel-pair items (>= 2 per SM)
+    (64, 320, 100, 8), (32, 331, 64, 4), (16, 400, 130, 8),
 ]
 
 
@@ -283,6 +285,17 @@ def test_invalid_arguments_rejected():
     vis = plan.empty_vis(1, "cuda")
     with pytest.raises(corr.CorrError):            # TC engine takes integer samples only
         plan.run(x, vis, plan.empty_workspace(TC, 1), engine=TC)
+    plan.close()
+    # packed rows of 130 bytes: only the plane feed can read them, so the workspace is required
+    plan = corr.Plan(65, 1, 16, 8)
+    x = torch.zeros(65 * 16 * 2, dtype=torch.uint8, device="cuda")
+    vis = plan.empty_vis(1, "cuda")
+    assert plan.workspace_size(TC) > 0 and plan.workspace_size(FP32) == 0
     with pytest.raises(corr.CorrError):            # missing workspace
-        plan.run(x, vis, None, engine=FP32)
+        plan.run(x, vis, None, engine=TC)
+    with pytest.raises(corr.CorrError) as e:       # the packed feed cannot address these rows
+        plan.set_operands(corr.OPERANDS_PACKED, 0)
+    assert e.value.status == corr.EUNSUPPORTED
+    with pytest.raises(corr.CorrError):
+        plan.set_operands(3, 0)
     plan.close()
