@@ -635,6 +635,8 @@ def run_shape(args):
     engine = {"tc": corr.ENGINE_TC, "fp32": corr.ENGINE_FP32}[args.engine]
     plan.set_operands({"auto": corr.OPERANDS_AUTO, "packed": corr.OPERANDS_PACKED, "planes": corr.OPERANDS_PLANES}[args.feed],
                       {"auto": corr.ITEMS_AUTO, "tiles": corr.ITEMS_TILES, "wide": corr.ITEMS_WIDE}[args.items])
+    if args.op_stages:
+        plan.set_tuning(args.op_stages, 0)
     if bits == 4:
         x = synth.torch_uniform_packed4(1, t, c, n, 7000, dev)
     elif bits == 8:
@@ -656,7 +658,7 @@ def run_shape(args):
     hbm, bf16, src = _peaks()
     by = t * c * n * {4: 1, 8: 2, 32: 8}[bits] + (8 if bits == 32 else 16) * P * c
     out = {"workload": f"shape {n} inputs x {c} channels x {t} samples, {bits}-bit, engine {args.engine}, "
-                       f"feed {args.feed}, items {args.items}",
+                       f"feed {args.feed}, items {args.items}, operand stages {args.op_stages or 'default'}",
            "value": P * c * t / (ms / 1e3) / 1e12, "unit": "TeraCMAC/s", "ms": ms, "steps": args.steps,
            "tensor_tflops_algorithmic": 8.0 * P * c * t / (ms / 1e3) / 1e12,
            "hbm_frac": by / (ms / 1e3) / 1e9 / hbm, "algorithmic_bytes": by}
@@ -838,6 +840,7 @@ def main():
     ap.add_argument("--engine", default="tc", choices=["tc", "fp32"], help="shape workload: X engine")
     ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes"], help="shape workload: operand feed")
     ap.add_argument("--items", default="auto", choices=["auto", "tiles", "wide"], help="shape workload: item shape")
+    ap.add_argument("--op-stages", type=int, default=0, help="shape workload: operand-ring depth (0: default)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--no-configs", action="store_true", help="the headline workload only")
     ap.add_argument("--dump-inputs", type=int, default=1024,

@@ -111,8 +111,9 @@ corr_status corr_plan_info(corr_plan plan, int64_t *n_baselines, size_t *packed_
 /*
  * Launch knobs of the tensor-core kernel for this plan (no counterpart in the paper: they
  * shape the pipeline, not what it computes).  op_stages = depth of the operand ring in shared
- * memory, 0 = the default; a depth that leaves fewer than 3 stages for the sample ring is
- * reduced to what fits.  float_planes (CORR_ENGINE_BF16X3 on float samples): 0 = the
+ * memory, 0 = the default; for the packed feed a depth that leaves fewer than 3 stages for the
+ * sample ring is reduced to what fits; the plane feed uses the requested depth when it is
+ * smaller than what fits (by default as deep as fits).  float_planes (CORR_ENGINE_BF16X3 on float samples): 0 = the
  * default, the tensor-core kernel loads the floats and splits them into bf16 hi + lo itself
  * where it can (arrays of at most 64 inputs, an even count), needing no workspace; 1 = always
  * split into hi/lo planes in the workspace first.  Results are identical for every setting.

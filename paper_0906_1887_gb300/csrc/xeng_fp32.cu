@@ -226,11 +226,13 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
 // The plain form as run by corr_xengine_run: no unpack pass, and no products below the
 // diagonal.  A 64 x 64 tile of input pairs is split into 4 x 4 sub-blocks of contiguous inputs
 // (16 x 16 of them); a thread owns one sub-block: rows 4gi .. 4gi+3, columns 4gj .. 4gj+3, 16
-// complex accumulators.  Off-diagonal tiles (I < J) use 256 threads, one per sub-block; diagonal
-// tiles (I = J) only need the 136 sub-blocks with gi <= gj and run in 160-thread blocks (136
-// working, the rest only load), so the 64-input stream computes 2176 products per 2080 baselines
-// instead of 4096.  Each 32-sample chunk of the tile's one or two 64-input blocks is loaded with
-// consecutive threads on consecutive inputs (coalesced), converted to float2 (re, im) and stored
+// complex accumulators.  Off-diagonal tiles (I < J) use 256 threads, one per sub-block.  Diagonal
+// tiles (I = J) only need the part of the tile on or above the diagonal: there a thread owns a
+// 2 x 4 sub-block (rows 2gi, 2gi + 1), 272 of them meet the upper triangle, and 288-thread blocks
+// (94% of the lanes computing, 8 accumulators each, three blocks per SM) cover them, so the
+// 64-input stream computes 2176 products per 2080 baselines instead of 4096.  Each 64-sample
+// chunk of the tile's one or two 64-input blocks is loaded with consecutive threads on
+// consecutive inputs (coalesced), converted to float2 (re, im) and stored
 // in shared memory with two pad slots after every four inputs: a thread's four inputs are then
 // two 16-byte loads, and the 16 sub-block columns of a warp hit distinct bank groups in pairs.
 // Exactness for integer samples as in the plane-fed engine above: one fp32 partial per 64-sample
@@ -239,7 +241,7 @@ namespace {
 
 constexpr int kDChunk = 64;            // samples per shared-memory chunk (one fp32 partial each)
 constexpr int kDRow = 64 + 32;         // float2 slots per sample row (inputs + pads)
-constexpr int kDiagThreads = 160;      // 136 sub-blocks with gi <= gj, rounded to whole warps
+constexpr int kDiagThreads = 288;      // the 272 2 x 4 sub-blocks of the upper triangle, whole warps
 constexpr int kOffThreads = 256;
 
 __device__ __forceinline__ int dslot(int i) { return i + 2 * (i >> 2); }
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
                             int64_t n_items, void* __restrict__ vis, int accumulate, int vec) {
     constexpr bool kInt = BITS != 32;
     constexpr int kThreads = DIAG ? kDiagThreads : kOffThreads;
+    constexpr int R = DIAG ? 2 : 4;                  // rows (inputs i) of a thread's sub-block; 4 columns
     constexpr int kBlocks = DIAG ? 1 : 2;            // 64-input blocks per tile
     extern __shared__ __align__(16) float2 s_dyn[];   // [kBlocks][kDChunk * kDRow]
     float2 (*s)[kDChunk * kDRow] = reinterpret_cast<float2 (*)[kDChunk * kDRow]>(s_dyn);
@@ -378,15 +381,16 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
     int gi, gj;
     bool active = true;
     if (DIAG) {
-        // tid -> the tid-th sub-block (gi <= gj) in row-major order
+        // tid -> the tid-th needed 2 x 4 sub-block in row-major order: rows 2gi, 2gi + 1 meet the
+        // upper triangle in the column groups gj = floor(gi / 2) .. 15
         int g = 0, rem = tid;
-        while (g < 16 && rem >= 16 - g) {
-            rem -= 16 - g;
+        while (g < 32 && rem >= 16 - (g >> 1)) {
+            rem -= 16 - (g >> 1);
             ++g;
         }
-        active = g < 16;
+        active = g < 32;
         gi = active ? g : 0;
-        gj = active ? g + rem : 0;
+        gj = active ? (g >> 1) + rem : 0;
     } else {
         gi = tid >> 4;
         gj = tid & 15;
@@ -411,10 +415,10 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
         constexpr int kSegment = 32768;
         for (int s0 = 0; s0 < n_time; s0 += kSegment) {
             const int s1 = min(n_time, s0 + kSegment);
-            float pr[4][4], pi[4][4];
-            typename std::conditional<kInt, int, float>::type tr[4][4], ti[4][4];
+            float pr[R][4], pi[R][4];
+            typename std::conditional<kInt, int, float>::type tr[R][4], ti[R][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < R; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     pr[a][b] = pi[a][b] = 0.f;
@@ -432,14 +436,20 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
                 if (active) {
 #pragma unroll 2
                     for (int t = 0; t < kDChunk; ++t) {
-                        const float4 a01 = *reinterpret_cast<const float4*>(sa + t * kDRow + 6 * gi);
-                        const float4 a23 = *reinterpret_cast<const float4*>(sa + t * kDRow + 6 * gi + 2);
+                        // the row inputs R gi .. R gi + R - 1 and column inputs 4 gj .. 4 gj + 3: whole
+                        // 16-byte slot pairs (a group of four inputs never straddles a pad)
+                        float ar[R], ai[R];
+                        const float4 a01 = *reinterpret_cast<const float4*>(sa + t * kDRow + dslot(R * gi));
+                        ar[0] = a01.x, ai[0] = a01.y, ar[1] = a01.z, ai[1] = a01.w;
+                        if constexpr (R == 4) {
+                            const float4 a23 = *reinterpret_cast<const float4*>(sa + t * kDRow + dslot(R * gi) + 2);
+                            ar[2] = a23.x, ai[2] = a23.y, ar[3] = a23.z, ai[3] = a23.w;
+                        }
                         const float4 b01 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj);
                         const float4 b23 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj + 2);
-                        const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
                         const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
 #pragma unroll
-                        for (int x = 0; x < 4; ++x)
+                        for (int x = 0; x < R; ++x)
 #pragma unroll
                             for (int y = 0; y < 4; ++y) {
                                 // x_i conj(x_j): re = ar br + ai bi, im = ai br - ar bi
@@ -453,7 +463,7 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
                 __syncthreads();
                 {   // flush every chunk of 64 samples
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < R; ++a)
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             if constexpr (kInt) {
@@ -470,8 +480,8 @@ __global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 
             if (!active) continue;
             const bool add = accumulate || s0 > 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int i = I * 64 + 4 * gi + a;
+            for (int a = 0; a < R; ++a) {
+                const int i = I * 64 + R * gi + a;
                 if (i >= n_inputs) continue;
                 const int64_t row = dc * P + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i;
 #pragma unroll

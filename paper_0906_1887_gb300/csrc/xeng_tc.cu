@@ -1169,8 +1169,10 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     } else {
         prm->raw_stage_bytes = 0;
         prm->raw_stages = 0;
+        // as deep as fits, or the requested depth when that is smaller
         prm->op_stages = (kSmemBudget - stage_space) / prm->op_stage_bytes;
         if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
+        if (tune.op_stages >= 2 && tune.op_stages < prm->op_stages) prm->op_stages = tune.op_stages;
     }
     if (prm->op_stages < 2 || prm->op_stages > kMaxOpStages) {
         delete prm;
@@ -1206,6 +1208,7 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
     CUtensorMap mh, ml;
     TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_planes, d_vis, 1};
     TcTuning tune{};
+    tune.op_stages = p.tc_op_stages;
     if (d_planes_lo) {
         if (!make_plane_map(&mh, d_planes, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) ||
             !make_plane_map(&ml, d_planes_lo, p.kp, rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16))

@@ -229,3 +229,35 @@ def test_open_stream_rejections():
     assert srv.wait(c_, 30.0)[0] == corr.OK and np.array_equal(j["host_out"].numpy(), j["ref"])
     assert srv.close_stream(2) == corr.OK
     srv.close()
+
+
+def test_large_jobs_issued_in_channel_slices():
+    # a 1024-input job of 40 channels x 2048 samples is issued as X-stage launches over channel
+    # ranges of ~4e10 CMACs (37 + 3 channels here); channels on both sides of the cut match the
+    # oracle, as an arena job and as the two accumulating jobs of an open stream's interval
+    from paper_0906_1887_gb300 import corr
+    n, c, t = 1024, 40, 2048
+    packs = []
+    for k in range(2):
+        re, im = synth.uniform_ints(8100 + k, t, c, n, -128, 127)
+        packs.append(np.ascontiguousarray(synth.pack(re, im, 8)))
+    host_in = [torch.from_numpy(p.reshape(-1).view(np.uint8)).pin_memory() for p in packs]
+    P = n * (n + 1) // 2
+    out = torch.empty((c, P, 2), dtype=torch.int64).pin_memory()
+    chans = [0, 36, 37, 39]
+    srv = corr.Server(4096 * MiB, n_streams=2)
+    jid = srv.submit(n, c, t, 8, host_in[0], out)
+    assert srv.wait(jid, 120.0)[0] == corr.OK, corr.last_error()
+    ref = oracle.xcorr_int(packs[0], n, c, t, 8, chans=chans)
+    for k, ch in enumerate(chans):
+        assert np.array_equal(out.numpy()[ch], ref[k]), ch
+    srv.release(jid)
+    srv.open_stream(5, n, c, t, 8, ring_slots=2, jobs_per_dump=2)
+    out.fill_(-1)
+    ids = [srv.submit(n, c, t, 8, host_in[0], None, stream_tag=5), srv.submit(n, c, t, 8, host_in[1], out, stream_tag=5)]
+    for i in ids:
+        assert srv.wait(i, 120.0)[0] == corr.OK, corr.last_error()
+    ref = oracle.xcorr_int(np.concatenate([p.reshape(t, c, -1) for p in packs]), n, c, 2 * t, 8, chans=chans)
+    for k, ch in enumerate(chans):
+        assert np.array_equal(out.numpy()[ch], ref[k]), ch
+    srv.close()
