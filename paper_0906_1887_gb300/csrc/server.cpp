@@ -18,7 +18,6 @@
 // their arena blocks and wakes waiters.  All host waits are bounded; the kernels' own waits
 // are bounded and report through the status words.
 #include <algorithm>
-#include <cmath>
 #include <atomic>
 #include <cstdint>
 #include <chrono>
@@ -31,8 +30,6 @@
 #include <thread>
 #include <unordered_map>
 #include <vector>
-
-#include <cuda_fp16.h>
 
 #include "corr_internal.h"
 
@@ -244,22 +241,7 @@ cudaError_t run_x(const Plan& p, const corr_job_desc& d, bool raw, const char* d
         return e == cudaSuccess ? launch_xeng_tc(p, d_ws, d_ws + half, 1, d_vis, accumulate, s) : e;
     }
     cudaError_t e = launch_unpack_fp16(p, d_packed, 1, d_ws, s);
-    if (e != cudaSuccess) return e;
-    // A large job's X stage is issued as several launches over consecutive channel ranges (the
-    // planes and the visibilities of a channel are contiguous), each of about kSliceCmac CMACs
-    // (~1 ms): a persistent kernel holds every SM until it ends, so these launch boundaries are
-    // where the GPU can take another stream's more urgent kernel first.
-    constexpr double kSliceCmac = 4.0e10;
-    const double per_chan = (double)p.n_baselines * p.n_time;
-    const int chans = (int)std::max(1.0, std::min((double)p.n_chan, std::floor(kSliceCmac / per_chan)));
-    const size_t plane_chan = (size_t)p.nb * kBlockRows * p.kp;   // fp16 elements of one channel's planes
-    for (int c0 = 0; c0 < p.n_chan && e == cudaSuccess; c0 += chans) {
-        Plan q = p;
-        q.n_chan = std::min(chans, p.n_chan - c0);
-        e = launch_xeng_tc(q, reinterpret_cast<const __half*>(d_ws) + (size_t)c0 * plane_chan, nullptr, 1,
-                           static_cast<char*>(d_vis) + (size_t)c0 * (size_t)p.n_baselines * 16, accumulate, s);
-    }
-    return e;
+    return e == cudaSuccess ? launch_xeng_tc(p, d_ws, nullptr, 1, d_vis, accumulate, s) : e;
 }
 
 // Issue one admitted job on its stream (called with the lock released).

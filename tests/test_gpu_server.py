@@ -231,10 +231,10 @@ def test_open_stream_rejections():
     srv.close()
 
 
-def test_large_jobs_issued_in_channel_slices():
-    # a 1024-input job of 40 channels x 2048 samples is issued as X-stage launches over channel
-    # ranges of ~4e10 CMACs (37 + 3 channels here); channels on both sides of the cut match the
-    # oracle, as an arena job and as the two accumulating jobs of an open stream's interval
+def test_large_job_on_the_plane_feed():
+    # a 1024-input job of 40 channels x 2048 samples (the plane feed with wide items) matches the
+    # oracle on sampled channels, as an arena job and as the two accumulating jobs of an open
+    # stream's interval
     from paper_0906_1887_gb300 import corr
     n, c, t = 1024, 40, 2048
     packs = []
