@@ -138,7 +138,9 @@ def _stream_jobs(seed, k, n, c, t, bits):
     return packs
 
 
-@pytest.mark.parametrize("n,c,t,bits,ring", [(64, 12, 300, 8, 2), (96, 5, 130, 4, 3), (40, 6, 100, 8, 1)])
+@pytest.mark.parametrize("n,c,t,bits,ring", [(64, 12, 300, 8, 2), (96, 5, 130, 4, 3), (40, 6, 100, 8, 1),
+                                             # the plane feed: rows of 130 bytes; 256 inputs of 4 bits
+                                             (65, 3, 200, 8, 2), (256, 2, 70, 4, 2)])
 def test_open_stream_sums_equal_oracle_over_concatenated_samples(n, c, t, bits, ring):
     # additivity: the k jobs of one interval sum to the correlation of their concatenated samples
     from paper_0906_1887_gb300 import corr
@@ -261,3 +263,36 @@ def test_large_job_on_the_plane_feed():
     for k, ch in enumerate(chans):
         assert np.array_equal(out.numpy()[ch], ref[k]), ch
     srv.close()
+
+
+def test_close_stream_bounded_when_jobs_cannot_run():
+    # host-made failure: the dispatcher is paused, so the stream's queued jobs never start;
+    # close_stream gives up after its bound, cancels them and the server stays usable
+    from paper_0906_1887_gb300 import corr
+    srv = corr.Server(64 * MiB, n_streams=2, flags=corr.SERVER_START_PAUSED)
+    srv.open_stream(4, 32, 4, 64, 8, ring_slots=2, jobs_per_dump=2)
+    j = _job(6, 32, 4, 64, 8)
+    a = srv.submit(32, 4, 64, 8, j["host_in"], None, stream_tag=4)
+    b = srv.submit(32, 4, 64, 8, j["host_in"], j["host_out"], stream_tag=4)
+    t0 = time.time()
+    assert srv.close_stream(4, drain_timeout_s=0.2) == corr.ETIMEOUT
+    assert time.time() - t0 < 20
+    assert srv.poll(a)[0] == corr.EBUSY and srv.poll(b)[0] == corr.EBUSY     # cancelled
+    assert srv.stats()["open_streams"] == 0 and srv.stats()["bytes_in_use"] == 0
+    # the tag is free again and the server still runs jobs once resumed
+    srv.resume()
+    c_ = srv.submit(32, 4, 64, 8, j["host_in"], j["host_out"], stream_tag=4)
+    assert srv.wait(c_, 30.0)[0] == corr.OK and np.array_equal(j["host_out"].numpy(), j["ref"])
+    srv.close()
+
+
+def test_destroy_with_open_streams_and_queued_jobs():
+    from paper_0906_1887_gb300 import corr
+    srv = corr.Server(64 * MiB, n_streams=2)
+    srv.open_stream(1, 64, 8, 256, 8, ring_slots=3, jobs_per_dump=4)
+    srv.open_stream(2, 16, 4, 64, 4, ring_slots=1, jobs_per_dump=1, dump_mode=corr.STREAM_DUMP_AVERAGED)
+    j = _job(7, 64, 8, 256, 8)
+    k = _job(8, 16, 4, 64, 4)
+    ids = [srv.submit(64, 8, 256, 8, j["host_in"], None, stream_tag=1) for _ in range(3)]
+    ids += [srv.submit(16, 4, 64, 4, k["host_in"], None, stream_tag=2) for _ in range(3)]
+    assert srv.close(drain_timeout_s=30.0) == corr.OK
