@@ -548,6 +548,9 @@ def run_fx(args):
            "real_time_factor": 1000.0 / ms,
            "bf16x3_chain": {"ms_per_step": res["bf16x3"], "value": cm / (res["bf16x3"] / 1e3) / 1e12,
                             "real_time_factor": 1000.0 / res["bf16x3"]},
+           # Table 4's actual column: the 1.28 MHz band processed in this time per second of data
+           "processed_bandwidth_mhz": {"fp32_chain": 1.28 / (ms / 1e3), "bf16x3_chain": 1.28 / (res["bf16x3"] / 1e3),
+                                       "paper_c1060_gp4_mhz": 6.9},
            "fstage": {"kernel": "fengine_kernel<complex8>", "ms": f_ms, "bound": "hbm", "achieved": gbs,
                       "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": f_bytes,
                       "peak_source": src},
@@ -860,7 +863,7 @@ def main():
 
     import torch
 
-    from paper_0906_1887_gb300 import corr, synth
+    from paper_0906_1887_gb300 import corr, metrics, synth
 
     if args.dumps != N_DUMPS:
         WORKLOAD = WORKLOAD.replace("x 200 dumps", f"x {args.dumps} dumps (reduced for profiling)")
@@ -1006,6 +1009,11 @@ def main():
                    "n_dumps": N_DUMPS, "sample_bits": BITS, "engine": "fused tcgen05 X stage: packed 8-bit -> fp16 in shared memory, fp32 accum, exact int64",
                    "l2": "inputs (19.7 GB per step) far larger than L2; no flush", "parallelism": f"replicas{world}"},
         "real_time_factor": rtf,
+        # Table 4's measure: the signal bandwidth these CMAC rates would sustain for the paper's
+        # 64-input system (B = CMAC/s / 2080); the paper's best, GP4 on a Tesla C1060, processed 6.9 MHz
+        "signal_bandwidth_mhz_at_64_inputs": {"device_resident": metrics.mhz_at_64_inputs(value),
+                                              "e2e": metrics.mhz_at_64_inputs(e2e_value),
+                                              "paper_c1060_gp4_mhz": 6.9},
         "fp32_path": {"value": value32, "unit": "TeraCMAC/s", "ms_per_step": ms32, "speedup_tc_over_fp32": value / value32},
         "e2e": {"value": e2e_value, "unit": "TeraCMAC/s", "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": h2d_bytes,

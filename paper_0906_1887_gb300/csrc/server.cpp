@@ -691,14 +691,15 @@ corr_status corr_server_destroy(corr_server S, double drain_timeout_s) {
         S->stop = true;
         S->cv_dispatch.notify_all();
     }
-    // the streams must be idle before the arena goes away: wait for them (the kernels'
-    // own waits are bounded, so this returns)
+    // the dispatcher issues nothing more once it sees stop (it may be finishing one issue now);
+    // then the streams must be idle before the arena goes away: wait for them (the kernels' own
+    // waits are bounded, so this returns), and the completion thread retires what is left
+    S->dispatcher.join();
     for (auto st : S->streams) cudaStreamSynchronize(st);
     for (auto& kv : S->open_streams) {
         cudaStreamSynchronize(kv.second->copy_s);
         cudaStreamSynchronize(kv.second->comp_s);
     }
-    S->dispatcher.join();
     S->completer.join();
     for (auto& kv : S->jobs) {
         if (kv.second.ev_start) cudaEventDestroy(kv.second.ev_start);
