@@ -4,7 +4,11 @@
 // through shared memory so each global read feeds several products, with consecutive
 // threads on consecutive data so every access is coalesced, and accumulates over a
 // large batch in registers (Sec. 4, last paragraphs).  The same ideas, sized for an
-// sm_103a SM: a block owns a 64 x 64 tile of input pairs of one channel, stages 32
+// sm_103a SM.  This file holds three kernels: the plane-fed one right below (fp16/fp32
+// planes written by the unpack pass), and two that read the packed samples themselves
+// (float32 samples; 4/8-bit samples), further down.
+//
+// Plane-fed kernel: a block owns a 64 x 64 tile of input pairs of one channel, stages 32
 // time samples of both 64-input blocks in shared memory, and each thread keeps a 4 x 4
 // register tile of complex accumulators (16 products per 16 shared-memory reads per
 // sample).  Tiles cover the upper triangle i <= j only.
@@ -224,7 +228,8 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
 // ---- FP32 CUDA-core engine reading the packed samples directly ----------------------------
 //
 // The plain form as run by corr_xengine_run: no unpack pass, and no products below the
-// diagonal.  A 64 x 64 tile of input pairs is split into 4 x 4 sub-blocks of contiguous inputs
+// diagonal.  Float32 samples use the kernel of this section; 4/8-bit samples the 4 x 8
+// sub-block kernel of the next one.  A 64 x 64 tile of input pairs is split into 4 x 4 sub-blocks of contiguous inputs
 // (16 x 16 of them); a thread owns one sub-block: rows 4gi .. 4gi+3, columns 4gj .. 4gj+3, 16
 // complex accumulators.  Off-diagonal tiles (I < J) use 256 threads, one per sub-block.  Diagonal
 // tiles (I = J) only need the part of the tile on or above the diagonal: there a thread owns a
@@ -531,7 +536,7 @@ cudaError_t launch_packed(const Plan& p, const void* d_packed, int n_dumps, void
                                  smem_off);
     if (e != cudaSuccess) return e;
     if (diag_items > 0) {
-        const int64_t cap = (int64_t)p.n_sm * 3;
+        const int64_t cap = (int64_t)p.n_sm * 2;
         const int grid = (int)(diag_items < cap ? diag_items : cap);
         xeng_fp32_packed_kernel<BITS, true><<<grid, kDiagThreads, smem_diag, s>>>(
             src, p.n_inputs, p.n_chan, p.n_time, p.nb, diag_items, d_vis, accumulate, vec);
@@ -547,12 +552,421 @@ cudaError_t launch_packed(const Plan& p, const void* d_packed, int n_dumps, void
     return cudaGetLastError();
 }
 
+// ---- integer samples: 4 x 8 register sub-blocks, several channels per block ----
+//
+// For 4/8-bit samples a thread owns a 4 x 8 sub-block (rows 4g .. 4g+3, columns 8h .. 8h+7, 32
+// complex accumulators): per sample it reads 12 float2 operands with six 16-byte loads for 128
+// FFMAs, against three loads per 32 FFMAs for 2 x 4, so shared memory is no longer the limit.
+// Only fp32 partial sums stay in registers; they are exact integers for a whole segment (8-bit:
+// |Re| <= 2 * 128^2 = 2^15 per sample, so 512 samples keep every partial within 2^24; 4-bit:
+// |Re| <= 2^7, segments of 32768 samples) and each segment is added into the int64 output in
+// place.  An off-diagonal 64 x 64 tile is 128 sub-blocks; a diagonal tile's upper triangle is 56
+// sub-blocks (the strictly-upper 8 x 8 blocks) and 8 triangle threads (the 8 x 8 blocks on the
+// diagonal, 28 pairs and 8 autos each: the same 128 FFMAs), so no lane idles and no product
+// falls below the diagonal.  A block runs four (diagonal, 256 threads) or two (off-diagonal, 256
+// threads) channel-dumps of the same tile side by side, two blocks per SM at 128 registers a
+// thread; what the loop does not need (the tile, the channel group, sizes) lives in shared
+// memory or the kernel parameters, not in registers.  Sample rows in shared memory carry two pad
+// slots after every eight inputs, so the eight column groups of a quarter-warp fall in distinct
+// bank groups and a row group's loads are broadcasts.  The packed bytes of the next 32-sample
+// chunk are copied asynchronously (cp.async, no registers) while the block computes the current
+// one, then converted to float2 rows in shared memory.
+constexpr int kIChunk = 32;                          // samples per shared-memory chunk
+constexpr int kIRow = 80;                            // float2 slots per sample row (64 + 16 pads)
+constexpr int kIDiagCh = 4;
+constexpr int kIOffCh = 2;
+constexpr int kIDiagThreads = kIDiagCh * 64;         // 4 x (56 sub-blocks + 8 triangles)
+constexpr int kIOffThreads = kIOffCh * 128;          // 256
+
+__device__ __forceinline__ int islot(int i) { return i + 2 * (i >> 3); }
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int BITS, int NBLK>
+struct IShape {
+    static constexpr int kBps = BITS == 4 ? 1 : 2;        // packed bytes per input sample
+    static constexpr int kPieces = 64 * kBps / 16;        // 16-byte pieces per 64-input block row
+    static constexpr int kPerPiece = 16 / kBps;           // inputs per piece
+    static constexpr int kPerCh = NBLK * kIChunk * kPieces;   // pieces per channel-dump and chunk
+};
+
+// Raw staging of one chunk (vector form: packed rows of whole 16-byte pieces).  Piece k of the
+// chunk is (q, t, blk, piece) with piece fastest; channel-dump q's packed row of sample t starts
+// at element base[q] + t * tstride (base[q] < 0: past the last channel-dump, zero fill), and so
+// do inputs past the last one and samples past s1.
+template <int BITS, int NBLK, int KCH, int NT>
+__device__ __forceinline__ void istage(const unsigned char* __restrict__ packed, uint4* __restrict__ raw,
+                                       const int64_t* __restrict__ base, int64_t tstride, int tid, int n_inputs,
+                                       int t0, int s1, int I, int J) {
+    using S = IShape<BITS, NBLK>;
+    for (int k = tid; k < KCH * S::kPerCh; k += NT) {
+        const int q = k / S::kPerCh, r = k % S::kPerCh;
+        const int piece = r % S::kPieces, blk = (r / S::kPieces) % NBLK, t = r / (S::kPieces * NBLK);
+        const int i0 = (blk ? J : I) * 64 + piece * S::kPerPiece;
+        const int64_t b = base[q];
+        const unsigned char* src = packed;
+        int bytes = 0;
+        if (b >= 0 && t0 + t < s1 && i0 < n_inputs) {
+            src = packed + (b + (int64_t)(t0 + t) * tstride + i0) * S::kBps;
+            bytes = 16;
+        }
+        cp_async16(raw + k, src, bytes);
+    }
+}
+
+// raw pieces -> float2 rows s[((q * NBLK + blk) * kIChunk + t) * kIRow + islot(i)].
+template <int BITS, int NBLK, int KCH, int NT>
+__device__ __forceinline__ void iconvert(const uint4* __restrict__ raw, float2* __restrict__ s, int tid) {
+    using S = IShape<BITS, NBLK>;
+    for (int k = tid; k < KCH * S::kPerCh; k += NT) {
+        const int q = k / S::kPerCh, r = k % S::kPerCh;
+        const int piece = r % S::kPieces, blk = (r / S::kPieces) % NBLK, t = r / (S::kPieces * NBLK);
+        float2* row = s + ((q * NBLK + blk) * kIChunk + t) * kIRow;
+        const uint4 v = raw[k];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        if constexpr (BITS == 8) {
+            // 8 inputs of (re, im) bytes: eight contiguous slots.  Byte b -> float without an integer
+            // conversion: b + 128 (the XOR with 0x80) placed in the low mantissa bits of 2^23 is the
+            // float 2^23 + b + 128 exactly; subtracting 2^23 + 128 leaves b (IEEE-754 binary32)
+            float4* dst = reinterpret_cast<float4*>(row + islot(piece * 8));
+            constexpr float kOff = 8388736.0f;   // 2^23 + 128
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const uint32_t wb = w[x] ^ 0x80808080u;
+                dst[x] = make_float4(__uint_as_float(__byte_perm(wb, 0x4Bu, 0x4550)) - kOff,
+                                     __uint_as_float(__byte_perm(wb, 0x4Bu, 0x4551)) - kOff,
+                                     __uint_as_float(__byte_perm(wb, 0x4Bu, 0x4552)) - kOff,
+                                     __uint_as_float(__byte_perm(wb, 0x4Bu, 0x4553)) - kOff);
+            }
+        } else {
+            // 16 inputs, one byte each (high nibble re, low nibble im): two groups of eight
+#pragma unroll
+            for (int gg = 0; gg < 2; ++gg) {
+                float4* dst = reinterpret_cast<float4*>(row + islot(piece * 16 + 8 * gg));
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const uint32_t a = w[2 * gg + (x >> 1)] >> (16 * (x & 1));
+                    const uint32_t b0 = a & 0xFF, b1 = (a >> 8) & 0xFF;
+                    dst[x] = make_float4((float)((int)(b0 << 24) >> 28), (float)((int)(b0 << 28) >> 28),
+                                         (float)((int)(b1 << 24) >> 28), (float)((int)(b1 << 28) >> 28));
+                }
+            }
+        }
+    }
+}
+
+// Element-wise form for packed rows that are not whole 16-byte pieces (one load at a time: the
+// accumulators stay in registers meanwhile).
+template <int BITS, int NBLK, int KCH, int NT>
+__device__ __forceinline__ void iload_scalar(const unsigned char* __restrict__ packed, float2* __restrict__ s,
+                                             const int64_t* __restrict__ base, int64_t tstride, int tid,
+                                             int n_inputs, int t0, int s1, int I, int J) {
+    constexpr int kPerCh = NBLK * kIChunk * 64;
+    for (int k = tid; k < KCH * kPerCh; k += NT) {
+        const int q = k / kPerCh, r = k % kPerCh;
+        const int x = r & 63, blk = (r >> 6) % NBLK, t = r / (64 * NBLK);
+        const int ig = (blk ? J : I) * 64 + x;
+        const int64_t b = base[q];
+        float2 v = make_float2(0.f, 0.f);
+        if (b >= 0 && t0 + t < s1 && ig < n_inputs) v = load_packed<BITS>(packed, b + (int64_t)(t0 + t) * tstride + ig);
+        s[((q * NBLK + blk) * kIChunk + t) * kIRow + islot(x)] = v;
+    }
+}
+
+// one sample's operands of a 4 x 8 sub-block: rows (4 inputs) and four of the eight columns
+struct IRows {
+    float r[4], i[4];
+};
+__device__ __forceinline__ IRows ild4(const float2* p) {
+    const float4 u = *reinterpret_cast<const float4*>(p), v = *reinterpret_cast<const float4*>(p + 2);
+    return IRows{{u.x, u.z, v.x, v.z}, {u.y, u.w, v.y, v.w}};
+}
+// x_i conj(x_j) into columns y0 .. y0 + 3 of a 4 x 8 sub-block: re = ar br + ai bi into
+// acc[8x + y], im = ai br - ar bi into acc[32 + 8x + y]
+__device__ __forceinline__ void icmac(float (&acc)[64], const IRows& a, const IRows& b, int y0) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            float& r = acc[8 * x + y0 + y];
+            float& m = acc[32 + 8 * x + y0 + y];
+            r = fmaf(a.r[x], b.r[y], r);
+            r = fmaf(a.i[x], b.i[y], r);
+            m = fmaf(a.i[x], b.r[y], m);
+            m = fmaf(-a.r[x], b.i[y], m);
+        }
+}
+
+// The upper triangle of an 8 x 8 diagonal block (inputs v[0..7]): the 28 pairs x < y (pair k in
+// row-major order: re acc[2k], im acc[2k + 1]) and the 8 autos (acc[56 + x]; their imaginary part
+// is zero and not computed): 128 FFMAs, as for a 4 x 8 sub-block.
+__device__ __host__ constexpr int tri_pair(int x, int y) { return x * 7 - x * (x - 1) / 2 + (y - x - 1); }
+__device__ __forceinline__ void itri(float (&acc)[64], const IRows& lo, const IRows& hi) {
+    float r[8], m[8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        r[x] = lo.r[x], m[x] = lo.i[x];
+        r[4 + x] = hi.r[x], m[4 + x] = hi.i[x];
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        acc[56 + x] = fmaf(r[x], r[x], acc[56 + x]);
+        acc[56 + x] = fmaf(m[x], m[x], acc[56 + x]);
+#pragma unroll
+        for (int y = x + 1; y < 8; ++y) {
+            float& re = acc[2 * tri_pair(x, y)];
+            float& im = acc[2 * tri_pair(x, y) + 1];
+            re = fmaf(r[x], r[y], re);
+            re = fmaf(m[x], m[y], re);
+            im = fmaf(m[x], r[y], im);
+            im = fmaf(-r[x], m[y], im);
+        }
+    }
+}
+
+// A thread's work in a block.  Off-diagonal tiles: two channel-dumps (q) x 128 sub-blocks of 4 x 8
+// (row group g = loc / 8, column group h = loc % 8).  Diagonal tiles: the 64 x 64 upper triangle
+// is 28 strictly-upper 8 x 8 blocks (R < C), each two 4 x 8 sub-blocks (rows 8R .. 8R+3 and
+// 8R+4 .. 8R+7), and 8 diagonal 8 x 8 triangles; four channel-dumps give 224 sub-block threads
+// (seven warps) and 32 triangle threads (the eighth warp): no idle lane and no product below the
+// diagonal.
+template <bool DIAG>
+struct ISub {
+    int q, g, h;       // channel-dump, row group (4 inputs), column group (8 inputs)
+    bool tri;          // diagonal tiles: the triangle of the 8-input block h
+    __device__ __forceinline__ explicit ISub(int tid) {
+        if (DIAG) {
+            tri = tid >= kIDiagCh * 56;
+            if (tri) {
+                q = (tid - kIDiagCh * 56) >> 3;
+                g = 0;
+                h = (tid - kIDiagCh * 56) & 7;
+            } else {
+                q = tid / 56;
+                const int loc = tid % 56, pair = loc >> 1;
+                int R = 0, rem = pair;
+                while (rem >= 7 - R) {
+                    rem -= 7 - R;
+                    ++R;
+                }
+                g = 2 * R + (loc & 1);
+                h = R + 1 + rem;
+            }
+        } else {
+            tri = false;
+            q = tid >> 7;
+            g = (tid & 127) >> 3;
+            h = tid & 7;
+        }
+    }
+};
+
+// The block's current work item, kept in shared memory rather than registers: the sample loop
+// needs every register it can get for accumulators and operands, and these values are only read
+// between chunks (staging) and at the end of a segment (the flush).
+template <int KCH>
+struct IItem {
+    int64_t base[KCH];   // element offset of each channel-dump's sample-0 row; -1 past the last one
+    int64_t dc0;         // first channel-dump of the group
+    int I, J;            // tile: input blocks of the rows and of the columns
+};
+
+// One exact partial into the int64 output: the first segment stores (or, accumulating, adds);
+// later segments add with fire-and-forget 64-bit reductions (no old values in registers; each
+// output element has one writing thread, so program order keeps the sum).
+__device__ __forceinline__ void iflush(longlong2* dst, float re, float im, bool add) {
+    const long long r = __float2int_rn(re), m = __float2int_rn(im);
+    if (add) {
+        unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+        atomicAdd(d, (unsigned long long)r);
+        atomicAdd(d + 1, (unsigned long long)m);
+    } else {
+        *dst = make_longlong2(r, m);
+    }
+}
+
+// VEC: packed rows of whole 16-byte pieces (staged copies); otherwise element-wise loads.
+// P = baselines per channel-dump, tstride = elements from one sample row to the next.
+template <int BITS, bool DIAG, bool VEC>
+__global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
+    xeng_fp32_int_kernel(const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
+                         int n_tiles, int64_t P, int64_t tstride, int64_t n_dc, int64_t n_items,
+                         longlong2* __restrict__ vis, int accumulate) {
+    constexpr int kCh = DIAG ? kIDiagCh : kIOffCh;
+    constexpr int kThreads = DIAG ? kIDiagThreads : kIOffThreads;
+    constexpr int NBLK = DIAG ? 1 : 2;
+    constexpr int kSeg = BITS == 8 ? 512 : 32768;    // exact fp32 partials (see above)
+    // [kCh][NBLK][kIChunk][kIRow] float2 rows, then the raw pieces of one chunk, then the item
+    extern __shared__ __align__(16) float2 s_dyn[];
+    uint4* raw = reinterpret_cast<uint4*>(s_dyn + kCh * NBLK * kIChunk * kIRow);
+    IItem<kCh>* item_s = reinterpret_cast<IItem<kCh>*>(raw + kCh * IShape<BITS, NBLK>::kPerCh);
+    const volatile IItem<kCh>* info = item_s;
+    const int tid = threadIdx.x;
+    const float2 *sa, *sb;
+    bool tri;
+    {
+        const ISub<DIAG> u(tid);
+        tri = u.tri;
+        sa = s_dyn + (u.q * NBLK) * kIChunk * kIRow + (u.tri ? islot(8 * u.h) : islot(4 * u.g));
+        sb = s_dyn + (u.q * NBLK + NBLK - 1) * kIChunk * kIRow + islot(8 * u.h);
+    }
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (tid == 0) {
+            const int tile = (int)(item % n_tiles);
+            int I, J;
+            if (DIAG) {
+                I = J = tile;
+            } else {
+                off_tile(tile, nb, I, J);
+            }
+            item_s->I = I;
+            item_s->J = J;
+            item_s->dc0 = item / n_tiles * kCh;
+        }
+        if (tid < kCh) {
+            const int64_t e = item / n_tiles * kCh + tid;
+            item_s->base[tid] = e < n_dc ? ((e / n_chan) * n_time * n_chan + e % n_chan) * (int64_t)n_inputs : -1;
+        }
+        __syncthreads();
+        for (int s0 = 0; s0 < n_time; s0 += kSeg) {
+            const int s1 = min(n_time, s0 + kSeg);
+            float acc[64];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+            if (VEC && s0 == 0)
+                istage<BITS, NBLK, kCh, kThreads>(packed, raw, item_s->base, tstride, tid, n_inputs, 0, s1, info->I,
+                                                  info->J);
+            cp_async_commit();
+            for (int t0 = s0; t0 < s1; t0 += kIChunk) {
+                if constexpr (VEC) {
+                    // raw holds this chunk (staged one chunk ahead); every thread is past the
+                    // previous chunk's products, so the rows may be overwritten
+                    cp_async_wait_all();
+                    __syncthreads();
+                    iconvert<BITS, NBLK, kCh, kThreads>(raw, s_dyn, tid);
+                    __syncthreads();
+                    // stage the next chunk: the rest of this segment, then the next segment's first
+                    const int tn = t0 + kIChunk;
+                    if (tn < n_time)
+                        istage<BITS, NBLK, kCh, kThreads>(packed, raw, item_s->base, tstride, tid, n_inputs, tn,
+                                                          tn < s1 ? s1 : min(n_time, s1 + kSeg), info->I, info->J);
+                    cp_async_commit();
+                } else {
+                    __syncthreads();
+                    iload_scalar<BITS, NBLK, kCh, kThreads>(packed, s_dyn, item_s->base, tstride, tid, n_inputs, t0,
+                                                            s1, info->I, info->J);
+                    __syncthreads();
+                }
+                // (a register-prefetching pipeline across samples measured slower: the other
+                // resident warps already cover the shared-memory latency)
+                if (DIAG && tri) {   // warp-uniform
+#pragma unroll 1
+                    for (int t = 0; t < kIChunk; ++t) itri(acc, ild4(sa + t * kIRow), ild4(sa + t * kIRow + 4));
+                } else {
+#pragma unroll 1
+                    for (int t = 0; t < kIChunk; ++t) {
+                        const IRows a = ild4(sa + t * kIRow), b0 = ild4(sb + t * kIRow), b1 = ild4(sb + t * kIRow + 4);
+                        icmac(acc, a, b0, 0);
+                        icmac(acc, a, b1, 4);
+                    }
+                }
+            }
+            const ISub<DIAG> u(tid);
+            const int64_t dc = info->dc0 + u.q;
+            if (dc >= n_dc) continue;
+            const bool add = accumulate || s0 > 0;
+            const int I = info->I, J = info->J;
+            const int64_t row0 = dc * P;
+            auto row_of = [&](int i) { return row0 + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i; };
+            if (DIAG && u.tri) {
+                const int i0 = I * 64 + 8 * u.h;
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int i = i0 + x;
+                    if (i >= n_inputs) continue;
+                    longlong2* rowp = vis + row_of(i);
+                    iflush(rowp + i, acc[56 + x], 0.f, add);
+#pragma unroll
+                    for (int y = x + 1; y < 8; ++y)
+                        if (i0 + y < n_inputs)
+                            iflush(rowp + i0 + y, acc[2 * tri_pair(x, y)], acc[2 * tri_pair(x, y) + 1], add);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = I * 64 + 4 * u.g + a;
+                    if (i >= n_inputs) continue;
+                    longlong2* rowp = vis + row_of(i);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int j = J * 64 + 8 * u.h + b;
+                        if (j < i || j >= n_inputs) continue;
+                        iflush(rowp + j, acc[8 * a + b], acc[32 + 8 * a + b], add);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int BITS, bool VEC>
+cudaError_t launch_int_feed(const Plan& p, const unsigned char* src, int64_t n_dc, longlong2* out, int accumulate,
+                            cudaStream_t s) {
+    const int bps = BITS == 4 ? 1 : 2;
+    const int64_t diag_items = (n_dc + kIDiagCh - 1) / kIDiagCh * p.nb;
+    const int64_t off_items = (n_dc + kIOffCh - 1) / kIOffCh * (p.nb * (p.nb - 1) / 2);
+    // rows (20 KB per channel-dump and block), one chunk of raw pieces, the row bases
+    const int per = kIChunk * kIRow * (int)sizeof(float2) + kIChunk * 64 * bps;
+    const int smem_diag = kIDiagCh * per + (int)sizeof(IItem<kIDiagCh>);          // 96 KB (8-bit)
+    const int smem_off = kIOffCh * 2 * per + (int)sizeof(IItem<kIOffCh>);         // 96 KB (8-bit)
+    const int64_t P = p.n_baselines, tstride = (int64_t)p.n_chan * p.n_inputs;
+    cudaError_t e = cudaFuncSetAttribute(xeng_fp32_int_kernel<BITS, true, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_diag);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xeng_fp32_int_kernel<BITS, false, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_off);
+    if (e != cudaSuccess) return e;
+    if (diag_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 2;
+        const int grid = (int)(diag_items < cap ? diag_items : cap);
+        xeng_fp32_int_kernel<BITS, true, VEC><<<grid, kIDiagThreads, smem_diag, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb, P, tstride, n_dc, diag_items, out, accumulate);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (off_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 2;
+        const int grid = (int)(off_items < cap ? off_items : cap);
+        xeng_fp32_int_kernel<BITS, false, VEC><<<grid, kIOffThreads, smem_off, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb * (p.nb - 1) / 2, P, tstride, n_dc, off_items, out,
+            accumulate);
+    }
+    return cudaGetLastError();
+}
+
+template <int BITS>
+cudaError_t launch_int(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate, cudaStream_t s) {
+    const auto* src = static_cast<const unsigned char*>(d_packed);
+    const int bps = BITS == 4 ? 1 : 2;
+    const bool vec = ((int64_t)p.n_inputs * bps) % 16 == 0 && (reinterpret_cast<uintptr_t>(d_packed) & 15u) == 0;
+    const int64_t n_dc = (int64_t)n_dumps * p.n_chan;
+    auto* out = static_cast<longlong2*>(d_vis);
+    return vec ? launch_int_feed<BITS, true>(p, src, n_dc, out, accumulate, s)
+               : launch_int_feed<BITS, false>(p, src, n_dc, out, accumulate, s);
+}
+
 }  // namespace
 
 cudaError_t launch_xeng_fp32_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                     cudaStream_t s) {
-    if (p.sample_bits == 4) return launch_packed<4>(p, d_packed, n_dumps, d_vis, accumulate, s);
-    if (p.sample_bits == 8) return launch_packed<8>(p, d_packed, n_dumps, d_vis, accumulate, s);
+    if (p.sample_bits == 4) return launch_int<4>(p, d_packed, n_dumps, d_vis, accumulate, s);
+    if (p.sample_bits == 8) return launch_int<8>(p, d_packed, n_dumps, d_vis, accumulate, s);
     return launch_packed<32>(p, d_packed, n_dumps, d_vis, accumulate, s);
 }
 

@@ -142,6 +142,25 @@ def test_fp32_combined_epilogue_edges(n, t, bits, lo):
     assert int(ref[0, 0, 0]) == 2 * t * lo * lo
 
 
+@pytest.mark.parametrize("n,c,t,bits,lo", [(64, 1, 511, 8, -128), (64, 1, 512, 8, -128), (64, 5, 513, 8, -128),
+                                           (128, 3, 1025, 8, -128), (72, 2, 1536, 8, -128),
+                                           (32, 1, 32768 + 32, 4, -8), (16, 3, 65536 + 96, 4, -8)])
+def test_fp32_segment_edges(n, c, t, bits, lo):
+    # the FP32 engine keeps exact fp32 partials over segments of 512 (8-bit) or 32768 (4-bit)
+    # samples and adds each segment into the int64 output: full-scale samples put a partial at
+    # 2^24 (8-bit) on a segment edge; rows of whole 16-byte pieces (the staged-copy path), channel
+    # counts that leave the last group of a block partly empty
+    re = np.full((t, c, n), lo, np.int16)
+    im = np.full((t, c, n), lo, np.int16)
+    im[:, :, 3] = -lo - 1
+    re[::3, :, 7] = -lo - 1
+    p = synth.pack(re, im, bits)
+    v = run_engine(p, n, c, t, bits, FP32)[0]
+    ref = oracle.xcorr_int(p, n, c, t, bits)
+    assert np.array_equal(v, ref)
+    assert int(ref[0, 0, 0]) == 2 * t * lo * lo
+
+
 @pytest.mark.parametrize("engine", [TC, FP32])
 def test_int64_beyond_int32(engine):
     t = 65536 + 64
