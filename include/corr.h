@@ -371,6 +371,8 @@ typedef struct {
     int plane_min_nb;           /* jobs of at least this many blocks read planes (0: none) */
     size_t plane_bytes;         /* the batch's plane workspace */
     int wide;                   /* plane jobs run wide work items (see CORR_ITEMS_WIDE) */
+    int plane_splits;           /* plane jobs in this many launches, each run's unpack overlapping the
+                                   previous run's tensor-core launch (1: unpacks, then one launch) */
 } corr_batch_stats;
 
 /*
@@ -383,7 +385,8 @@ typedef struct {
  * / appended to that JSON-lines file, keyed by the job sizes and the library build.
  * AUTOTUNE with ACCUMULATE is rejected (tuning runs would add into the accumulators).
  * With CORR_BATCH_GRAPH the launches are captured into a CUDA graph once.  Allocates a
- * small device status block and a stream.
+ * small device status block and a stream (with CORR_BATCH_PLANES two more, a high-priority one
+ * for the tensor-core launches and a low-priority one for the unpacks, and a few events).
  */
 corr_status corr_batch_create(corr_batch *out, const corr_job *jobs, int n_jobs, int flags,
                               const char *tune_cache);
@@ -391,9 +394,13 @@ corr_status corr_batch_create(corr_batch *out, const corr_job *jobs, int n_jobs,
  * pair_cpi (channels per work item of single-block arrays, 1 or 2), order (0: costliest jobs'
  * items first, 1: the caller's order), plane_min_nb (jobs of at least this many 64-input blocks
  * read fp16 planes; 0 = none; > 0 needs CORR_BATCH_PLANES), wide (plane jobs: 1 = wide work
- * items, 0 = single tiles).  A captured graph is re-captured.  Results are identical for every
- * shape.  Not concurrent with corr_batch_run. */
-corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide);
+ * items, 0 = single tiles), plane_splits (1..8: the plane jobs in this many launches of about
+ * equal products; the unpacks run back to back on the low-priority stream and each launch waits
+ * for its own jobs' unpacks, so unpacking overlaps the tensor cores' work; each such launch
+ * leaves 10 KB of shared memory per SM for an unpack block).  A captured graph is re-captured.
+ * Results are identical for every shape.  Not concurrent with corr_batch_run. */
+corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide,
+                                 int plane_splits);
 /* Run the batch on `stream` (graph replay when captured).  Asynchronous. */
 corr_status corr_batch_run(corr_batch b, void *stream);
 corr_status corr_batch_info(corr_batch b, corr_batch_stats *stats);

@@ -49,7 +49,7 @@ SIGNATURES = {
     "corr_selftest_stall": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _P(_c_int)]),
     "corr_batch_create": (_c_int, [_P(_vp), _vp, _c_int, _c_int, ctypes.c_char_p]),
     "corr_batch_run": (_c_int, [_vp, _vp]),
-    "corr_batch_set_shape": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "corr_batch_set_shape": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
     "corr_batch_info": (_c_int, [_vp, _vp]),
     "corr_batch_check": (_c_int, [_vp, _P(_c_int)]),
     "corr_batch_destroy": (_c_int, [_vp]),
@@ -314,7 +314,7 @@ class BatchStats(ctypes.Structure):
                 ("tuned", ctypes.c_int), ("n_items", ctypes.c_int64), ("cmacs", ctypes.c_double),
                 ("op_stages", ctypes.c_int), ("pair_cpi", ctypes.c_int), ("order", ctypes.c_int),
                 ("tune_ms", ctypes.c_float), ("plane_min_nb", ctypes.c_int), ("plane_bytes", ctypes.c_size_t),
-                ("wide", ctypes.c_int)]
+                ("wide", ctypes.c_int), ("plane_splits", ctypes.c_int)]
 
 
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_ACCUMULATE, BATCH_PLANES = 1, 2, 4, 8
@@ -339,9 +339,10 @@ class Batch:
     def run(self, stream=None):
         check(lib().corr_batch_run(self._h, _stream_handle(stream)), "corr_batch_run")
 
-    def set_shape(self, op_stages: int = 0, pair_cpi: int = 2, order: int = 0, plane_min_nb: int = 0, wide: int = 1):
+    def set_shape(self, op_stages: int = 0, pair_cpi: int = 2, order: int = 0, plane_min_nb: int = 0, wide: int = 1,
+                  plane_splits: int = 1):
         """Launch shape chosen by the caller instead of the tuner (results do not depend on it)."""
-        check(lib().corr_batch_set_shape(self._h, op_stages, pair_cpi, order, plane_min_nb, wide),
+        check(lib().corr_batch_set_shape(self._h, op_stages, pair_cpi, order, plane_min_nb, wide, plane_splits),
               "corr_batch_set_shape")
 
     def info(self) -> dict:

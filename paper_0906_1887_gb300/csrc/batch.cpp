@@ -42,8 +42,15 @@ struct TuneChoice {
     int order = 0;       // 0: items of the costliest jobs first; 1: jobs in the caller's order
     int plane_min_nb = 0;   // jobs of at least this many 64-input blocks read fp16 planes (0: none)
     int wide = 1;           // plane jobs: wide items (block I against J, J + 1 in one MMA)
+    int plane_splits = 1;   // plane jobs in this many launches, each next one's unpack beside the last
     float ms = 0.f;
 };
+
+// Shared memory a plane-fed launch leaves free on each SM when unpacks run beside it: one 8-bit
+// unpack block (8 KB static + the 1 KB every block reserves), which still leaves the wide
+// items' three-stage ring in place.
+constexpr int kOverlapReserve = 10 * 1024;
+constexpr int kMaxPlaneSplits = 8;
 
 // The build this file was compiled in: tuning results of another build are not reused.
 constexpr const char* kBuildStamp = __DATE__ " " __TIME__;
@@ -75,6 +82,10 @@ struct corr_batch_s {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t gx = nullptr;
     cudaStream_t own_stream = nullptr;
+    // overlapped plane launches: tensor-core launches on a high-priority stream, unpacks on a
+    // low-priority one, so the launches' CTAs are placed first and unpack blocks fill the rest
+    cudaStream_t x_stream = nullptr, u_stream = nullptr;
+    std::vector<cudaEvent_t> events;      // fork, unpack-done per split, join
     double cmacs = 0.0;
     int64_t items = 0;
     corr::TuneChoice choice;
@@ -153,27 +164,106 @@ bool build_groups(corr_batch_s* b, const TuneChoice& ch) {
     return true;
 }
 
-cudaError_t launch_groups(corr_batch_s* b, cudaStream_t s) {
-    for (auto& g : b->groups) {
-        if (g.planes)   // the unpack of every plane job first (each writes its own planes)
-            for (size_t i = 0; i < g.job_index.size(); ++i) {
-                const corr_job& j = b->jobs[g.job_index[i]];
-                const Plan p = plan_of_job(j, b->n_sm);
-                cudaError_t e = launch_unpack_fp16(p, j.packed, 1, const_cast<void*>(g.specs[i].data), s);
-                if (e != cudaSuccess) return e;
-            }
-        // at most kMaxJobs jobs per launch
-        for (size_t k0 = 0; k0 < g.specs.size(); k0 += kMaxJobsPerLaunch) {
-            const int n = (int)std::min(g.specs.size() - k0, (size_t)kMaxJobsPerLaunch);
-            cudaError_t e = g.planes ? launch_xeng_tc_plane_jobs(g.specs.data() + k0, g.maps.data() + k0, n,
-                                                                 b->accumulate, b->d_status, b->n_sm, g.tune, s,
-                                                                 g.maps_wide.data() + k0)
-                                     : launch_xeng_tc_raw_jobs(g.specs.data() + k0, g.maps.data() + k0, n,
-                                                               b->accumulate, b->d_status, b->n_sm, g.tune, s);
-            if (e != cudaSuccess) return e;
-        }
+cudaError_t unpack_range(corr_batch_s* b, const ModeGroup& g, size_t i0, size_t i1, cudaStream_t s,
+                         int blocks_per_sm = 0) {
+    for (size_t i = i0; i < i1; ++i) {   // each plane job writes its own planes
+        const corr_job& j = b->jobs[g.job_index[i]];
+        const Plan p = plan_of_job(j, b->n_sm);
+        const cudaError_t e =
+            launch_unpack_fp16(p, j.packed, 1, const_cast<void*>(g.specs[i].data), s, blocks_per_sm);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The group's jobs [i0, i1) in launches of at most kMaxJobsPerLaunch jobs.
+cudaError_t x_range(corr_batch_s* b, const ModeGroup& g, size_t i0, size_t i1, const TcTuning& tune,
+                    cudaStream_t s) {
+    for (size_t k0 = i0; k0 < i1; k0 += kMaxJobsPerLaunch) {
+        const int n = (int)std::min(i1 - k0, (size_t)kMaxJobsPerLaunch);
+        const cudaError_t e =
+            g.planes ? launch_xeng_tc_plane_jobs(g.specs.data() + k0, g.maps.data() + k0, n, b->accumulate,
+                                                 b->d_status, b->n_sm, tune, s, g.maps_wide.data() + k0)
+                     : launch_xeng_tc_raw_jobs(g.specs.data() + k0, g.maps.data() + k0, n, b->accumulate,
+                                               b->d_status, b->n_sm, tune, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Split points of the plane jobs (launch order) into `splits` runs of about equal products.
+std::vector<size_t> split_points(const corr_batch_s* b, const ModeGroup& g, int splits) {
+    std::vector<double> cost(g.specs.size());
+    double total = 0.0;
+    for (size_t i = 0; i < g.specs.size(); ++i) {
+        const corr_job& j = b->jobs[g.job_index[i]];
+        cost[i] = (double)n_baselines(j.n_inputs) * j.n_chan * j.n_time;
+        total += cost[i];
+    }
+    std::vector<size_t> pts{0};
+    double acc = 0.0;
+    for (size_t i = 0; i < g.specs.size(); ++i) {
+        acc += cost[i];
+        if ((int)pts.size() < splits && acc >= total * pts.size() / splits && i + 1 < g.specs.size())
+            pts.push_back(i + 1);
+    }
+    pts.push_back(g.specs.size());
+    return pts;
+}
+
+cudaError_t launch_groups(corr_batch_s* b, cudaStream_t s) {
+    const int splits = b->choice.plane_splits;
+    const ModeGroup* plane_group = nullptr;
+    int n_plane_groups = 0;
+    for (auto& g : b->groups)
+        if (g.planes) {
+            plane_group = &g;
+            ++n_plane_groups;
+        }
+    if (splits <= 1 || n_plane_groups != 1 || plane_group->specs.size() < 2 || !b->x_stream) {
+        // one launch per group, each plane group's unpacks first
+        for (auto& g : b->groups) {
+            if (g.planes) {
+                const cudaError_t e = unpack_range(b, g, 0, g.specs.size(), s);
+                if (e != cudaSuccess) return e;
+            }
+            const cudaError_t e = x_range(b, g, 0, g.specs.size(), g.tune, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // Overlapped form: the plane jobs in `splits` launches; the unpacks run back to back on the
+    // low-priority stream and each launch waits for its own jobs' unpacks, so the unpack of the
+    // next run of jobs (and the first run's, beside the packed-sample launches) proceeds while
+    // the tensor cores work on the current one:
+    //   u: U1 -> e1 -> U2 -> e2 -> ...        x: packed launches, [e1] X1, [e2] X2, ...
+    const ModeGroup& pg = *plane_group;
+    const std::vector<size_t> pts = split_points(b, pg, splits);
+    const size_t n_runs = pts.size() - 1;
+    if (b->events.size() < n_runs + 2) return cudaErrorInvalidValue;
+    cudaEvent_t ev_fork = b->events[0], ev_join = b->events[n_runs + 1];
+    cudaError_t e = cudaEventRecord(ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->x_stream, ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->u_stream, ev_fork, 0);
+    // the first run's unpacks have the GPU to themselves (beside the packed-sample launches at
+    // most); the later ones take one block per SM, which fits beside a tensor-core CTA whichever
+    // of the two is placed first
+    for (size_t r = 0; r < n_runs && e == cudaSuccess; ++r) {
+        e = unpack_range(b, pg, pts[r], pts[r + 1], b->u_stream, r == 0 ? 0 : 1);
+        if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + r], b->u_stream);
+    }
+    for (auto& g : b->groups)
+        if (!g.planes && e == cudaSuccess) e = x_range(b, g, 0, g.specs.size(), g.tune, b->x_stream);
+    TcTuning tune = pg.tune;
+    tune.smem_reserve = kOverlapReserve;
+    for (size_t r = 0; r < n_runs && e == cudaSuccess; ++r) {
+        e = cudaStreamWaitEvent(b->x_stream, b->events[1 + r], 0);
+        if (e == cudaSuccess) e = x_range(b, pg, pts[r], pts[r + 1], tune, b->x_stream);
+    }
+    // join: the caller's stream continues after the last launch (which followed every unpack)
+    if (e == cudaSuccess) e = cudaEventRecord(ev_join, b->x_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+    return e;
 }
 
 std::string signature(const corr_batch_s* b) {
@@ -210,6 +300,7 @@ void load_cache_file(const char* path) {
         if ((p = strstr(k1, "\"order\": "))) c.order = atoi(p + 9);
         if ((p = strstr(k1, "\"plane_min_nb\": "))) c.plane_min_nb = atoi(p + 16);
         if ((p = strstr(k1, "\"wide\": "))) c.wide = atoi(p + 8);
+        if ((p = strstr(k1, "\"plane_splits\": "))) c.plane_splits = atoi(p + 16);
         if ((p = strstr(k1, "\"ms\": "))) c.ms = (float)atof(p + 6);
         if (c.pair_cpi != 1 && c.pair_cpi != 2) continue;
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -224,8 +315,8 @@ void append_cache_file(const char* path, const std::string& key, const TuneChoic
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"op_stages\": %d, \"pair_cpi\": %d, \"order\": %d, \"plane_min_nb\": %d, "
-            "\"wide\": %d, \"ms\": %.6f}\n",
-            key.c_str(), c.op_stages, c.pair_cpi, c.order, c.plane_min_nb, c.wide, c.ms);
+            "\"wide\": %d, \"plane_splits\": %d, \"ms\": %.6f}\n",
+            key.c_str(), c.op_stages, c.pair_cpi, c.order, c.plane_min_nb, c.wide, c.plane_splits, c.ms);
     fclose(f);
 }
 
@@ -297,6 +388,7 @@ corr_status autotune(corr_batch_s* b, const char* cache_path) {
     float best_ms = 1e30f;
     cudaStream_t s = b->own_stream;
     for (auto& c : cands) {
+        b->choice = c;
         if (!build_groups(b, c)) return set_error(CORR_EINVAL, "tensor map encoding failed");
         cudaError_t err;
         const float ms = time_groups(b, s, 3, &err);
@@ -305,6 +397,23 @@ corr_status autotune(corr_batch_s* b, const char* cache_path) {
         if (ms < best_ms) {
             best_ms = ms;
             best = c;
+        }
+    }
+    // second stage: the best shape with its plane jobs split into overlapped launches
+    if (best.plane_min_nb > 0) {
+        for (int splits : {2, 3, 4}) {
+            TuneChoice c = best;
+            c.plane_splits = splits;
+            b->choice = c;
+            if (!build_groups(b, c)) return set_error(CORR_EINVAL, "tensor map encoding failed");
+            cudaError_t err;
+            const float ms = time_groups(b, s, 3, &err);
+            if (err != cudaSuccess) return cuda_error(err, "autotune run");
+            c.ms = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
         }
     }
     b->choice = best;
@@ -368,6 +477,17 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && (flags & CORR_BATCH_PLANES)) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->x_stream, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->u_stream, cudaStreamNonBlocking, least);
+        for (int k = 0; k < kMaxPlaneSplits + 2 && e == cudaSuccess; ++k) {
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->events.push_back(ev);
+        }
+    }
     if (e != cudaSuccess) {
         corr_batch_destroy(b);
         return cuda_error(e, "corr_batch_create");
@@ -421,12 +541,13 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
     return CORR_OK;
 }
 
-corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide) {
+corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int order, int plane_min_nb, int wide,
+                                 int plane_splits) {
     if (!b) return set_error(CORR_EINVAL, "corr_batch_set_shape: NULL batch");
     if (op_stages < 0 || op_stages > 16 || (pair_cpi != 1 && pair_cpi != 2) || (order != 0 && order != 1) ||
-        plane_min_nb < 0 || (wide != 0 && wide != 1))
+        plane_min_nb < 0 || (wide != 0 && wide != 1) || plane_splits < 1 || plane_splits > kMaxPlaneSplits)
         return set_error(CORR_EINVAL, "corr_batch_set_shape: op_stages in [0, 16], pair_cpi 1 or 2, order 0 or 1, "
-                                      "plane_min_nb >= 0, wide 0 or 1");
+                                      "plane_min_nb >= 0, wide 0 or 1, plane_splits in [1, %d]", kMaxPlaneSplits);
     if (plane_min_nb > 0 && !b->d_planes)
         return set_error(CORR_EINVAL, "plane_min_nb > 0 needs a batch created with CORR_BATCH_PLANES");
     TuneChoice c;
@@ -435,6 +556,7 @@ corr_status corr_batch_set_shape(corr_batch b, int op_stages, int pair_cpi, int 
     c.order = order;
     c.plane_min_nb = plane_min_nb;
     c.wide = wide;
+    c.plane_splits = plane_splits;
     if (!build_groups(b, c)) return set_error(CORR_EINVAL, "tensor map encoding failed");
     b->choice = c;
     b->tuned = false;
@@ -475,6 +597,7 @@ corr_status corr_batch_info(corr_batch b, corr_batch_stats* st) {
     st->tune_ms = b->choice.ms;
     st->plane_min_nb = b->choice.plane_min_nb;
     st->wide = b->choice.wide;
+    st->plane_splits = b->choice.plane_splits;
     st->plane_bytes = b->plane_bytes;
     return CORR_OK;
 }
@@ -496,6 +619,9 @@ corr_status corr_batch_destroy(corr_batch b) {
     if (b->gx) cudaGraphExecDestroy(b->gx);
     if (b->g) cudaGraphDestroy(b->g);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    if (b->x_stream) cudaStreamDestroy(b->x_stream);
+    if (b->u_stream) cudaStreamDestroy(b->u_stream);
+    for (auto ev : b->events) cudaEventDestroy(ev);
     if (b->d_status) cudaFree(b->d_status);
     if (b->d_planes) cudaFree(b->d_planes);
     delete b;

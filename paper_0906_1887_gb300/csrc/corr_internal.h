@@ -58,8 +58,10 @@ size_t plane_elem_bytes(const Plan& p);              // 2 (fp16) or 4 (fp32)
 size_t planes_bytes(const Plan& p, int n_dumps);     // one set of planes
 
 // Kernel launchers (return cudaSuccess or the launch error).
+// blocks_per_sm > 0 caps the vectorised kernel's grid at that many blocks per SM (a launch that
+// runs beside a tensor-core launch takes one, which fits next to its CTA in either launch order)
 cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps, void* d_planes,
-                               cudaStream_t s);
+                               cudaStream_t s, int blocks_per_sm = 0);
 cudaError_t launch_unpack_f32(const Plan& p, const void* d_packed, int n_dumps, void* d_planes,
                               cudaStream_t s);
 cudaError_t launch_unpack_bf16x2(const Plan& p, const void* d_packed, int n_dumps, void* d_hi,
@@ -98,6 +100,7 @@ struct TcJobSpec {
 // Launch-shape knobs the autotuner chooses (0 = default).
 struct TcTuning {
     int op_stages = 0;
+    int smem_reserve = 0;         // plane feed: shared memory per SM left free for a concurrent kernel
     uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
 };

@@ -127,7 +127,9 @@ struct FastTile {
     static constexpr int kTileBytes = kTimeBlock * kRowBytes;
 };
 
-template <int BITS>
+// kGroup: tiles whose loads a block issues together (1 for the full grid; 8 for a launch of one
+// block per SM beside a tensor-core launch, 64 KB in flight per block)
+template <int BITS, int kGroup>
 __global__ void __launch_bounds__(FastTile<BITS>::kThreads) unpack_fast_kernel(
     const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb_count, int kp,
     int64_t n_tiles, __half* __restrict__ planes) {
@@ -137,91 +139,126 @@ __global__ void __launch_bounds__(FastTile<BITS>::kThreads) unpack_fast_kernel(
     const int tb_count = kp / kTimeBlock;
     const int64_t row_bytes = (int64_t)n_inputs * (BITS == 8 ? 2 : 1);
     constexpr int kPieces = F::kRowBytes / 16;          // 16-byte pieces per packed row
+    constexpr int kPer = kTimeBlock * kPieces / F::kThreads;   // pieces a thread moves per tile (2)
+    static_assert(kPer * F::kThreads == kTimeBlock * kPieces, "whole pieces per thread");
     // conversion task of this thread
     const int q = tid & 7, pw = tid >> 3;             // sample group, word within the row
     const uint32_t* src = tile + (size_t)(8 * q) * F::kWords;
-    for (int64_t t_idx = blockIdx.x; t_idx < n_tiles; t_idx += gridDim.x) {
-        const int tb = (int)(t_idx % tb_count);
-        const int64_t rest = t_idx / tb_count;
-        const int nb = (int)(rest % nb_count);
-        const int64_t dc = rest / nb_count;          // dump * n_chan + chan
-        const int64_t d = dc / n_chan;
-        const int c = (int)(dc % n_chan);
-        const int64_t valid = row_bytes - (int64_t)nb * F::kRowBytes;   // bytes of this block's row that exist
-        // load: each thread moves kTileBytes / 16 / kThreads = 2 pieces
-        for (int k = tid; k < kTimeBlock * kPieces; k += F::kThreads) {
-            const int t = k / kPieces, piece = k % kPieces;
-            const int tg = tb * kTimeBlock + t;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (tg < n_time && (int64_t)piece * 16 < valid) {
-                const int64_t off = ((d * n_time + tg) * n_chan + c) * row_bytes + (int64_t)nb * F::kRowBytes + piece * 16;
-                v = *reinterpret_cast<const uint4*>(packed + off);
-            }
-            const int chunk = BITS == 8 ? (piece ^ ((t >> 3) & 7)) : (piece ^ ((t >> 3) & 3));
-            *reinterpret_cast<uint4*>(tile + t * F::kWords + chunk * 4) = v;
-        }
-        __syncthreads();
-        uint32_t w[8];
+    // A block takes kGroup tiles at a time (strided by the grid) and issues every load of the
+    // group before converting any: kGroup x 8 KB in flight per block.
+    for (int64_t t_base = blockIdx.x; t_base < n_tiles; t_base += (int64_t)kGroup * gridDim.x) {
+        uint4 v[kGroup][kPer];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int t = 8 * q + e;
-            const int word = BITS == 8 ? (pw ^ (((t >> 3) & 7) << 2)) : (pw ^ (((t >> 3) & 3) << 2));
-            w[e] = src[e * F::kWords + word];
-        }
-        __syncthreads();   // the tile is free for the next load once every thread holds its words
-        const int64_t row0 = (dc * nb_count + nb) * (int64_t)kBlockRows;
-        __half* out = planes + row0 * kp + (int64_t)tb * kTimeBlock + 8 * q;
-        if constexpr (BITS == 8) {
-            // word pw = (re, im) of inputs 2pw, 2pw + 1 -> plane rows 4pw + k, k = byte lane
-            const __half2 bias = conv::bias8();
+        for (int gi = 0; gi < kGroup; ++gi) {
+            const int64_t t_idx = t_base + (int64_t)gi * gridDim.x;
+            const bool tile_ok = t_idx < n_tiles;
+            const int tb = tile_ok ? (int)(t_idx % tb_count) : 0;
+            const int64_t rest = tile_ok ? t_idx / tb_count : 0;
+            const int nb = (int)(rest % nb_count);
+            const int64_t dc = rest / nb_count;          // dump * n_chan + chan
+            const int64_t d = dc / n_chan;
+            const int c = (int)(dc % n_chan);
+            const int64_t valid = row_bytes - (int64_t)nb * F::kRowBytes;   // bytes of this block's row that exist
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t sel = conv::lane_selector(k);
-                uint4 o;
-                o.x = conv::pair_to_half2(w[0], w[1], sel, conv::kFlip8, bias);
-                o.y = conv::pair_to_half2(w[2], w[3], sel, conv::kFlip8, bias);
-                o.z = conv::pair_to_half2(w[4], w[5], sel, conv::kFlip8, bias);
-                o.w = conv::pair_to_half2(w[6], w[7], sel, conv::kFlip8, bias);
-                *reinterpret_cast<uint4*>(out + (int64_t)(4 * pw + k) * kp) = o;
+            for (int u = 0; u < kPer; ++u) {
+                const int k = tid + u * F::kThreads;
+                const int t = k / kPieces, piece = k % kPieces;
+                const int tg = tb * kTimeBlock + t;
+                v[gi][u] = make_uint4(0u, 0u, 0u, 0u);
+                if (tile_ok && tg < n_time && (int64_t)piece * 16 < valid) {
+                    const int64_t off =
+                        ((d * n_time + tg) * n_chan + c) * row_bytes + (int64_t)nb * F::kRowBytes + piece * 16;
+                    v[gi][u] = *reinterpret_cast<const uint4*>(packed + off);
+                }
             }
-        } else {
-            // word pw = inputs 4pw .. 4pw + 3, high nibble re, low nibble im -> rows 8pw + 2k (+1)
-            const __half2 bias = conv::bias4();
-            uint32_t hi[8], lo[8];
+        }
+#pragma unroll
+        for (int gi = 0; gi < kGroup; ++gi) {
+            const int64_t t_idx = t_base + (int64_t)gi * gridDim.x;
+            if (t_idx >= n_tiles) break;   // uniform across the block
+            const int tb = (int)(t_idx % tb_count);
+            const int64_t rest = t_idx / tb_count;
+            const int nb = (int)(rest % nb_count);
+            const int64_t dc = rest / nb_count;
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int k = tid + u * F::kThreads;
+                const int t = k / kPieces, piece = k % kPieces;
+                const int chunk = BITS == 8 ? (piece ^ ((t >> 3) & 7)) : (piece ^ ((t >> 3) & 3));
+                *reinterpret_cast<uint4*>(tile + t * F::kWords + chunk * 4) = v[gi][u];
+            }
+            __syncthreads();
+            uint32_t w[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;
-                lo[e] = w[e] & 0x0F0F0F0Fu;
+                const int t = 8 * q + e;
+                const int word = BITS == 8 ? (pw ^ (((t >> 3) & 7) << 2)) : (pw ^ (((t >> 3) & 3) << 2));
+                w[e] = src[e * F::kWords + word];
             }
+            __syncthreads();   // the tile is free for the next store once every thread holds its words
+            const int64_t row0 = (dc * nb_count + nb) * (int64_t)kBlockRows;
+            __half* out = planes + row0 * kp + (int64_t)tb * kTimeBlock + 8 * q;
+            if constexpr (BITS == 8) {
+                // word pw = (re, im) of inputs 2pw, 2pw + 1 -> plane rows 4pw + k, k = byte lane
+                const __half2 bias = conv::bias8();
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t sel = conv::lane_selector(k);
-                uint4 o;
-                o.x = conv::pair_to_half2(hi[0], hi[1], sel, conv::kFlip4, bias);
-                o.y = conv::pair_to_half2(hi[2], hi[3], sel, conv::kFlip4, bias);
-                o.z = conv::pair_to_half2(hi[4], hi[5], sel, conv::kFlip4, bias);
-                o.w = conv::pair_to_half2(hi[6], hi[7], sel, conv::kFlip4, bias);
-                *reinterpret_cast<uint4*>(out + (int64_t)(8 * pw + 2 * k) * kp) = o;
-                o.x = conv::pair_to_half2(lo[0], lo[1], sel, conv::kFlip4, bias);
-                o.y = conv::pair_to_half2(lo[2], lo[3], sel, conv::kFlip4, bias);
-                o.z = conv::pair_to_half2(lo[4], lo[5], sel, conv::kFlip4, bias);
-                o.w = conv::pair_to_half2(lo[6], lo[7], sel, conv::kFlip4, bias);
-                *reinterpret_cast<uint4*>(out + (int64_t)(8 * pw + 2 * k + 1) * kp) = o;
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t sel = conv::lane_selector(k);
+                    uint4 o;
+                    o.x = conv::pair_to_half2(w[0], w[1], sel, conv::kFlip8, bias);
+                    o.y = conv::pair_to_half2(w[2], w[3], sel, conv::kFlip8, bias);
+                    o.z = conv::pair_to_half2(w[4], w[5], sel, conv::kFlip8, bias);
+                    o.w = conv::pair_to_half2(w[6], w[7], sel, conv::kFlip8, bias);
+                    *reinterpret_cast<uint4*>(out + (int64_t)(4 * pw + k) * kp) = o;
+                }
+            } else {
+                // word pw = inputs 4pw .. 4pw + 3, high nibble re, low nibble im -> rows 8pw + 2k (+1)
+                const __half2 bias = conv::bias4();
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;
+                    lo[e] = w[e] & 0x0F0F0F0Fu;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t sel = conv::lane_selector(k);
+                    uint4 o;
+                    o.x = conv::pair_to_half2(hi[0], hi[1], sel, conv::kFlip4, bias);
+                    o.y = conv::pair_to_half2(hi[2], hi[3], sel, conv::kFlip4, bias);
+                    o.z = conv::pair_to_half2(hi[4], hi[5], sel, conv::kFlip4, bias);
+                    o.w = conv::pair_to_half2(hi[6], hi[7], sel, conv::kFlip4, bias);
+                    *reinterpret_cast<uint4*>(out + (int64_t)(8 * pw + 2 * k) * kp) = o;
+                    o.x = conv::pair_to_half2(lo[0], lo[1], sel, conv::kFlip4, bias);
+                    o.y = conv::pair_to_half2(lo[2], lo[3], sel, conv::kFlip4, bias);
+                    o.z = conv::pair_to_half2(lo[4], lo[5], sel, conv::kFlip4, bias);
+                    o.w = conv::pair_to_half2(lo[6], lo[7], sel, conv::kFlip4, bias);
+                    *reinterpret_cast<uint4*>(out + (int64_t)(8 * pw + 2 * k + 1) * kp) = o;
+                }
             }
         }
     }
 }
 
 template <int BITS>
-cudaError_t launch_fast(const Plan& p, const void* d_packed, int n_dumps, void* planes, cudaStream_t s) {
+cudaError_t launch_fast(const Plan& p, const void* d_packed, int n_dumps, void* planes, cudaStream_t s,
+                       int blocks_per_sm) {
     using F = FastTile<BITS>;
     const int64_t n_tiles = (int64_t)n_dumps * p.n_chan * p.nb * (p.kp / kTimeBlock);
-    const int64_t cap = (int64_t)p.n_sm * (BITS == 8 ? 8 : 16);
-    const int grid = (int)(n_tiles < cap ? n_tiles : cap);
-    if (grid < 1) return cudaSuccess;
-    unpack_fast_kernel<BITS><<<grid, F::kThreads, 0, s>>>(static_cast<const unsigned char*>(d_packed), p.n_inputs,
-                                                          p.n_chan, p.n_time, p.nb, p.kp, n_tiles,
-                                                          static_cast<__half*>(planes));
+    if (n_tiles < 1) return cudaSuccess;
+    const auto* src = static_cast<const unsigned char*>(d_packed);
+    auto* out = static_cast<__half*>(planes);
+    if (blocks_per_sm > 0) {   // few blocks: each keeps eight tiles of loads in flight
+        const int64_t cap = (int64_t)p.n_sm * blocks_per_sm;
+        const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+        unpack_fast_kernel<BITS, 8><<<grid, F::kThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.kp,
+                                                                 n_tiles, out);
+    } else {                   // the whole GPU: many blocks, one tile each at a time
+        const int64_t cap = (int64_t)p.n_sm * (BITS == 8 ? 8 : 16);
+        const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+        unpack_fast_kernel<BITS, 1><<<grid, F::kThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.kp,
+                                                                 n_tiles, out);
+    }
     return cudaGetLastError();
 }
 
@@ -237,15 +274,16 @@ cudaError_t launch(const Plan& p, const void* d_packed, int n_dumps, void* o0, v
 
 }  // namespace
 
-cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s) {
+cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s,
+                               int blocks_per_sm) {
     // packed rows of whole 16-byte pieces (and a 16-byte aligned base) take the vectorised kernel
     const int64_t row = (int64_t)p.n_inputs * (p.sample_bits == 8 ? 2 : 1);
     const bool fast = row % 16 == 0 && (reinterpret_cast<uintptr_t>(d_packed) & 15u) == 0 &&
                       (reinterpret_cast<uintptr_t>(d_planes) & 15u) == 0;
     if (p.sample_bits == 4)
-        return fast ? launch_fast<4>(p, d_packed, n_dumps, d_planes, s)
+        return fast ? launch_fast<4>(p, d_packed, n_dumps, d_planes, s, blocks_per_sm)
                     : launch<4, kOutF16>(p, d_packed, n_dumps, d_planes, nullptr, s);
-    return fast ? launch_fast<8>(p, d_packed, n_dumps, d_planes, s)
+    return fast ? launch_fast<8>(p, d_packed, n_dumps, d_planes, s, blocks_per_sm)
                 : launch<8, kOutF16>(p, d_packed, n_dumps, d_planes, nullptr, s);
 }
 

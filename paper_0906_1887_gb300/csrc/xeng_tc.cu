@@ -1169,8 +1169,9 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     } else {
         prm->raw_stage_bytes = 0;
         prm->raw_stages = 0;
-        // as deep as fits, or the requested depth when that is smaller
-        prm->op_stages = (kSmemBudget - stage_space) / prm->op_stage_bytes;
+        // as deep as fits (less any reserve for a kernel running beside it), or the requested
+        // depth when that is smaller
+        prm->op_stages = (kSmemBudget - stage_space - tune.smem_reserve) / prm->op_stage_bytes;
         if (prm->op_stages > kMaxOpStages) prm->op_stages = kMaxOpStages;
         if (tune.op_stages >= 2 && tune.op_stages < prm->op_stages) prm->op_stages = tune.op_stages;
     }

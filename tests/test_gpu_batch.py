@@ -104,8 +104,10 @@ def test_batch_plane_path_every_shape_bit_exact(jobs, graph):
     b = corr.Batch(_descs(jobs), flags=corr.BATCH_PLANES | (corr.BATCH_GRAPH if graph else 0))
     info = b.info()
     assert info["plane_bytes"] > 0 and info["plane_min_nb"] == 4
-    for plane_min_nb, order, ops, wide in [(0, 0, 0, 1), (2, 0, 3, 1), (4, 1, 5, 0), (8, 0, 4, 1), (2, 1, 0, 0)]:
-        b.set_shape(ops, 2, order, plane_min_nb, wide)
+    for plane_min_nb, order, ops, wide, splits in [(0, 0, 0, 1, 1), (2, 0, 3, 1, 1), (4, 1, 5, 0, 1), (8, 0, 4, 1, 1),
+                                                   (2, 1, 0, 0, 1), (2, 0, 0, 1, 2), (2, 0, 0, 1, 3), (2, 1, 4, 0, 8)]:
+        # plane_splits > 1: the plane jobs in several launches, unpacks overlapped on another stream
+        b.set_shape(ops, 2, order, plane_min_nb, wide, splits)
         for j in jobs:
             j["vis"].fill_(-5)
         b.run()
@@ -120,6 +122,7 @@ def test_batch_autotune_with_planes(jobs):
     b = corr.Batch(_descs(jobs), flags=corr.BATCH_AUTOTUNE | corr.BATCH_PLANES)
     info = b.info()
     assert info["tuned"] == 1 and info["plane_min_nb"] in (0, 2, 4, 8) and info["wide"] in (0, 1)
+    assert 1 <= info["plane_splits"] <= 4
     for j in jobs:
         j["vis"].fill_(-5)
     b.run()
@@ -127,4 +130,6 @@ def test_batch_autotune_with_planes(jobs):
     _check(jobs)
     with pytest.raises(corr.CorrError):
         corr.Batch(_descs(jobs)).set_shape(0, 2, 0, 2, 1)   # planes need CORR_BATCH_PLANES
+    with pytest.raises(corr.CorrError):
+        b.set_shape(0, 2, 0, 2, 1, 9)   # at most 8 plane launches
     b.close()
