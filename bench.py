@@ -712,6 +712,20 @@ def run_dump(args):
     return line
 
 
+def _stream_latency(ok, s_, t_job_ms):
+    """One open stream's latency summary: p50/p99 (ms), the fraction within its own sample time,
+    its jobs' mean device time and mean wait from submission to the start of its copy."""
+    lat = np.array([r[3] - r[1] for r in ok if r[4] == s_]) * 1e3
+    if not len(lat):
+        return {"stream": s_, "jobs": 0}
+    gpu = np.array([r[6] for r in ok if r[4] == s_])
+    queued = np.array([r[2] - r[1] for r in ok if r[4] == s_]) * 1e3
+    return {"stream": s_, "jobs": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "sample_time_ms": t_job_ms,
+            "frac_within_sample_time": float(np.mean(lat < t_job_ms)), "mean_gpu_ms": float(gpu.mean()),
+            "mean_queued_ms": float(queued.mean())}
+
+
 def run_serve(args):
     """Serving loop (config 5): 8 input streams, each a random array drawn once from the seed
     (32..512 dual-pol antennas, 128..1536 channels, 256..1024 samples per job, 4 or 8 bits), each
@@ -819,6 +833,7 @@ def run_serve(args):
             "real_time_factor": float(t_job.sum() / 1e3 / wall) if len(lat) else None,
             "tera_cmac_per_s": cm / wall / 1e12, "offered_tera_cmac_per_s": offered / 1e12,
             "device_state_bytes": arena_state,
+            "per_stream": [_stream_latency(ok, s_, shapes[s_][2] / CHANNEL_RATE_HZ * 1e3) for s_ in range(n_streams)],
             "latency": "submit to the job's samples accumulated on the device (closing jobs: to the dump in "
                        "pinned host memory); target p99 below the job's own sample time and every dump within "
                        "its dump interval"}

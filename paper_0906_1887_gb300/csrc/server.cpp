@@ -108,7 +108,8 @@ struct Job {
     bool raw = false;
     int stream = -1;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    int* h_status = nullptr;   // pinned host copy of the kernel status words
+    int* h_status = nullptr;   // the kernels' status words in mapped pinned memory (host view)
+    int* d_status = nullptr;   // the same words, device view
     float gpu_ms = 0.f;
     void* d_vis = nullptr;     // device result while the job keeps it
     bool stream_job = false;   // runs on an open stream's device state
@@ -124,13 +125,18 @@ struct StreamState {
     size_t off = 0, bytes = 0;           // arena block
     size_t slot_bytes = 0;               // one ring slot (packed samples of one job)
     char* slots = nullptr;               // [ring_slots] sample slots
-    int* status = nullptr;               // [ring_slots][4] kernel status words
     char* acc = nullptr;                 // accumulators [C][P][2]
     char* ws = nullptr;                  // sample planes when the kernel cannot read the packed layout
     char* dumpbuf = nullptr;             // averaged mode: float32 [C][P][2]
     char* phasor = nullptr;              // averaged mode with delays: float2 [C][N]
     bool raw = false;
     cudaStream_t copy_s = nullptr, comp_s = nullptr;
+    // averaged dumps: the readout of the dump buffer to the host runs on out_s, so the stream's
+    // next jobs (which only need the dump kernel to have read the accumulators) do not queue
+    // behind a copy of several GB; the next dump kernel waits for the previous readout (ev_out)
+    cudaStream_t out_s = nullptr;
+    cudaEvent_t ev_dumped = nullptr, ev_out = nullptr;
+    bool out_pending = false;
     std::vector<cudaEvent_t> slot_full, slot_free;
     int64_t n_submitted = 0, n_retired = 0;
     bool closing = false;
@@ -195,7 +201,6 @@ size_t stream_layout(StreamState& st, char* base) {
         off += round_up(bytes);
         return ptr;
     };
-    st.status = reinterpret_cast<int*>(take((size_t)st.d.ring_slots * 16));
     st.slots = take(st.slot_bytes * (size_t)st.d.ring_slots);
     st.acc = take(vis_bytes(d));
     st.ws = ws ? take(ws) : nullptr;
@@ -203,6 +208,72 @@ size_t stream_layout(StreamState& st, char* base) {
     st.phasor = (avg && st.d.d_delays) ? take((size_t)d.n_chan * d.n_inputs * 8) : nullptr;
     return off;
 }
+
+}  // namespace
+}  // namespace corr
+
+namespace corr {
+namespace {
+
+// Per-job resources recycled from job to job: pinned status words (allocated kStatusChunk jobs'
+// worth at a time) and timing events.  Allocating and freeing them per job put cudaMallocHost
+// and cudaFreeHost -- which can wait for the device -- on the submit and release paths under
+// the server lock, where a release behind a deep GPU queue stalled dispatch for every stream.
+constexpr int kStatusChunk = 4096;
+struct JobResources {
+    struct Slot {
+        int* host;   // mapped pinned memory: the kernels write a job's status words here directly
+        int* dev;    // the same words as a device pointer
+    };
+    std::vector<int*> chunks;
+    std::vector<Slot> free_status;
+    std::vector<cudaEvent_t> events, free_events;
+    cudaError_t take_status(Slot* out) {
+        if (free_status.empty()) {
+            int* c = nullptr;
+            int* d = nullptr;
+            cudaError_t e = cudaHostAlloc((void**)&c, (size_t)kStatusChunk * 4 * sizeof(int), cudaHostAllocMapped);
+            if (e != cudaSuccess) return e;
+            e = cudaHostGetDevicePointer((void**)&d, c, 0);
+            if (e != cudaSuccess) {
+                cudaFreeHost(c);
+                return e;
+            }
+            chunks.push_back(c);
+            for (int k = kStatusChunk - 1; k >= 0; --k) free_status.push_back(Slot{c + 4 * k, d + 4 * k});
+        }
+        *out = free_status.back();
+        free_status.pop_back();
+        memset(out->host, 0, 4 * sizeof(int));   // zeroed before the job's kernels are issued
+        return cudaSuccess;
+    }
+    void give_status(const Slot& s) {
+        if (s.host) free_status.push_back(s);
+    }
+    cudaError_t take_event(cudaEvent_t* out) {
+        if (free_events.empty()) {
+            cudaEvent_t ev = nullptr;
+            const cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return e;
+            events.push_back(ev);
+            free_events.push_back(ev);
+        }
+        *out = free_events.back();
+        free_events.pop_back();
+        return cudaSuccess;
+    }
+    void give_event(cudaEvent_t ev) {
+        if (ev) free_events.push_back(ev);
+    }
+    void destroy() {
+        for (auto ev : events) cudaEventDestroy(ev);
+        for (auto c : chunks) cudaFreeHost(c);
+        events.clear();
+        free_events.clear();
+        chunks.clear();
+        free_status.clear();
+    }
+};
 
 }  // namespace
 }  // namespace corr
@@ -223,6 +294,7 @@ struct corr_server_s {
     std::thread dispatcher, completer;
     corr_server_stats stats{};
     std::map<int, corr::StreamState*> open_streams;   // by stream_tag
+    corr::JobResources res;                           // recycled status words and events (lock held)
 };
 
 namespace corr {
@@ -248,18 +320,17 @@ cudaError_t run_x(const Plan& p, const corr_job_desc& d, bool raw, const char* d
 cudaError_t issue(corr_server_s* S, Job& j) {
     cudaStream_t s = S->streams[j.stream];
     char* base = S->d_base + j.off;
-    int* d_status = reinterpret_cast<int*>(base);
     char* d_packed = base + round_up(16);
     char* d_vis = d_packed + round_up(packed_bytes(j.desc));
     char* d_ws = d_vis + round_up(vis_bytes(j.desc));
     Plan p = plan_of(j.desc, S->device, S->n_sm);
-    p.d_status = d_status;
+    // the kernels write the status words straight into the job's mapped pinned slot (zeroed at
+    // submission): no copy of 16 bytes queued on a copy engine behind other jobs' large copies
+    p.d_status = j.d_status;
     cudaError_t e = cudaEventRecord(j.ev_start, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 16, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc),
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = run_x(p, j.desc, j.raw, d_packed, d_vis, d_ws, 0, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_status, d_status, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && j.desc.host_vis)
         e = cudaMemcpyAsync(j.desc.host_vis, d_vis, vis_bytes(j.desc), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_done, s);
@@ -274,9 +345,8 @@ cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
     const int R = st.d.ring_slots;
     const int slot = (int)(j.seq % R);
     char* d_packed = st.slots + (size_t)slot * st.slot_bytes;
-    int* d_status = st.status + 4 * slot;
     Plan p = plan_of(j.desc, S->device, S->n_sm);
-    p.d_status = d_status;
+    p.d_status = j.d_status;   // mapped pinned status words (see issue())
     const bool sums = st.d.dump_mode == CORR_STREAM_DUMP_SUMS;
     // an interval's first job overwrites the accumulators (the previous interval's dump, issued
     // earlier on the same stream, has read them): that is the reset of Fig. 1, with no extra pass
@@ -288,21 +358,33 @@ cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
         e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc), cudaMemcpyHostToDevice, st.copy_s);
     if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[slot], st.copy_s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[slot], 0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 16, st.comp_s);
     if (e == cudaSuccess) e = run_x(p, j.desc, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
     if (e == cudaSuccess) e = cudaEventRecord(st.slot_free[slot], st.comp_s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(j.h_status, d_status, 16, cudaMemcpyDeviceToHost, st.comp_s);
     if (e == cudaSuccess && j.closes) {
         if (sums) {
             e = cudaMemcpyAsync(j.desc.host_vis, st.acc, vis_bytes(j.desc), cudaMemcpyDeviceToHost, st.comp_s);
         } else {
-            // Fig. 1: read out and divide by the update count (the next job's overwrite resets)
-            const corr_status cs = corr_dump(reinterpret_cast<corr_plan>(&p), st.acc, (int)j.n_accum, st.d.d_delays,
-                                             st.d.d_freqs, st.phasor, st.dumpbuf, 0, st.comp_s);
-            if (cs != CORR_OK) e = cudaErrorLaunchFailure;
-            if (e == cudaSuccess && j.desc.host_vis)
-                e = cudaMemcpyAsync(j.desc.host_vis, st.dumpbuf, (size_t)p.n_baselines * p.n_chan * 8,
-                                    cudaMemcpyDeviceToHost, st.comp_s);
+            // Fig. 1: read out and divide by the update count (the next job's overwrite resets).
+            // The dump buffer must have reached the host from the previous dump first.
+            if (st.out_pending) e = cudaStreamWaitEvent(st.comp_s, st.ev_out, 0);
+            if (e == cudaSuccess) {
+                const corr_status cs = corr_dump(reinterpret_cast<corr_plan>(&p), st.acc, (int)j.n_accum,
+                                                 st.d.d_delays, st.d.d_freqs, st.phasor, st.dumpbuf, 0, st.comp_s);
+                if (cs != CORR_OK) e = cudaErrorLaunchFailure;
+            }
+            if (e == cudaSuccess && j.desc.host_vis) {
+                e = cudaEventRecord(st.ev_dumped, st.comp_s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st.out_s, st.ev_dumped, 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(j.desc.host_vis, st.dumpbuf, (size_t)p.n_baselines * p.n_chan * 8,
+                                        cudaMemcpyDeviceToHost, st.out_s);
+                if (e == cudaSuccess) e = cudaEventRecord(st.ev_out, st.out_s);
+                if (e == cudaSuccess) {
+                    st.out_pending = true;
+                    // the job is done when its dump is in host memory
+                    return cudaEventRecord(j.ev_done, st.out_s);
+                }
+            }
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_done, st.comp_s);
@@ -379,7 +461,10 @@ void dispatcher_loop(corr_server_s* S) {
             // nothing of this job is queued behind a failed call that we can rely on; mark it
             // failed once its stream has drained the calls that were accepted
             cudaStreamSynchronize(j.stream_job ? j.st->comp_s : S->streams[j.stream]);
-            if (j.stream_job) cudaStreamSynchronize(j.st->copy_s);
+            if (j.stream_job) {
+                cudaStreamSynchronize(j.st->copy_s);
+                cudaStreamSynchronize(j.st->out_s);
+            }
             j.state = kFailed;
             j.final_status = CORR_ECUDA;
             j.t_done = now_s();
@@ -455,6 +540,10 @@ void completer_loop(corr_server_s* S) {
 void free_stream_state(corr_server_s* S, StreamState* st) {
     if (st->copy_s) cudaStreamSynchronize(st->copy_s);
     if (st->comp_s) cudaStreamSynchronize(st->comp_s);
+    if (st->out_s) cudaStreamSynchronize(st->out_s);
+    if (st->ev_dumped) cudaEventDestroy(st->ev_dumped);
+    if (st->ev_out) cudaEventDestroy(st->ev_out);
+    if (st->out_s) cudaStreamDestroy(st->out_s);
     for (auto ev : st->slot_full)
         if (ev) cudaEventDestroy(ev);
     for (auto ev : st->slot_free)
@@ -513,6 +602,10 @@ corr_status corr_server_create(corr_server* out, size_t hbm_budget_bytes, int n_
         delete S;
         return cuda_error(e, "cudaStreamCreate");
     }
+    {   // the first chunk of pinned status words now, not under the lock of the first submission
+        JobResources::Slot warm{};
+        if (S->res.take_status(&warm) == cudaSuccess) S->res.give_status(warm);
+    }
     S->paused = (flags & CORR_SERVER_START_PAUSED) != 0;
     S->stats.arena_bytes = hbm_budget_bytes;
     S->dispatcher = std::thread(dispatcher_loop, S);
@@ -560,15 +653,17 @@ corr_status corr_submit(corr_server S, const corr_job_desc* d, uint64_t* job_id)
                              S->arena->size());
         }
     }
-    cudaError_t e = cudaEventCreate(&j.ev_start);
-    if (e == cudaSuccess) e = cudaEventCreate(&j.ev_done);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&j.h_status, 16);
+    cudaError_t e = S->res.take_event(&j.ev_start);
+    if (e == cudaSuccess) e = S->res.take_event(&j.ev_done);
+    JobResources::Slot slot{};
+    if (e == cudaSuccess) e = S->res.take_status(&slot);
+    j.h_status = slot.host;
+    j.d_status = slot.dev;
     if (e != cudaSuccess) {
-        if (j.ev_start) cudaEventDestroy(j.ev_start);
-        if (j.ev_done) cudaEventDestroy(j.ev_done);
+        S->res.give_event(j.ev_start);
+        S->res.give_event(j.ev_done);
         return cuda_error(e, "corr_submit");
     }
-    memset(j.h_status, 0, 16);
     if (st) st->n_submitted++;
     j.id = S->next_id++;
     j.t_submit = now_s();
@@ -621,9 +716,9 @@ corr_status corr_release(corr_server S, uint64_t job_id) {
         S->stats.bytes_in_use = S->arena->used();
         S->cv_dispatch.notify_all();
     }
-    if (j.ev_start) cudaEventDestroy(j.ev_start);
-    if (j.ev_done) cudaEventDestroy(j.ev_done);
-    if (j.h_status) cudaFreeHost(j.h_status);
+    S->res.give_event(j.ev_start);
+    S->res.give_event(j.ev_done);
+    S->res.give_status(JobResources::Slot{j.h_status, j.d_status});
     S->jobs.erase(it);
     return CORR_OK;
 }
@@ -699,13 +794,10 @@ corr_status corr_server_destroy(corr_server S, double drain_timeout_s) {
     for (auto& kv : S->open_streams) {
         cudaStreamSynchronize(kv.second->copy_s);
         cudaStreamSynchronize(kv.second->comp_s);
+        cudaStreamSynchronize(kv.second->out_s);
     }
     S->completer.join();
-    for (auto& kv : S->jobs) {
-        if (kv.second.ev_start) cudaEventDestroy(kv.second.ev_start);
-        if (kv.second.ev_done) cudaEventDestroy(kv.second.ev_done);
-        if (kv.second.h_status) cudaFreeHost(kv.second.h_status);
-    }
+    S->res.destroy();   // every job's events and status words came from the pools
     for (auto& kv : S->open_streams) free_stream_state(S, kv.second);
     S->open_streams.clear();
     for (auto st : S->streams) cudaStreamDestroy(st);
@@ -771,6 +863,9 @@ corr_status corr_server_open_stream(corr_server S, int stream_tag, const corr_st
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st->copy_s, cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st->comp_s, cudaStreamNonBlocking, prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st->out_s, cudaStreamNonBlocking, prio);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_dumped, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st->ev_out, cudaEventDisableTiming);
     st->slot_full.assign(d->ring_slots, nullptr);
     st->slot_free.assign(d->ring_slots, nullptr);
     for (int k = 0; k < d->ring_slots && e == cudaSuccess; ++k) {
