@@ -774,6 +774,7 @@ struct IItem {
     int64_t base[KCH];   // element offset of each channel-dump's sample-0 row; -1 past the last one
     int64_t dc0;         // first channel-dump of the group
     int I, J;            // tile: input blocks of the rows and of the columns
+    int s_begin, s_end;  // the item's range of samples
 };
 
 // One exact partial into the int64 output: the first segment stores (or, accumulating, adds);
@@ -791,12 +792,14 @@ __device__ __forceinline__ void iflush(longlong2* dst, float re, float im, bool 
 }
 
 // VEC: packed rows of whole 16-byte pieces (staged copies); otherwise element-wise loads.
-// P = baselines per channel-dump, tstride = elements from one sample row to the next.
+// P = baselines per channel-dump, tstride = elements from one sample row to the next.  An item is
+// (channel group, sample range, tile); with ts > 1 sample ranges of range_len samples (whole
+// chunks) go to different blocks, every range adds into an output the launcher zeroed first.
 template <int BITS, bool DIAG, bool VEC>
 __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
     xeng_fp32_int_kernel(const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
-                         int n_tiles, int64_t P, int64_t tstride, int64_t n_dc, int64_t n_items,
-                         longlong2* __restrict__ vis, int accumulate) {
+                         int n_tiles, int64_t P, int64_t tstride, int64_t n_dc, int64_t n_items, int ts,
+                         int range_len, longlong2* __restrict__ vis, int accumulate) {
     constexpr int kCh = DIAG ? kIDiagCh : kIOffCh;
     constexpr int kThreads = DIAG ? kIDiagThreads : kIOffThreads;
     constexpr int NBLK = DIAG ? 1 : 2;
@@ -825,22 +828,26 @@ __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
             } else {
                 off_tile(tile, nb, I, J);
             }
+            const int64_t rest = item / n_tiles;
+            const int r = (int)(rest % ts);
             item_s->I = I;
             item_s->J = J;
-            item_s->dc0 = item / n_tiles * kCh;
+            item_s->dc0 = rest / ts * kCh;
+            item_s->s_begin = r * range_len;
+            item_s->s_end = min(n_time, (r + 1) * range_len);
         }
         if (tid < kCh) {
-            const int64_t e = item / n_tiles * kCh + tid;
+            const int64_t e = item / n_tiles / ts * kCh + tid;
             item_s->base[tid] = e < n_dc ? ((e / n_chan) * n_time * n_chan + e % n_chan) * (int64_t)n_inputs : -1;
         }
         __syncthreads();
-        for (int s0 = 0; s0 < n_time; s0 += kSeg) {
-            const int s1 = min(n_time, s0 + kSeg);
+        for (int s0 = info->s_begin; s0 < info->s_end; s0 += kSeg) {
+            const int s1 = min(info->s_end, s0 + kSeg);
             float acc[64];
 #pragma unroll
             for (int k = 0; k < 64; ++k) acc[k] = 0.f;
-            if (VEC && s0 == 0)
-                istage<BITS, NBLK, kCh, kThreads>(packed, raw, item_s->base, tstride, tid, n_inputs, 0, s1, info->I,
+            if (VEC && s0 == info->s_begin)
+                istage<BITS, NBLK, kCh, kThreads>(packed, raw, item_s->base, tstride, tid, n_inputs, s0, s1, info->I,
                                                   info->J);
             cp_async_commit();
             for (int t0 = s0; t0 < s1; t0 += kIChunk) {
@@ -852,10 +859,10 @@ __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
                     iconvert<BITS, NBLK, kCh, kThreads>(raw, s_dyn, tid);
                     __syncthreads();
                     // stage the next chunk: the rest of this segment, then the next segment's first
-                    const int tn = t0 + kIChunk;
-                    if (tn < n_time)
+                    const int tn = t0 + kIChunk, se = info->s_end;
+                    if (tn < se)
                         istage<BITS, NBLK, kCh, kThreads>(packed, raw, item_s->base, tstride, tid, n_inputs, tn,
-                                                          tn < s1 ? s1 : min(n_time, s1 + kSeg), info->I, info->J);
+                                                          tn < s1 ? s1 : min(se, s1 + kSeg), info->I, info->J);
                     cp_async_commit();
                 } else {
                     __syncthreads();
@@ -880,7 +887,7 @@ __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
             const ISub<DIAG> u(tid);
             const int64_t dc = info->dc0 + u.q;
             if (dc >= n_dc) continue;
-            const bool add = accumulate || s0 > 0;
+            const bool add = accumulate || s0 > info->s_begin || ts > 1;
             const int I = info->I, J = info->J;
             const int64_t row0 = dc * P;
             auto row_of = [&](int i) { return row0 + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i; };
@@ -912,16 +919,37 @@ __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
                 }
             }
         }
+        // every thread is done with this item's record before thread 0 writes the next one
+        __syncthreads();
     }
+}
+
+// Sample ranges per item for a launch of base_items items: with fewer than two waves of two
+// blocks per SM, the sample axis is split (whole chunks, at least 64 samples a range).
+void sample_ranges(const Plan& p, int64_t base_items, int* ts, int* range_len) {
+    const int64_t target = 4LL * p.n_sm;
+    int64_t t = 1;
+    if (base_items > 0 && base_items < target) t = (target + base_items - 1) / base_items;
+    const int64_t t_max = (p.n_time + 63) / 64;
+    if (t > t_max) t = t_max;
+    if (t < 1) t = 1;
+    int len = (int)((p.n_time + t - 1) / t);
+    len = (len + kIChunk - 1) / kIChunk * kIChunk;
+    *range_len = len;
+    *ts = (p.n_time + len - 1) / len;
 }
 
 template <int BITS, bool VEC>
 cudaError_t launch_int_feed(const Plan& p, const unsigned char* src, int64_t n_dc, longlong2* out, int accumulate,
                             cudaStream_t s) {
     const int bps = BITS == 4 ? 1 : 2;
-    const int64_t diag_items = (n_dc + kIDiagCh - 1) / kIDiagCh * p.nb;
-    const int64_t off_items = (n_dc + kIOffCh - 1) / kIOffCh * (p.nb * (p.nb - 1) / 2);
-    // rows (20 KB per channel-dump and block), one chunk of raw pieces, the row bases
+    const int64_t diag_base = (n_dc + kIDiagCh - 1) / kIDiagCh * p.nb;
+    const int64_t off_base = (n_dc + kIOffCh - 1) / kIOffCh * (p.nb * (p.nb - 1) / 2);
+    int ts_d, len_d, ts_o, len_o;
+    sample_ranges(p, diag_base, &ts_d, &len_d);
+    sample_ranges(p, off_base, &ts_o, &len_o);
+    const int64_t diag_items = diag_base * ts_d, off_items = off_base * ts_o;
+    // rows (20 KB per channel-dump and block), one chunk of raw pieces, the item
     const int per = kIChunk * kIRow * (int)sizeof(float2) + kIChunk * 64 * bps;
     const int smem_diag = kIDiagCh * per + (int)sizeof(IItem<kIDiagCh>);          // 96 KB (8-bit)
     const int smem_off = kIOffCh * 2 * per + (int)sizeof(IItem<kIOffCh>);         // 96 KB (8-bit)
@@ -931,12 +959,16 @@ cudaError_t launch_int_feed(const Plan& p, const unsigned char* src, int64_t n_d
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(xeng_fp32_int_kernel<BITS, false, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem_off);
+    // split sample ranges add into the output: it starts from zero unless accumulating
+    if (e == cudaSuccess && !accumulate && (ts_d > 1 || ts_o > 1))
+        e = cudaMemsetAsync(out, 0, (size_t)n_dc * P * sizeof(longlong2), s);
     if (e != cudaSuccess) return e;
     if (diag_items > 0) {
         const int64_t cap = (int64_t)p.n_sm * 2;
         const int grid = (int)(diag_items < cap ? diag_items : cap);
         xeng_fp32_int_kernel<BITS, true, VEC><<<grid, kIDiagThreads, smem_diag, s>>>(
-            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb, P, tstride, n_dc, diag_items, out, accumulate);
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb, P, tstride, n_dc, diag_items, ts_d, len_d, out,
+            accumulate);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -944,8 +976,8 @@ cudaError_t launch_int_feed(const Plan& p, const unsigned char* src, int64_t n_d
         const int64_t cap = (int64_t)p.n_sm * 2;
         const int grid = (int)(off_items < cap ? off_items : cap);
         xeng_fp32_int_kernel<BITS, false, VEC><<<grid, kIOffThreads, smem_off, s>>>(
-            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb * (p.nb - 1) / 2, P, tstride, n_dc, off_items, out,
-            accumulate);
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb * (p.nb - 1) / 2, P, tstride, n_dc, off_items, ts_o,
+            len_o, out, accumulate);
     }
     return cudaGetLastError();
 }
