@@ -912,6 +912,7 @@ corr_status corr_server_close_stream(corr_server S, int stream_tag, double drain
         lock.unlock();
         cudaStreamSynchronize(st->copy_s);
         cudaStreamSynchronize(st->comp_s);
+        cudaStreamSynchronize(st->out_s);
         lock.lock();
         // the completion thread retires the issued jobs once their events are complete
         S->cv_done.wait_for(lock, std::chrono::seconds(10), [&] { return st->n_retired == st->n_submitted; });
