@@ -228,28 +228,12 @@ cudaError_t launch_xeng_fp32(const Plan& p, const void* d_planes, int n_dumps, v
 // ---- FP32 CUDA-core engine reading the packed samples directly ----------------------------
 //
 // The plain form as run by corr_xengine_run: no unpack pass, and no products below the
-// diagonal.  Float32 samples use the kernel of this section; 4/8-bit samples the 4 x 8
-// sub-block kernel of the next one.  A 64 x 64 tile of input pairs is split into 4 x 4 sub-blocks of contiguous inputs
-// (16 x 16 of them); a thread owns one sub-block: rows 4gi .. 4gi+3, columns 4gj .. 4gj+3, 16
-// complex accumulators.  Off-diagonal tiles (I < J) use 256 threads, one per sub-block.  Diagonal
-// tiles (I = J) only need the part of the tile on or above the diagonal: there a thread owns a
-// 2 x 4 sub-block (rows 2gi, 2gi + 1), 272 of them meet the upper triangle, and 288-thread blocks
-// (94% of the lanes computing, 8 accumulators each, three blocks per SM) cover them, so the
-// 64-input stream computes 2176 products per 2080 baselines instead of 4096.  Each 64-sample
-// chunk of the tile's one or two 64-input blocks is loaded with consecutive threads on
-// consecutive inputs (coalesced), converted to float2 (re, im) and stored
-// in shared memory with two pad slots after every four inputs: a thread's four inputs are then
-// two 16-byte loads, and the 16 sub-block columns of a warp hit distinct bank groups in pairs.
-// Exactness for integer samples as in the plane-fed engine above: one fp32 partial per 64-sample
-// chunk (|Re| <= 2^21), int32 totals over segments of at most 32768 samples, int64 output.
+// diagonal.  Two kernels below share one design (4 x 8 register sub-blocks, diagonal tiles as
+// sub-blocks plus 8 x 8 triangles, several channel-dumps per block): one for 4/8-bit samples
+// (converted in shared memory, exact integer partials into the int64 output) and one for float32
+// samples (copied straight into shared memory, fp32 partials over 64 samples into the float32
+// output).
 namespace {
-
-constexpr int kDChunk = 64;            // samples per shared-memory chunk (one fp32 partial each)
-constexpr int kDRow = 64 + 32;         // float2 slots per sample row (inputs + pads)
-constexpr int kDiagThreads = 288;      // the 272 2 x 4 sub-blocks of the upper triangle, whole warps
-constexpr int kOffThreads = 256;
-
-__device__ __forceinline__ int dslot(int i) { return i + 2 * (i >> 2); }
 
 template <int BITS>
 __device__ __forceinline__ float2 load_packed(const unsigned char* __restrict__ p, int64_t idx) {
@@ -273,283 +257,6 @@ __device__ __forceinline__ void off_tile(int tile, int nb, int& I, int& J) {
     }
     I = i;
     J = i + 1 + rem;
-}
-
-// A chunk of kDChunk samples of the tile's kBlocks 64-input blocks -> float2 rows in shared
-// memory.  Vector form (packed rows of whole 16-byte pieces): every thread issues up to four
-// 16-byte loads before converting any, so their latencies overlap; a piece holds 8 (8-bit),
-// 16 (4-bit) or 2 (float) inputs of one sample.
-template <int BITS, int NBLK, int NT>
-__device__ __forceinline__ void load_chunk_vec(const unsigned char* __restrict__ packed,
-                                               float2 (*s)[kDChunk * kDRow], int tid, int64_t d, int c, int n_chan,
-                                               int n_time, int n_inputs, int t0, int s1, int I, int J) {
-    constexpr int kBps = BITS == 4 ? 1 : (BITS == 8 ? 2 : 8);
-    constexpr int kPieces = 64 * kBps / 16;             // 16-byte pieces per block row
-    constexpr int kPerPiece = 16 / kBps;                // inputs per piece
-    constexpr int kTotal = NBLK * kDChunk * kPieces;
-    const int64_t row_bytes = (int64_t)n_inputs * kBps;
-    for (int base = tid; base < kTotal; base += 4 * NT) {
-        uint4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = base + u * NT;
-            v[u] = make_uint4(0u, 0u, 0u, 0u);
-            if (k < kTotal) {
-                const int blk = k / (kDChunk * kPieces), rest = k % (kDChunk * kPieces);
-                const int t = rest / kPieces, piece = rest % kPieces;
-                const int i0 = (blk ? J : I) * 64 + piece * kPerPiece;
-                if (t0 + t < s1 && i0 < n_inputs)
-                    v[u] = *reinterpret_cast<const uint4*>(
-                        packed + ((d * n_time + t0 + t) * n_chan + c) * row_bytes + (int64_t)i0 * kBps);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = base + u * NT;
-            if (k >= kTotal) break;
-            const int blk = k / (kDChunk * kPieces), rest = k % (kDChunk * kPieces);
-            const int t = rest / kPieces, piece = rest % kPieces;
-            float2* row = s[blk] + t * kDRow;
-            const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-            if constexpr (BITS == 8) {
-                // 8 inputs: bytes (re, im) pairs; two groups of four contiguous slots
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const uint32_t a = w[2 * g], b = w[2 * g + 1];
-                    float4* dst = reinterpret_cast<float4*>(row + dslot(piece * 8 + 4 * g));
-                    dst[0] = make_float4((float)(signed char)(a & 0xFF), (float)(signed char)((a >> 8) & 0xFF),
-                                         (float)(signed char)((a >> 16) & 0xFF), (float)(signed char)(a >> 24));
-                    dst[1] = make_float4((float)(signed char)(b & 0xFF), (float)(signed char)((b >> 8) & 0xFF),
-                                         (float)(signed char)((b >> 16) & 0xFF), (float)(signed char)(b >> 24));
-                }
-            } else if constexpr (BITS == 4) {
-                // 16 inputs: one byte each, high nibble re, low nibble im; four groups of four
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const uint32_t a = w[g];
-                    float4* dst = reinterpret_cast<float4*>(row + dslot(piece * 16 + 4 * g));
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t b0 = (a >> (16 * h)) & 0xFF, b1 = (a >> (16 * h + 8)) & 0xFF;
-                        dst[h] = make_float4((float)((int)(b0 << 24) >> 28), (float)((int)(b0 << 28) >> 28),
-                                             (float)((int)(b1 << 24) >> 28), (float)((int)(b1 << 28) >> 28));
-                    }
-                }
-            } else {
-                // 2 inputs of (re, im) float32: contiguous slots (an even input starts a slot pair)
-                *reinterpret_cast<uint4*>(row + dslot(piece * 2)) = v[u];
-            }
-        }
-    }
-}
-
-// Element-wise form for packed rows that are not whole 16-byte pieces, four loads in flight.
-template <int BITS, int NBLK, int NT>
-__device__ __forceinline__ void load_chunk_scalar(const unsigned char* __restrict__ packed,
-                                                  float2 (*s)[kDChunk * kDRow], int tid, int64_t d, int c, int n_chan,
-                                                  int n_time, int n_inputs, int t0, int s1, int I, int J) {
-    constexpr int kTotal = NBLK * kDChunk * 64;
-    for (int base = tid; base < kTotal; base += 4 * NT) {
-        float2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = base + u * NT;
-            v[u] = make_float2(0.f, 0.f);
-            if (k < kTotal) {
-                const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
-                const int t = rest >> 6, ig = (blk ? J : I) * 64 + (rest & 63);
-                if (t0 + t < s1 && ig < n_inputs)
-                    v[u] = load_packed<BITS>(packed, ((d * n_time + t0 + t) * n_chan + c) * (int64_t)n_inputs + ig);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = base + u * NT;
-            if (k >= kTotal) break;
-            const int blk = k / (kDChunk * 64), rest = k % (kDChunk * 64);
-            s[blk][(rest >> 6) * kDRow + dslot(rest & 63)] = v[u];
-        }
-    }
-}
-
-template <int BITS, bool DIAG>
-__global__ void __launch_bounds__(DIAG ? kDiagThreads : kOffThreads, DIAG ? 3 : 2)
-    xeng_fp32_packed_kernel(const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
-                            int64_t n_items, void* __restrict__ vis, int accumulate, int vec) {
-    constexpr bool kInt = BITS != 32;
-    constexpr int kThreads = DIAG ? kDiagThreads : kOffThreads;
-    constexpr int R = DIAG ? 2 : 4;                  // rows (inputs i) of a thread's sub-block; 4 columns
-    constexpr int kBlocks = DIAG ? 1 : 2;            // 64-input blocks per tile
-    extern __shared__ __align__(16) float2 s_dyn[];   // [kBlocks][kDChunk * kDRow]
-    float2 (*s)[kDChunk * kDRow] = reinterpret_cast<float2 (*)[kDChunk * kDRow]>(s_dyn);
-    const int tid = threadIdx.x;
-    int gi, gj;
-    bool active = true;
-    if (DIAG) {
-        // tid -> the tid-th needed 2 x 4 sub-block in row-major order: rows 2gi, 2gi + 1 meet the
-        // upper triangle in the column groups gj = floor(gi / 2) .. 15
-        int g = 0, rem = tid;
-        while (g < 32 && rem >= 16 - (g >> 1)) {
-            rem -= 16 - (g >> 1);
-            ++g;
-        }
-        active = g < 32;
-        gi = active ? g : 0;
-        gj = active ? (g >> 1) + rem : 0;
-    } else {
-        gi = tid >> 4;
-        gj = tid & 15;
-    }
-    const float2* sa = s[0];
-    const float2* sb = s[kBlocks - 1];
-    const int64_t P = (int64_t)n_inputs * (n_inputs + 1) / 2;
-    const int n_off = nb * (nb - 1) / 2;
-
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        int I, J;
-        int64_t dc;
-        if (DIAG) {
-            I = J = (int)(item % nb);
-            dc = item / nb;
-        } else {
-            off_tile((int)(item % n_off), nb, I, J);
-            dc = item / n_off;
-        }
-        const int64_t d = dc / n_chan;
-        const int c = (int)(dc % n_chan);
-        constexpr int kSegment = 32768;
-        for (int s0 = 0; s0 < n_time; s0 += kSegment) {
-            const int s1 = min(n_time, s0 + kSegment);
-            float pr[R][4], pi[R][4];
-            typename std::conditional<kInt, int, float>::type tr[R][4], ti[R][4];
-#pragma unroll
-            for (int a = 0; a < R; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    pr[a][b] = pi[a][b] = 0.f;
-                    tr[a][b] = ti[a][b] = 0;
-                }
-            for (int t0 = s0; t0 < s1; t0 += kDChunk) {
-                // load + convert this chunk of the tile's blocks (zero past the last input/sample)
-                if (vec) {
-                    load_chunk_vec<BITS, kBlocks, kThreads>(packed, s, tid, d, c, n_chan, n_time, n_inputs, t0, s1, I, J);
-                } else {
-                    load_chunk_scalar<BITS, kBlocks, kThreads>(packed, s, tid, d, c, n_chan, n_time, n_inputs, t0, s1, I,
-                                                               J);
-                }
-                __syncthreads();
-                if (active) {
-#pragma unroll 2
-                    for (int t = 0; t < kDChunk; ++t) {
-                        // the row inputs R gi .. R gi + R - 1 and column inputs 4 gj .. 4 gj + 3: whole
-                        // 16-byte slot pairs (a group of four inputs never straddles a pad)
-                        float ar[R], ai[R];
-                        const float4 a01 = *reinterpret_cast<const float4*>(sa + t * kDRow + dslot(R * gi));
-                        ar[0] = a01.x, ai[0] = a01.y, ar[1] = a01.z, ai[1] = a01.w;
-                        if constexpr (R == 4) {
-                            const float4 a23 = *reinterpret_cast<const float4*>(sa + t * kDRow + dslot(R * gi) + 2);
-                            ar[2] = a23.x, ai[2] = a23.y, ar[3] = a23.z, ai[3] = a23.w;
-                        }
-                        const float4 b01 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj);
-                        const float4 b23 = *reinterpret_cast<const float4*>(sb + t * kDRow + 6 * gj + 2);
-                        const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
-#pragma unroll
-                        for (int x = 0; x < R; ++x)
-#pragma unroll
-                            for (int y = 0; y < 4; ++y) {
-                                // x_i conj(x_j): re = ar br + ai bi, im = ai br - ar bi
-                                pr[x][y] = fmaf(ar[x], br[y], pr[x][y]);
-                                pr[x][y] = fmaf(ai[x], bi[y], pr[x][y]);
-                                pi[x][y] = fmaf(ai[x], br[y], pi[x][y]);
-                                pi[x][y] = fmaf(-ar[x], bi[y], pi[x][y]);
-                            }
-                    }
-                }
-                __syncthreads();
-                {   // flush every chunk of 64 samples
-#pragma unroll
-                    for (int a = 0; a < R; ++a)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            if constexpr (kInt) {
-                                tr[a][b] += __float2int_rn(pr[a][b]);   // exact: |partial| <= 2^21
-                                ti[a][b] += __float2int_rn(pi[a][b]);
-                            } else {
-                                tr[a][b] += pr[a][b];
-                                ti[a][b] += pi[a][b];
-                            }
-                            pr[a][b] = pi[a][b] = 0.f;
-                        }
-                }
-            }
-            if (!active) continue;
-            const bool add = accumulate || s0 > 0;
-#pragma unroll
-            for (int a = 0; a < R; ++a) {
-                const int i = I * 64 + R * gi + a;
-                if (i >= n_inputs) continue;
-                const int64_t row = dc * P + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int j = J * 64 + 4 * gj + b;
-                    if (j < i || j >= n_inputs) continue;
-                    if constexpr (kInt) {
-                        longlong2* dst = reinterpret_cast<longlong2*>(vis) + row + j;
-                        longlong2 v = make_longlong2(tr[a][b], ti[a][b]);
-                        if (add) {
-                            const longlong2 o = *dst;
-                            v.x += o.x;
-                            v.y += o.y;
-                        }
-                        *dst = v;
-                    } else {
-                        float2* dst = reinterpret_cast<float2*>(vis) + row + j;
-                        float2 v = make_float2(tr[a][b], ti[a][b]);
-                        if (add) {
-                            const float2 o = *dst;
-                            v.x += o.x;
-                            v.y += o.y;
-                        }
-                        *dst = v;
-                    }
-                }
-            }
-        }
-    }
-}
-
-template <int BITS>
-cudaError_t launch_packed(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
-                          cudaStream_t s) {
-    const auto* src = static_cast<const unsigned char*>(d_packed);
-    // 16-byte loads when every packed row (and so every block's piece) starts 16-byte aligned
-    const int bps = BITS == 4 ? 1 : (BITS == 8 ? 2 : 8);
-    const int vec = ((int64_t)p.n_inputs * bps) % 16 == 0 && (reinterpret_cast<uintptr_t>(d_packed) & 15u) == 0;
-    const int64_t diag_items = (int64_t)n_dumps * p.n_chan * p.nb;
-    const int64_t off_items = (int64_t)n_dumps * p.n_chan * (p.nb * (p.nb - 1) / 2);
-    const int smem_diag = kDChunk * kDRow * (int)sizeof(float2);     // 48 KB
-    const int smem_off = 2 * smem_diag;                                // 96 KB
-    cudaError_t e = cudaFuncSetAttribute(xeng_fp32_packed_kernel<BITS, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_diag);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(xeng_fp32_packed_kernel<BITS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_off);
-    if (e != cudaSuccess) return e;
-    if (diag_items > 0) {
-        const int64_t cap = (int64_t)p.n_sm * 2;
-        const int grid = (int)(diag_items < cap ? diag_items : cap);
-        xeng_fp32_packed_kernel<BITS, true><<<grid, kDiagThreads, smem_diag, s>>>(
-            src, p.n_inputs, p.n_chan, p.n_time, p.nb, diag_items, d_vis, accumulate, vec);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (off_items > 0) {
-        const int64_t cap = (int64_t)p.n_sm * 2;
-        const int grid = (int)(off_items < cap ? off_items : cap);
-        xeng_fp32_packed_kernel<BITS, false><<<grid, kOffThreads, smem_off, s>>>(
-            src, p.n_inputs, p.n_chan, p.n_time, p.nb, off_items, d_vis, accumulate, vec);
-    }
-    return cudaGetLastError();
 }
 
 // ---- integer samples: 4 x 8 register sub-blocks, several channels per block ----
@@ -662,11 +369,11 @@ __device__ __forceinline__ void iconvert(const uint4* __restrict__ raw, float2* 
 
 // Element-wise form for packed rows that are not whole 16-byte pieces (one load at a time: the
 // accumulators stay in registers meanwhile).
-template <int BITS, int NBLK, int KCH, int NT>
+template <int BITS, int NBLK, int KCH, int NT, int CHUNK = kIChunk>
 __device__ __forceinline__ void iload_scalar(const unsigned char* __restrict__ packed, float2* __restrict__ s,
                                              const int64_t* __restrict__ base, int64_t tstride, int tid,
                                              int n_inputs, int t0, int s1, int I, int J) {
-    constexpr int kPerCh = NBLK * kIChunk * 64;
+    constexpr int kPerCh = NBLK * CHUNK * 64;
     for (int k = tid; k < KCH * kPerCh; k += NT) {
         const int q = k / kPerCh, r = k % kPerCh;
         const int x = r & 63, blk = (r >> 6) % NBLK, t = r / (64 * NBLK);
@@ -674,7 +381,7 @@ __device__ __forceinline__ void iload_scalar(const unsigned char* __restrict__ p
         const int64_t b = base[q];
         float2 v = make_float2(0.f, 0.f);
         if (b >= 0 && t0 + t < s1 && ig < n_inputs) v = load_packed<BITS>(packed, b + (int64_t)(t0 + t) * tstride + ig);
-        s[((q * NBLK + blk) * kIChunk + t) * kIRow + islot(x)] = v;
+        s[((q * NBLK + blk) * CHUNK + t) * kIRow + islot(x)] = v;
     }
 }
 
@@ -924,6 +631,175 @@ __global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
     }
 }
 
+// ---- float32 samples: the same sub-blocks, rows copied straight into shared memory ----
+//
+// Float samples need no conversion: 16-byte pieces (two inputs' (re, im)) go from the packed rows
+// into the float2 rows with cp.async, into one of two row buffers while the block computes on the
+// other (16-sample chunks, so both buffers of four diagonal or two off-diagonal channel-dumps fit
+// two blocks per SM).  Accuracy as in the kernels above: fp32 partials over 64 samples, each added
+// into the float32 output (the first stored unless accumulating or split over sample ranges,
+// later ones by vector float2 reductions, one writing thread per element).
+constexpr int kFChunk = 16;
+constexpr int kFSeg = 64;
+
+template <int NBLK, int KCH, int NT>
+__device__ __forceinline__ void fstage(const float2* __restrict__ packed, float2* __restrict__ rows,
+                                       const int64_t* __restrict__ base, int64_t tstride, int tid, int n_inputs,
+                                       int t0, int s1, int I, int J) {
+    constexpr int kPieces = 32;                       // 16-byte pieces (two inputs) per 64-input row
+    constexpr int kPerCh = NBLK * kFChunk * kPieces;
+    for (int k = tid; k < KCH * kPerCh; k += NT) {
+        const int q = k / kPerCh, r = k % kPerCh;
+        const int piece = r % kPieces, blk = (r / kPieces) % NBLK, t = r / (kPieces * NBLK);
+        const int i0 = (blk ? J : I) * 64 + 2 * piece;
+        const int64_t b = base[q];
+        const float2* src = packed;
+        int bytes = 0;
+        if (b >= 0 && t0 + t < s1 && i0 < n_inputs) {
+            src = packed + b + (int64_t)(t0 + t) * tstride + i0;
+            bytes = 16;
+        }
+        cp_async16(rows + ((q * NBLK + blk) * kFChunk + t) * kIRow + islot(2 * piece), src, bytes);
+    }
+}
+
+__device__ __forceinline__ void fflush(float2* dst, float re, float im, bool add) {
+    if (add) atomicAdd(dst, make_float2(re, im));
+    else *dst = make_float2(re, im);
+}
+
+// VEC: an even number of inputs and a 16-byte aligned base (whole 16-byte pieces); otherwise
+// element-wise loads.  Items and sample ranges as in xeng_fp32_int_kernel.
+template <bool DIAG, bool VEC>
+__global__ void __launch_bounds__(DIAG ? kIDiagThreads : kIOffThreads, 2)
+    xeng_fp32_float_kernel(const float2* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb,
+                           int n_tiles, int64_t P, int64_t tstride, int64_t n_dc, int64_t n_items, int ts,
+                           int range_len, float2* __restrict__ vis, int accumulate) {
+    constexpr int kCh = DIAG ? kIDiagCh : kIOffCh;
+    constexpr int kThreads = DIAG ? kIDiagThreads : kIOffThreads;
+    constexpr int NBLK = DIAG ? 1 : 2;
+    constexpr int kBuf = kCh * NBLK * kFChunk * kIRow;   // float2 slots of one row buffer
+    // two row buffers [kCh][NBLK][kFChunk][kIRow], then the item
+    extern __shared__ __align__(16) float2 s_dyn[];
+    IItem<kCh>* item_s = reinterpret_cast<IItem<kCh>*>(s_dyn + 2 * kBuf);
+    const volatile IItem<kCh>* info = item_s;
+    const int tid = threadIdx.x;
+    const float2 *sa, *sb;
+    bool tri;
+    {
+        const ISub<DIAG> u(tid);
+        tri = u.tri;
+        sa = s_dyn + (u.q * NBLK) * kFChunk * kIRow + (u.tri ? islot(8 * u.h) : islot(4 * u.g));
+        sb = s_dyn + (u.q * NBLK + NBLK - 1) * kFChunk * kIRow + islot(8 * u.h);
+    }
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (tid == 0) {
+            const int tile = (int)(item % n_tiles);
+            int I, J;
+            if (DIAG) {
+                I = J = tile;
+            } else {
+                off_tile(tile, nb, I, J);
+            }
+            const int64_t rest = item / n_tiles;
+            const int r = (int)(rest % ts);
+            item_s->I = I;
+            item_s->J = J;
+            item_s->dc0 = rest / ts * kCh;
+            item_s->s_begin = r * range_len;
+            item_s->s_end = min(n_time, (r + 1) * range_len);
+        }
+        if (tid < kCh) {
+            const int64_t e = item / n_tiles / ts * kCh + tid;
+            item_s->base[tid] = e < n_dc ? ((e / n_chan) * n_time * n_chan + e % n_chan) * (int64_t)n_inputs : -1;
+        }
+        __syncthreads();
+        const int sbeg = info->s_begin;
+        if (VEC) {
+            fstage<NBLK, kCh, kThreads>(packed, s_dyn, item_s->base, tstride, tid, n_inputs, sbeg,
+                                        min(info->s_end, sbeg + kFSeg), info->I, info->J);
+            cp_async_commit();
+        }
+        for (int s0 = sbeg; s0 < info->s_end; s0 += kFSeg) {
+            const int s1 = min(info->s_end, s0 + kFSeg);
+            float acc[64];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+            for (int t0 = s0; t0 < s1; t0 += kFChunk) {
+                const int buf = ((t0 - sbeg) / kFChunk) & 1;
+                if constexpr (VEC) {
+                    // this chunk has landed in buf; every thread is past the chunk before, which
+                    // used the other buffer: stage the next chunk there
+                    cp_async_wait_all();
+                    __syncthreads();
+                    const int tn = t0 + kFChunk, se = info->s_end;
+                    if (tn < se)
+                        fstage<NBLK, kCh, kThreads>(packed, s_dyn + (buf ^ 1) * kBuf, item_s->base, tstride, tid,
+                                                    n_inputs, tn, tn < s1 ? s1 : min(se, s1 + kFSeg), info->I,
+                                                    info->J);
+                    cp_async_commit();
+                } else {
+                    __syncthreads();
+                    iload_scalar<32, NBLK, kCh, kThreads, kFChunk>(reinterpret_cast<const unsigned char*>(packed),
+                                                                   s_dyn + buf * kBuf, item_s->base, tstride, tid,
+                                                                   n_inputs, t0, s1, info->I, info->J);
+                    __syncthreads();
+                }
+                const float2* pa = sa + buf * kBuf;
+                const float2* pb = sb + buf * kBuf;
+                if (DIAG && tri) {   // warp-uniform
+#pragma unroll 1
+                    for (int t = 0; t < kFChunk; ++t) itri(acc, ild4(pa + t * kIRow), ild4(pa + t * kIRow + 4));
+                } else {
+#pragma unroll 1
+                    for (int t = 0; t < kFChunk; ++t) {
+                        const IRows a = ild4(pa + t * kIRow), b0 = ild4(pb + t * kIRow), b1 = ild4(pb + t * kIRow + 4);
+                        icmac(acc, a, b0, 0);
+                        icmac(acc, a, b1, 4);
+                    }
+                }
+            }
+            const ISub<DIAG> u(tid);
+            const int64_t dc = info->dc0 + u.q;
+            if (dc >= n_dc) continue;
+            const bool add = accumulate || s0 > sbeg || ts > 1;
+            const int I = info->I, J = info->J;
+            const int64_t row0 = dc * P;
+            auto row_of = [&](int i) { return row0 + (int64_t)i * n_inputs - (int64_t)i * (i - 1) / 2 - i; };
+            if (DIAG && u.tri) {
+                const int i0 = I * 64 + 8 * u.h;
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int i = i0 + x;
+                    if (i >= n_inputs) continue;
+                    float2* rowp = vis + row_of(i);
+                    fflush(rowp + i, acc[56 + x], 0.f, add);
+#pragma unroll
+                    for (int y = x + 1; y < 8; ++y)
+                        if (i0 + y < n_inputs)
+                            fflush(rowp + i0 + y, acc[2 * tri_pair(x, y)], acc[2 * tri_pair(x, y) + 1], add);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = I * 64 + 4 * u.g + a;
+                    if (i >= n_inputs) continue;
+                    float2* rowp = vis + row_of(i);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int j = J * 64 + 8 * u.h + b;
+                        if (j < i || j >= n_inputs) continue;
+                        fflush(rowp + j, acc[8 * a + b], acc[32 + 8 * a + b], add);
+                    }
+                }
+            }
+        }
+        // every thread is done with this item's record before thread 0 writes the next one
+        __syncthreads();
+    }
+}
+
 // Sample ranges per item for a launch of base_items items: with fewer than two waves of two
 // blocks per SM, the sample axis is split (whole chunks, at least 64 samples a range).
 void sample_ranges(const Plan& p, int64_t base_items, int* ts, int* range_len) {
@@ -982,6 +858,56 @@ cudaError_t launch_int_feed(const Plan& p, const unsigned char* src, int64_t n_d
     return cudaGetLastError();
 }
 
+template <bool VEC>
+cudaError_t launch_float_feed(const Plan& p, const float2* src, int64_t n_dc, float2* out, int accumulate,
+                              cudaStream_t s) {
+    const int64_t diag_base = (n_dc + kIDiagCh - 1) / kIDiagCh * p.nb;
+    const int64_t off_base = (n_dc + kIOffCh - 1) / kIOffCh * (p.nb * (p.nb - 1) / 2);
+    int ts_d, len_d, ts_o, len_o;
+    sample_ranges(p, diag_base, &ts_d, &len_d);
+    sample_ranges(p, off_base, &ts_o, &len_o);
+    const int64_t diag_items = diag_base * ts_d, off_items = off_base * ts_o;
+    // two row buffers (10 KB per channel-dump and block each) and the item: 80 KB
+    const int smem_diag = 2 * kIDiagCh * kFChunk * kIRow * (int)sizeof(float2) + (int)sizeof(IItem<kIDiagCh>);
+    const int smem_off = 2 * kIOffCh * 2 * kFChunk * kIRow * (int)sizeof(float2) + (int)sizeof(IItem<kIOffCh>);
+    const int64_t P = p.n_baselines, tstride = (int64_t)p.n_chan * p.n_inputs;
+    cudaError_t e = cudaFuncSetAttribute(xeng_fp32_float_kernel<true, VEC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_diag);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xeng_fp32_float_kernel<false, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_off);
+    if (e == cudaSuccess && !accumulate && (ts_d > 1 || ts_o > 1))
+        e = cudaMemsetAsync(out, 0, (size_t)n_dc * P * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
+    if (diag_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 2;
+        const int grid = (int)(diag_items < cap ? diag_items : cap);
+        xeng_fp32_float_kernel<true, VEC><<<grid, kIDiagThreads, smem_diag, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb, P, tstride, n_dc, diag_items, ts_d, len_d, out,
+            accumulate);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (off_items > 0) {
+        const int64_t cap = (int64_t)p.n_sm * 2;
+        const int grid = (int)(off_items < cap ? off_items : cap);
+        xeng_fp32_float_kernel<false, VEC><<<grid, kIOffThreads, smem_off, s>>>(
+            src, p.n_inputs, p.n_chan, p.n_time, p.nb, p.nb * (p.nb - 1) / 2, P, tstride, n_dc, off_items, ts_o,
+            len_o, out, accumulate);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_float(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
+                         cudaStream_t s) {
+    const auto* src = static_cast<const float2*>(d_packed);
+    const bool vec = p.n_inputs % 2 == 0 && (reinterpret_cast<uintptr_t>(d_packed) & 15u) == 0;
+    const int64_t n_dc = (int64_t)n_dumps * p.n_chan;
+    auto* out = static_cast<float2*>(d_vis);
+    return vec ? launch_float_feed<true>(p, src, n_dc, out, accumulate, s)
+               : launch_float_feed<false>(p, src, n_dc, out, accumulate, s);
+}
+
 template <int BITS>
 cudaError_t launch_int(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate, cudaStream_t s) {
     const auto* src = static_cast<const unsigned char*>(d_packed);
@@ -999,7 +925,7 @@ cudaError_t launch_xeng_fp32_packed(const Plan& p, const void* d_packed, int n_d
                                     cudaStream_t s) {
     if (p.sample_bits == 4) return launch_int<4>(p, d_packed, n_dumps, d_vis, accumulate, s);
     if (p.sample_bits == 8) return launch_int<8>(p, d_packed, n_dumps, d_vis, accumulate, s);
-    return launch_packed<32>(p, d_packed, n_dumps, d_vis, accumulate, s);
+    return launch_float(p, d_packed, n_dumps, d_vis, accumulate, s);
 }
 
 }  // namespace corr

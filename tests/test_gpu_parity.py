@@ -269,6 +269,28 @@ def test_float_engines_ragged(n, c, t):
     check_bf16x3(run_engine(x, n, c, t, 32, BF16X3)[0], x, n, c, t)
 
 
+@pytest.mark.parametrize("n,c,t", [(128, 640, 300), (66, 600, 130), (63, 5, 2000)])
+def test_float_fp32_engine_ranges_and_accumulate(n, c, t):
+    # the FP32 engine on float samples: enough channels for one sample range per item (128 and
+    # 66 inputs: multi-block tiles, vector and element-wise staging), or few channels with the
+    # sample axis split across blocks (63 inputs, 2000 samples); then accumulating into its output
+    from paper_0906_1887_gb300 import corr
+    re, im = synth.correlated_gaussian(4100 + n, t, c, n, 4.0, 0.2, as_float=True)
+    x = synth.packf32(re, im)
+    ref = oracle.xcorr_f64(x, n, c, t)
+    plan = corr.Plan(n, c, t, 32)
+    xd = torch.from_numpy(x.reshape(-1).view(np.uint8)).cuda()
+    vis = plan.empty_vis(1, "cuda")
+    plan.run(xd, vis, None, engine=FP32)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    assert normwise_error(vis.cpu().numpy()[0], ref, n) <= 1e-6
+    plan.run(xd, vis, None, accumulate=True, engine=FP32)
+    torch.cuda.synchronize()
+    assert normwise_error(vis.cpu().numpy()[0], 2 * ref, n) <= 1e-6
+    plan.close()
+
+
 @pytest.mark.parametrize("n", [64, 192])
 def test_bounded_wait_gives_up_and_context_survives(n):
     # Failure detection without a GPU fault: the producer withholds one stage, the waiting
