@@ -415,10 +415,12 @@ corr_status corr_batch_destroy(corr_batch b);
  * previous one (Sec. 5, Table 3 notes).  A server takes correlation jobs from any number
  * of host threads (the mailbox), admits them in arrival order by device footprint into
  * an HBM arena allocated once (packed samples + visibilities + any workspace), and runs
- * each on one of n_streams CUDA streams: host-to-device copy, X stage, status readback
- * and, when host_vis is given, device-to-host copy of the visibilities -- so the copies
- * of some jobs overlap the kernels of others.  A job that can never fit the budget is
- * rejected at submission (CORR_EBUSY); one that fits waits until enough space is free.
+ * each on one of n_streams CUDA streams: host-to-device copy, X stage and, when host_vis is
+ * given, device-to-host copy of the visibilities -- so the copies of some jobs overlap the
+ * kernels of others.  The kernels write each job's status words straight into mapped pinned
+ * memory (no copy per job); events and status words are pooled, so submitting and releasing a
+ * job neither allocates nor frees.  A job that can never fit the budget is rejected at
+ * submission (CORR_EBUSY); one that fits waits until enough space is free.
  * Engines: the tensor-core X stage for 4/8-bit samples, BF16x3 for float samples.
  */
 typedef struct corr_server_s *corr_server;   /* opaque, owned by the library */
@@ -494,9 +496,12 @@ corr_status corr_server_destroy(corr_server s, double drain_timeout_s);
  *                                  d_delays is given and writes float32 [n_chan][P][2] into a
  *                                  device dump buffer (the next interval's first job overwrites
  *                                  the accumulators, which resets them);
- *                                  copied to the closing job's host_vis when it is not NULL, else
- *                                  left there (corr_job_result.d_vis) until the stream's next
- *                                  dump overwrites it.
+ *                                  copied to the closing job's host_vis when it is not NULL (on
+ *                                  a third CUDA stream of the open stream, so its next jobs do
+ *                                  not wait for the copy; the closing job completes when the
+ *                                  dump is in host memory), else left there
+ *                                  (corr_job_result.d_vis) until the stream's next dump
+ *                                  overwrites it.
  * The stream's CUDA streams get a priority from its dump length (shorter dumps, tighter
  * deadlines: higher priority), which orders kernels of different streams when the GPU is busy.
  * Jobs submitted with that stream_tag must have the stream's shape (CORR_EINVAL otherwise); they
