@@ -74,4 +74,35 @@ def test_headline_full_launch_sampled_dumps():
     auto_idx = torch.tensor([i * n - i * (i - 1) // 2 for i in range(n)], device=dev)
     autos = vis.index_select(2, auto_idx)
     assert bool((autos[..., 1] == 0).all()) and bool((autos[..., 0] >= 0).all())
+    # the FP32 CUDA-core engine on the same 200 dumps, as the benchmark runs it: both engines are
+    # exact on integer samples, so every one of the 200 x 768 x 2080 results must agree
+    vis32 = plan.empty_vis(d, dev)
+    vis32.fill_(-7)
+    plan.run(packed, vis32, None, engine=corr.ENGINE_FP32, n_dumps=d)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    assert torch.equal(vis32, vis)
+    plan.close()
+
+
+def test_large_array_fp32_equals_tensor_core_full_dump():
+    # one full dump of the 1024-input array (1536 channels x 256 samples): the plane-fed
+    # tensor-core path and the FP32 engine, all 1536 x 524800 results equal; two channels
+    # against the oracle
+    from paper_0906_1887_gb300 import corr
+    n, c, t = 1024, 1536, 256
+    dev = torch.device("cuda:0")
+    packed = synth.torch_correlated_gaussian_packed8(1, t, c, n, 8.0, 0.0, 3000, dev)
+    plan = corr.Plan(n, c, t, 8)
+    vis_tc = plan.empty_vis(1, dev)
+    plan.run(packed, vis_tc, plan.empty_workspace(corr.ENGINE_TC, 1, dev), engine=corr.ENGINE_TC)
+    vis32 = plan.empty_vis(1, dev)
+    plan.run(packed, vis32, None, engine=corr.ENGINE_FP32)
+    torch.cuda.synchronize()
+    assert plan.check_device() == 0
+    assert torch.equal(vis_tc, vis32)
+    for ch in (5, 1400):
+        one = packed[0, :, ch:ch + 1].contiguous().cpu().numpy()
+        ref = oracle.xcorr_int(one, n, 1, t, 8)[0]
+        assert np.array_equal(vis_tc[0, ch].cpu().numpy(), ref), ch
     plan.close()
