@@ -317,6 +317,17 @@ cudaError_t run_x(const Plan& p, const corr_job_desc& d, bool raw, const char* d
 }
 
 // Issue one admitted job on its stream (called with the lock released).
+// A job's samples to the device in pieces of at most kCopyPiece bytes: the copy engines serve
+// operations in order, so a small job's copy waits behind at most one piece of a large one.
+constexpr size_t kCopyPiece = (size_t)64 << 20;
+cudaError_t copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (size_t off = 0; off < bytes && e == cudaSuccess; off += kCopyPiece)
+        e = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off,
+                            std::min(kCopyPiece, bytes - off), cudaMemcpyHostToDevice, s);
+    return e;
+}
+
 cudaError_t issue(corr_server_s* S, Job& j) {
     cudaStream_t s = S->streams[j.stream];
     char* base = S->d_base + j.off;
@@ -328,8 +339,7 @@ cudaError_t issue(corr_server_s* S, Job& j) {
     // submission): no copy of 16 bytes queued on a copy engine behind other jobs' large copies
     p.d_status = j.d_status;
     cudaError_t e = cudaEventRecord(j.ev_start, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc),
-                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = copy_in(d_packed, j.desc.host_packed, packed_bytes(j.desc), s);
     if (e == cudaSuccess) e = run_x(p, j.desc, j.raw, d_packed, d_vis, d_ws, 0, s);
     if (e == cudaSuccess && j.desc.host_vis)
         e = cudaMemcpyAsync(j.desc.host_vis, d_vis, vis_bytes(j.desc), cudaMemcpyDeviceToHost, s);
@@ -355,7 +365,7 @@ cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
     if (j.seq >= R) e = cudaStreamWaitEvent(st.copy_s, st.slot_free[slot], 0);
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st.copy_s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_packed, j.desc.host_packed, packed_bytes(j.desc), cudaMemcpyHostToDevice, st.copy_s);
+        e = copy_in(d_packed, j.desc.host_packed, packed_bytes(j.desc), st.copy_s);
     if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[slot], st.copy_s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[slot], 0);
     if (e == cudaSuccess) e = run_x(p, j.desc, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
