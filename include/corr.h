@@ -417,9 +417,11 @@ corr_status corr_batch_destroy(corr_batch b);
  * an HBM arena allocated once (packed samples + visibilities + any workspace), and runs
  * each on one of n_streams CUDA streams: host-to-device copy, X stage and, when host_vis is
  * given, device-to-host copy of the visibilities -- so the copies of some jobs overlap the
- * kernels of others.  The kernels write each job's status words straight into mapped pinned
- * memory (no copy per job); events and status words are pooled, so submitting and releasing a
- * job neither allocates nor frees.  A job that can never fit the budget is rejected at
+ * kernels of others.  Jobs are issued earliest deadline first (submission time + the job's own
+ * sample time at a 10 kHz channel rate; an open stream's jobs keep their order), each when its
+ * samples fit a 256 MB budget of host-to-device bytes in flight.  The kernels write each job's
+ * status words straight into mapped pinned memory (no copy per job); events and status words
+ * are pooled, so submitting and releasing a job neither allocates nor frees.  A job that can never fit the budget is rejected at
  * submission (CORR_EBUSY); one that fits waits until enough space is free.
  * Engines: the tensor-core X stage for 4/8-bit samples, BF16x3 for float samples.
  */

@@ -117,6 +117,9 @@ struct Job {
     bool closes = false;       // ends a dump interval of its open stream
     int64_t n_accum = 0;       // samples summed in that dump
     StreamState* st = nullptr;  // the open stream's state (stream jobs)
+    double deadline = 0;       // t_submit + the job's own sample time (earliest-deadline-first issue)
+    cudaEvent_t ev_copied = nullptr;   // recorded after the job's samples reached the device
+    size_t copy_bytes = 0;     // its host-to-device bytes while they count against the copy budget
 };
 
 // Device state of one open input stream (corr_server_open_stream).
@@ -295,6 +298,8 @@ struct corr_server_s {
     corr_server_stats stats{};
     std::map<int, corr::StreamState*> open_streams;   // by stream_tag
     corr::JobResources res;                           // recycled status words and events (lock held)
+    size_t copy_inflight = 0;                         // host-to-device bytes issued and not yet landed
+    std::vector<uint64_t> copying;                    // jobs whose copies count against the budget
 };
 
 namespace corr {
@@ -340,6 +345,7 @@ cudaError_t issue(corr_server_s* S, Job& j) {
     p.d_status = j.d_status;
     cudaError_t e = cudaEventRecord(j.ev_start, s);
     if (e == cudaSuccess) e = copy_in(d_packed, j.desc.host_packed, packed_bytes(j.desc), s);
+    if (e == cudaSuccess) e = cudaEventRecord(j.ev_copied, s);
     if (e == cudaSuccess) e = run_x(p, j.desc, j.raw, d_packed, d_vis, d_ws, 0, s);
     if (e == cudaSuccess && j.desc.host_vis)
         e = cudaMemcpyAsync(j.desc.host_vis, d_vis, vis_bytes(j.desc), cudaMemcpyDeviceToHost, s);
@@ -366,6 +372,7 @@ cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st.copy_s);
     if (e == cudaSuccess)
         e = copy_in(d_packed, j.desc.host_packed, packed_bytes(j.desc), st.copy_s);
+    if (e == cudaSuccess) e = cudaEventRecord(j.ev_copied, st.copy_s);
     if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[slot], st.copy_s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[slot], 0);
     if (e == cudaSuccess) e = run_x(p, j.desc, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
@@ -401,26 +408,47 @@ cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
     return e;
 }
 
-// The next job the dispatcher may issue: the first job of an open stream in the mailbox (they
-// need no arena space), or the first other job if it fits the arena's free space (the others
-// wait behind it in arrival order).  Called with the lock held.
+// Copies in flight are capped so that a job with an early deadline never queues behind a
+// backlog of other jobs' copies (copy engines serve operations in order): a job may start its
+// copy when nothing is in flight or its bytes fit the budget with what is.
+constexpr size_t kCopyBudget = (size_t)256 << 20;
+// Deadlines: a job's own sample time at the paper's channel rate (1.28 MHz over 128 channels =
+// 10 kHz); only their order matters, so the rate is a scale, the same for every job.
+constexpr double kChannelRateHz = 10000.0;
+bool copy_fits(const corr_server_s* S, size_t bytes) {
+    return S->copy_inflight == 0 || S->copy_inflight + bytes <= kCopyBudget;
+}
+
+// The next job the dispatcher may issue, earliest deadline first among the candidates: the
+// first queued job of each open stream (a stream's jobs keep their order: ring slots, intervals)
+// once its ring slot is free on the device, and the first other job once it fits the arena's
+// free space (the others wait behind it in arrival order).  The earliest candidate is issued
+// when its copy fits the budget; otherwise nothing is, until the copies in flight drain (a later
+// deadline never overtakes it, so a large job is not starved by a stream of small ones).
+// Called with the lock held.
 bool pick_next(corr_server_s* S, std::deque<uint64_t>::iterator* pick) {
-    bool arena_head_seen = false;
+    bool arena_head_seen = false, found = false;
+    double best = 0;
+    std::vector<const StreamState*> heads;
     for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
         const Job& j = S->jobs[*it];
+        bool ready = false;
         if (j.stream_job) {
-            *pick = it;
-            return true;
-        }
-        if (!arena_head_seen) {
+            if (std::find(heads.begin(), heads.end(), j.st) != heads.end()) continue;
+            heads.push_back(j.st);
+            const int R = j.st->d.ring_slots;
+            ready = j.seq < R || cudaEventQuery(j.st->slot_free[(int)(j.seq % R)]) != cudaErrorNotReady;
+        } else if (!arena_head_seen) {
             arena_head_seen = true;
-            if (S->arena->fits(j.bytes)) {
-                *pick = it;
-                return true;
-            }
+            ready = S->arena->fits(j.bytes);
+        }
+        if (ready && (!found || j.deadline < best)) {
+            found = true;
+            best = j.deadline;
+            *pick = it;
         }
     }
-    return false;
+    return found && copy_fits(S, packed_bytes(S->jobs[**pick].desc));
 }
 
 void dispatcher_loop(corr_server_s* S) {
@@ -429,7 +457,10 @@ void dispatcher_loop(corr_server_s* S) {
     while (true) {
         std::deque<uint64_t>::iterator pick;
         bool have = false;
-        S->cv_dispatch.wait_for(lock, std::chrono::milliseconds(50), [&] {
+        // queued jobs blocked on a ring slot or on the copy budget are looked at again soon
+        // (the completion thread also wakes this thread when copies land or jobs finish)
+        const auto wait = S->queue.empty() ? std::chrono::microseconds(50000) : std::chrono::microseconds(500);
+        S->cv_dispatch.wait_for(lock, wait, [&] {
             if (S->stop) return true;
             if (S->paused || S->queue.empty()) return false;
             have = pick_next(S, &pick);
@@ -440,6 +471,8 @@ void dispatcher_loop(corr_server_s* S) {
         const uint64_t id = *pick;
         Job& j = S->jobs[id];
         cudaError_t e = cudaSuccess;
+        j.copy_bytes = packed_bytes(j.desc);
+        S->copy_inflight += j.copy_bytes;
         if (j.stream_job) {
             S->queue.erase(pick);
             j.state = kRunning;
@@ -466,8 +499,13 @@ void dispatcher_loop(corr_server_s* S) {
             lock.lock();
         }
         // the completion thread sees the job only once its events are recorded
-        if (e == cudaSuccess) S->running.push_back(id);
+        if (e == cudaSuccess) {
+            S->running.push_back(id);
+            S->copying.push_back(id);
+        }
         if (e != cudaSuccess) {
+            S->copy_inflight -= j.copy_bytes;
+            j.copy_bytes = 0;
             // nothing of this job is queued behind a failed call that we can rely on; mark it
             // failed once its stream has drained the calls that were accepted
             cudaStreamSynchronize(j.stream_job ? j.st->comp_s : S->streams[j.stream]);
@@ -494,6 +532,19 @@ void completer_loop(corr_server_s* S) {
     std::unique_lock<std::mutex> lock(S->mu);
     while (true) {
         bool progressed = false;
+        // copies that have landed give their bytes back to the copy budget
+        for (size_t k = 0; k < S->copying.size();) {
+            Job& j = S->jobs[S->copying[k]];
+            if (cudaEventQuery(j.ev_copied) == cudaErrorNotReady) {
+                ++k;
+                continue;
+            }
+            S->copy_inflight -= j.copy_bytes;
+            j.copy_bytes = 0;
+            S->copying[k] = S->copying.back();
+            S->copying.pop_back();
+            progressed = true;
+        }
         for (size_t k = 0; k < S->running.size();) {
             Job& j = S->jobs[S->running[k]];
             const cudaError_t q = cudaEventQuery(j.ev_done);
@@ -515,6 +566,13 @@ void completer_loop(corr_server_s* S) {
             }
             if (j.state == kDone) S->stats.completed++;
             else S->stats.failed++;
+            if (j.copy_bytes) {
+                // its copy preceded its completion event, whichever of the two this pass saw
+                // first: settle the copy budget before the job can be released
+                S->copy_inflight -= j.copy_bytes;
+                j.copy_bytes = 0;
+                S->copying.erase(std::find(S->copying.begin(), S->copying.end(), S->running[k]));
+            }
             if (j.stream_job) {
                 // an averaged dump left on the device stays in the stream's dump buffer
                 j.d_vis = (j.state == kDone && j.closes && !j.desc.host_vis &&
@@ -665,6 +723,7 @@ corr_status corr_submit(corr_server S, const corr_job_desc* d, uint64_t* job_id)
     }
     cudaError_t e = S->res.take_event(&j.ev_start);
     if (e == cudaSuccess) e = S->res.take_event(&j.ev_done);
+    if (e == cudaSuccess) e = S->res.take_event(&j.ev_copied);
     JobResources::Slot slot{};
     if (e == cudaSuccess) e = S->res.take_status(&slot);
     j.h_status = slot.host;
@@ -672,11 +731,13 @@ corr_status corr_submit(corr_server S, const corr_job_desc* d, uint64_t* job_id)
     if (e != cudaSuccess) {
         S->res.give_event(j.ev_start);
         S->res.give_event(j.ev_done);
+        S->res.give_event(j.ev_copied);
         return cuda_error(e, "corr_submit");
     }
     if (st) st->n_submitted++;
     j.id = S->next_id++;
     j.t_submit = now_s();
+    j.deadline = j.t_submit + (double)d->n_time / kChannelRateHz;
     *job_id = j.id;
     S->jobs.emplace(j.id, j);
     S->queue.push_back(j.id);
@@ -728,6 +789,7 @@ corr_status corr_release(corr_server S, uint64_t job_id) {
     }
     S->res.give_event(j.ev_start);
     S->res.give_event(j.ev_done);
+    S->res.give_event(j.ev_copied);
     S->res.give_status(JobResources::Slot{j.h_status, j.d_status});
     S->jobs.erase(it);
     return CORR_OK;
