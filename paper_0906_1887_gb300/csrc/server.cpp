@@ -471,13 +471,13 @@ void dispatcher_loop(corr_server_s* S) {
         const uint64_t id = *pick;
         Job& j = S->jobs[id];
         cudaError_t e = cudaSuccess;
-        j.copy_bytes = packed_bytes(j.desc);
-        S->copy_inflight += j.copy_bytes;
         if (j.stream_job) {
             S->queue.erase(pick);
             j.state = kRunning;
             j.t_start = now_s();
             StreamState* st = j.st;
+            j.copy_bytes = packed_bytes(j.desc);
+            S->copy_inflight += j.copy_bytes;
             lock.unlock();
             e = issue_stream(S, j, *st);
             lock.lock();
@@ -494,6 +494,8 @@ void dispatcher_loop(corr_server_s* S) {
             j.d_vis = S->d_base + off + round_up(16) + round_up(packed_bytes(j.desc));   // layout of issue()
             S->stats.bytes_in_use = S->arena->used();
             S->stats.peak_bytes = S->arena->peak();
+            j.copy_bytes = packed_bytes(j.desc);
+            S->copy_inflight += j.copy_bytes;
             lock.unlock();
             e = issue(S, j);
             lock.lock();
