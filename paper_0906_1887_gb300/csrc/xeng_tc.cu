@@ -369,26 +369,6 @@ __device__ __forceinline__ void convert_slice_f32(uint32_t raw_tile, uint32_t ds
     }
 }
 
-// Raw ring feed: packed tile [64 t][64 inputs] staged in shared memory (t rows PITCH bytes
-// apart), raw_lane = raw + the lane's byte offset.
-template <uint32_t PITCH>
-__device__ __forceinline__ void convert_slice8(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
-    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
-    uint32_t w[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
-    convert_words8(w, dst, q, cl);
-}
-
-template <uint32_t PITCH>
-__device__ __forceinline__ void convert_slice4(uint32_t raw_lane, uint32_t dst, int q, const ConvLane& cl) {
-    const uint32_t src = raw_lane + (uint32_t)q * (8u * PITCH);
-    uint32_t w[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * PITCH);
-    convert_words4(w, dst, q, cl);
-}
-
 __device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
                  : "memory");
