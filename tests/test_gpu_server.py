@@ -296,3 +296,33 @@ def test_destroy_with_open_streams_and_queued_jobs():
     ids = [srv.submit(64, 8, 256, 8, j["host_in"], None, stream_tag=1) for _ in range(3)]
     ids += [srv.submit(16, 4, 64, 4, k["host_in"], None, stream_tag=2) for _ in range(3)]
     assert srv.close(drain_timeout_s=30.0) == corr.OK
+
+
+def test_earliest_deadline_first_issue_order():
+    # jobs queued while the dispatcher is paused start in order of their deadlines (submission
+    # time + their own sample time), not in order of arrival: the first queued job of each open
+    # stream and the first arena job are the candidates
+    from paper_0906_1887_gb300 import corr
+    srv = corr.Server(256 * MiB, n_streams=2, flags=corr.SERVER_START_PAUSED)
+    specs = {1: (32, 4, 2048), 3: (32, 4, 512), 2: (32, 4, 64)}    # tag -> (n, c, t)
+    for tag, (n, c, t) in specs.items():
+        srv.open_stream(tag, n, c, t, 8, ring_slots=2, jobs_per_dump=1)
+    jobs, ids = {}, {}
+    for tag, (n, c, t) in specs.items():                           # arrival order 1, 3, 2
+        jobs[tag] = _job(7000 + tag, n, c, t, 8)
+        ids[tag] = srv.submit(n, c, t, 8, jobs[tag]["host_in"], jobs[tag]["host_out"], stream_tag=tag)
+    jobs["arena"] = _job(7100, 32, 4, 128, 8)
+    ids["arena"] = srv.submit(32, 4, 128, 8, jobs["arena"]["host_in"], jobs["arena"]["host_out"])
+    srv.resume()
+    starts = {}
+    for key, jid in ids.items():
+        st, r = srv.wait(jid, 60.0)
+        assert st == corr.OK, (key, corr.last_error())
+        assert np.array_equal(jobs[key]["host_out"].numpy(), jobs[key]["ref"]), key
+        starts[key] = r.t_start
+        srv.release(jid)
+    # deadlines: tag 2 (64 samples) < arena (128) < tag 3 (512) < tag 1 (2048)
+    assert sorted(starts, key=starts.get) == [2, "arena", 3, 1], starts
+    for tag in specs:
+        assert srv.close_stream(tag) == corr.OK
+    srv.close()
