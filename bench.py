@@ -287,8 +287,65 @@ def run_mwa32t(args):
                         "note": "one 4.3 MB dump is launch- and latency-bound, far from either roofline"},
            "fp32_path": {"kernel_ms": ms32, "value": cm / (ms32 / 1e3) / 1e12, "speedup_tc_over_fp32": ms32 / ms},
            "l2": "256 MB written between timed steps"}
+    # the plan's default feeds 4-bit samples as e4m3 operands (kind::f8f6f4); the same dump with
+    # fp16 operands: identical results, twice the operand bytes and MMAs per sample
+    plan16 = corr.Plan(n, c, t, 4)
+    plan16.set_operands(corr.OPERANDS_PACKED, 0)
+    vis16 = plan16.empty_vis(1, dev)
+    f16 = lambda: plan16.run(x, vis16, None, engine=corr.ENGINE_TC, stream=stream)   # noqa: E731
+    for _ in range(args.warmup):
+        f16()
+    tc()
+    torch.cuda.synchronize()
+    assert plan16.check_device() == 0 and torch.equal(vis, vis16)
+    ms16 = _event_ms(f16, steps, stream, flush)
+    res["operands"] = "e4m3 (tcgen05 kind::f8f6f4)"
+    res["fp16_operands"] = {"kernel_ms": ms16, "value": cm / (ms16 / 1e3) / 1e12, "same_bits": True}
+    plan16.close()
     plan.close()
+    del x, vis, vis16, ws32, flush
+    _free()
+    res["stream64_4bit"] = _stream4(args)
     return res
+
+
+def _stream4(args):
+    """A 4-bit stream at the headline's array size (64 inputs x 768 channels x 1000 samples per
+    dump, 50 dumps, 2.5 GB in) through fp16 and e4m3 operands: where the conversion and the
+    operand reads, not the launch, set the pace."""
+    import torch
+
+    from paper_0906_1887_gb300 import corr, synth
+    n, c, t, d = 64, 768, 1000, 50
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    x = synth.torch_uniform_packed4(d, t, c, n, 1100, dev, -8, 7).reshape(-1)
+    out = {}
+    vis = {}
+    for name, ops in (("fp16", corr.OPERANDS_PACKED), ("e4m3", corr.OPERANDS_PACKED_F8)):
+        plan = corr.Plan(n, c, t, 4)
+        plan.set_operands(ops, 0)
+        v = plan.empty_vis(d, dev)
+        fn = lambda: plan.run(x, v, None, engine=corr.ENGINE_TC, n_dumps=d, stream=stream)   # noqa: E731
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        assert plan.check_device() == 0
+        ms = _event_ms(fn, max(args.steps, 3), stream)
+        P = plan.n_baselines
+        by = d * (t * c * n + c * P * 16)
+        hbm, _, src = _peaks()
+        out[name] = {"kernel_ms": ms, "value": P * c * t * d / (ms / 1e3) / 1e12,
+                     "hbm_frac": by / (ms / 1e3) / 1e9 / hbm}
+        vis[name] = v
+        plan.close()
+    out["same_bits"] = bool(torch.equal(vis["fp16"], vis["e4m3"]))
+    out["workload"] = "stream64_4bit: 64 inputs x 768 ch x 1000 samples/dump x 50 dumps, 4-bit uniform [-8, 7]"
+    out["unit"] = "TeraCMAC/s"
+    out["l2"] = "inputs (2.5 GB) larger than L2"
+    del x, vis
+    _free()
+    return out
 
 
 def run_large(args):

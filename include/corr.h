@@ -130,16 +130,23 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
  * traffic).  operands:
  *   CORR_OPERANDS_AUTO    planes for arrays of at least 256 inputs (4 blocks) when a workspace
  *                         is given, and always where the packed rows are not 16-byte multiples;
- *   CORR_OPERANDS_PACKED  always the fused conversion (CORR_EUNSUPPORTED where rows are not
- *                         16-byte multiples);
- *   CORR_OPERANDS_PLANES  always planes (the workspace is then required).
+ *                         otherwise the fused conversion, into e4m3 operands for 4-bit samples;
+ *   CORR_OPERANDS_PACKED  always the fused conversion into fp16 operands (CORR_EUNSUPPORTED
+ *                         where rows are not 16-byte multiples);
+ *   CORR_OPERANDS_PLANES  always planes (the workspace is then required);
+ *   CORR_OPERANDS_PACKED_F8  4-bit samples only: the fused conversion into fp8 e4m3 operands
+ *                         (tcgen05 kind::f8f6f4, 128 samples per 128-byte operand row), which hold
+ *                         -8..7 exactly and halve the operand bytes per sample; fp32 accumulation
+ *                         as for fp16, so results stay bit-exact (CORR_EUNSUPPORTED for 8-bit
+ *                         samples, whose range e4m3 does not hold, or rows that are not 16-byte
+ *                         multiples).  The fused dump call keeps fp16 operands.
  * items (plane feed): CORR_ITEMS_WIDE = work items of block I against blocks J and J + 1 in one
  * M = 128, N = 256 MMA (a quarter fewer operand loads per tile); CORR_ITEMS_TILES = one 64 x 64
  * input tile per item; CORR_ITEMS_AUTO = wide, except single tiles for accumulating dumps of
  * fewer than 1024 samples (bound by their read-modify-write of the output).  CORR_EINVAL on
  * unknown values.
  */
-enum { CORR_OPERANDS_AUTO = 0, CORR_OPERANDS_PACKED = 1, CORR_OPERANDS_PLANES = 2 };
+enum { CORR_OPERANDS_AUTO = 0, CORR_OPERANDS_PACKED = 1, CORR_OPERANDS_PLANES = 2, CORR_OPERANDS_PACKED_F8 = 3 };
 enum { CORR_ITEMS_AUTO = 0, CORR_ITEMS_TILES = 1, CORR_ITEMS_WIDE = 2 };
 corr_status corr_plan_set_operands(corr_plan plan, int operands, int items);
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libcorr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, PENDING, EUNSUPPORTED = range(8)
 ENGINE_TC, ENGINE_FP32, ENGINE_BF16X3 = 0, 1, 2
-OPERANDS_AUTO, OPERANDS_PACKED, OPERANDS_PLANES = 0, 1, 2
+OPERANDS_AUTO, OPERANDS_PACKED, OPERANDS_PLANES, OPERANDS_PACKED_F8 = 0, 1, 2, 3
 ITEMS_AUTO, ITEMS_TILES, ITEMS_WIDE = 0, 1, 2
 F_COMPLEX8, F_COMPLEX4, F_REAL8 = 0, 1, 2
 STATUS_NAMES = {OK: "CORR_OK", EINVAL: "CORR_EINVAL", ENOMEM: "CORR_ENOMEM", ECUDA: "CORR_ECUDA",
@@ -240,8 +240,9 @@ class Plan:
         check(lib().corr_plan_set_tuning(self._h, op_stages, float_planes), "corr_plan_set_tuning")
 
     def set_operands(self, operands: int = OPERANDS_AUTO, items: int = ITEMS_AUTO):
-        """Operand feed of the tensor-core engine (packed samples or fp16 planes) and the plane
-        feed's work-item shape; results do not depend on either."""
+        """Operand feed of the tensor-core engine (packed samples into fp16 or, for 4-bit samples,
+        e4m3 operands, or fp16 planes) and the plane feed's work-item shape; results do not
+        depend on either."""
         check(lib().corr_plan_set_operands(self._h, operands, items), "corr_plan_set_operands")
 
     def workspace_size(self, engine: int, n_dumps: int = 1) -> int:

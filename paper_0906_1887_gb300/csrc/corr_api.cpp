@@ -126,14 +126,17 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
 
 corr_status corr_plan_set_operands(corr_plan plan, int operands, int items) {
     if (!plan) return set_error(CORR_EINVAL, "corr_plan_set_operands: plan is NULL");
-    if (operands < CORR_OPERANDS_AUTO || operands > CORR_OPERANDS_PLANES)
+    if (operands < CORR_OPERANDS_AUTO || operands > CORR_OPERANDS_PACKED_F8)
         return set_error(CORR_EINVAL, "operands=%d is not a CORR_OPERANDS_* value", operands);
     if (items < CORR_ITEMS_AUTO || items > CORR_ITEMS_WIDE)
         return set_error(CORR_EINVAL, "items=%d is not a CORR_ITEMS_* value", items);
     Plan* p = reinterpret_cast<Plan*>(plan);
-    if (operands == CORR_OPERANDS_PACKED && !tc_raw_supported(*p))
+    if ((operands == CORR_OPERANDS_PACKED || operands == CORR_OPERANDS_PACKED_F8) && !tc_raw_supported(*p))
         return set_error(CORR_EUNSUPPORTED, "packed rows of %d inputs are not 16-byte multiples: planes only",
                          p->n_inputs);
+    if (operands == CORR_OPERANDS_PACKED_F8 && p->sample_bits != 4)
+        return set_error(CORR_EUNSUPPORTED, "e4m3 operands hold 4-bit samples exactly, not %d-bit ones",
+                         p->sample_bits);
     p->tc_operands = operands;
     p->tc_items = items;
     return CORR_OK;

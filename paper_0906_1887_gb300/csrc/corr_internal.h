@@ -39,7 +39,8 @@ struct Plan {
     int* d_status = nullptr; // [4] device status words
     int tc_op_stages = 0;     // operand ring depth of the packed-sample kernel (0: default)
     int tc_float_planes = 0;  // BF16x3: 1 = hi/lo planes through memory even where the fused path applies
-    int tc_operands = 0;      // 4/8-bit, tensor cores: 0 auto, 1 packed samples (fused converters), 2 fp16 planes
+    int tc_operands = 0;      // 4/8-bit, tensor cores: 0 auto, 1 packed samples (fused converters), 2 fp16 planes,
+                              // 3 packed 4-bit samples converted to e4m3 operands
     int tc_items = 0;         // plane path: 0 auto (wide), 1 single tiles, 2 wide items
     // host-buffer pipeline (corr_xengine_run_host), created on first use
     char* pipe_dev = nullptr;   // 2 x (chunk inputs) + 2 x (chunk outputs) + workspace
@@ -103,6 +104,7 @@ struct TcTuning {
     int smem_reserve = 0;         // plane feed: shared memory per SM left free for a concurrent kernel
     uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
+    int f8_operands = 0;          // packed 4-bit samples: e4m3 operands (kind::f8f6f4), single-job launches
 };
 int tc_default_cpi(int n_inputs, int64_t channels, int n_sm);   // channels = dumps x n_chan of the launch
 // BF16x3 on float samples with the hi/lo split done in the tensor-core kernel (single-block arrays)
@@ -115,7 +117,7 @@ cudaError_t launch_xeng_tc_raw_dump(const Plan& p, const void* d_packed, int n_d
                                     float inv_n, cudaStream_t s);
 // Per-input phasors exp(+2 pi i nu_c tau_n) as float2 [C][N], formed in double precision.
 cudaError_t launch_phasors(const Plan& p, const double* d_delays, const double* d_freqs, void* d_g, cudaStream_t s);
-bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp);
+bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp, bool f8 = false);   // f8: 128-sample boxes
 // Jobs whose samples the unpack kernel already turned into fp16 planes (TcJobSpec::data = the
 // planes, [n_dumps][C][NB][128][Kp]); one channel per work item.
 bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp);

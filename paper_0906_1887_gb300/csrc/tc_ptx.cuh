@@ -155,6 +155,20 @@ __device__ __forceinline__ void mma_f16_lo(uint32_t d_tmem, uint32_t a_lo, uint3
         : "memory");
 }
 
+// The same with kind::f8f6f4: 8-bit float operands (both e4m3 here; the instruction
+// descriptor's A/B type code 0), K = 32 per MMA, so one K step is again 32 bytes of a row.
+__device__ __forceinline__ void mma_f8_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t desc_hi,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %3};\n\t"
+        "mov.b64 db, {%2, %3};\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on `bar` when every previously issued tcgen05.mma of this thread is done.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -204,6 +218,7 @@ __device__ __forceinline__ uint32_t sw128_desc_lo(uint32_t saddr) { return ((sad
 __host__ __device__ constexpr uint32_t sw128_desc_hi() { return (1024u >> 4) | (1u << 14) | (2u << 29); }
 
 // Instruction descriptor of kind::f16: fp32 accumulator, A/B fp16 (or bf16), both K-major.
+// Under kind::f8f6f4 the same word (type code 0) means A/B e4m3.
 __host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16) {
     return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
            (static_cast<uint32_t>(m >> 4) << 24);

@@ -49,6 +49,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -77,21 +78,25 @@ constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 // slot and its destination are 16-byte aligned together and the bulk copies stay aligned.
 constexpr int kStageRowBytesF = 66 * 8;
 
-enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRawF32 = 4 };
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRawF32 = 4, kRaw4F8 = 5 };
 
 template <int MODE>
 struct Cfg {
     // kRawF32: float32 complex samples loaded by TMA and split into bf16 hi + lo by the converter
     // warps (the BF16x3 products of the planes path, without the planes in memory)
     static constexpr bool kFloat = MODE == kRawF32;
-    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || kFloat);
+    // kRaw4F8: 4-bit samples converted to e4m3 operand bytes (kind::f8f6f4): a 128-byte operand
+    // row then holds 128 samples, so a stage covers 128 samples in four K = 32 MMAs
+    static constexpr bool kF8 = MODE == kRaw4F8;
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || kFloat || kF8);
     static constexpr bool kBits8 = MODE == kRaw8;
     static constexpr bool kSplit = (MODE == kPlanesBF16x3 || kFloat);
     static constexpr int kEpiWarps = 4;     // one per tensor-memory lane quarter
     static constexpr int kConvWarps = 8;
     static constexpr int kThreads = 64 + 32 * kEpiWarps + (kRaw ? 32 * kConvWarps : 0);
     static constexpr int kBps = kFloat ? 8 : (kBits8 ? 2 : 1);            // packed bytes per sample
-    static constexpr int kRawTileBytes = kRaw ? kTimeBlock * kBlockInputs * kBps : 0;
+    static constexpr int kStageT = kF8 ? 2 * kTimeBlock : kTimeBlock;    // samples per stage
+    static constexpr int kRawTileBytes = kRaw ? kStageT * kBlockInputs * kBps : 0;
     // x coordinate of a 64-input block in the raw tensor map: bytes, or 8-byte complex floats
     static constexpr int kMapX = kFloat ? kBlockInputs : kBlockInputs * kBps;
     static constexpr int kTilesPerOperand = kSplit ? 2 : 1;               // hi (+ lo)
@@ -336,6 +341,49 @@ __device__ __forceinline__ void convert_words4(const uint32_t (&w)[8], uint32_t 
     }
 }
 
+// Four exact e4m3 bytes (samples in order) from two fp16 pairs whose values are integers in
+// -8..7, which e4m3 (3 mantissa bits) holds exactly: the conversion cannot round.
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t h01, uint32_t h23) {
+    __half2_raw a, b;
+    a.x = (unsigned short)(h01 & 0xFFFFu);
+    a.y = (unsigned short)(h01 >> 16);
+    b.x = (unsigned short)(h23 & 0xFFFFu);
+    b.y = (unsigned short)(h23 >> 16);
+    const uint32_t lo = __nv_cvt_halfraw2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_halfraw2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
+
+// Packed 4-bit words -> e4m3 operand tile (128 samples per 128-byte row): lane l holds
+// w[e] = inputs 4m .. 4m+3 (m = l & 15) of sample 16c + e, e = 0..15, and writes, for the re
+// and im rows of each of its four inputs, the row's 16-byte chunk c (16 samples).
+__device__ __forceinline__ void convert_words4_f8(const uint32_t (&w)[16], uint32_t dst, int c, const ConvLane& cl) {
+    const __half2 bias = conv::bias4();
+    const uint32_t flip = conv::kFlip4;
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
+        lo[e] = w[e] & 0x0F0F0F0Fu;         // im nibble per byte
+    }
+    const uint32_t c16 = (uint32_t)c << 4;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t sel = cl.sel[kk];
+        const uint32_t at = dst + cl.rowoff[kk];
+        uint32_t r[4], m[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            r[o] = e4m3x4(pair_to_half2(hi[4 * o], hi[4 * o + 1], sel, flip, bias),
+                          pair_to_half2(hi[4 * o + 2], hi[4 * o + 3], sel, flip, bias));
+            m[o] = e4m3x4(pair_to_half2(lo[4 * o], lo[4 * o + 1], sel, flip, bias),
+                          pair_to_half2(lo[4 * o + 2], lo[4 * o + 3], sel, flip, bias));
+        }
+        st_shared_v4(at + (c16 ^ cl.r7x16[kk]), r[0], r[1], r[2], r[3]);
+        st_shared_v4(at + 128u + (c16 ^ (cl.r7x16[kk] + 16u)), m[0], m[1], m[2], m[3]);
+    }
+}
+
 // One warp-sized slice of a float32 tile -> bf16 hi and lo operand tiles (hi = bf16(x),
 // lo = bf16(x - hi), both rounded to nearest, as the planes path splits).  A raw sample row
 // holds 128 words, (re, im) of 64 inputs, so word w of a row is operand row w; lane l takes
@@ -395,6 +443,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         "%5}], [%6];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
         : "memory");
+}
+
+// One K step of a stage: 16 fp16 samples (kind::f16) or 32 e4m3 samples (kind::f8f6f4); either
+// way 32 bytes of each 128-byte operand row, so the descriptors advance alike.
+template <bool F8>
+__device__ __forceinline__ void mma_op(uint32_t d, uint32_t a_lo, uint32_t b_lo, uint32_t hi, uint32_t idesc,
+                                       uint32_t acc) {
+    if constexpr (F8) ptx::mma_f8_lo(d, a_lo, b_lo, hi, idesc, acc);
+    else ptx::mma_f16_lo(d, a_lo, b_lo, hi, idesc, acc);
 }
 
 // DUMP: the epilogue writes the dump-mode float pairs (out_mode = 1 jobs) instead of int64
@@ -471,7 +528,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 const TcJob& jb = prm.jobs[it.j];
                 const int I = it.I, J = it.J;
                 const bool same = it.same;
-                const int nkb = jb.kp / kTimeBlock;
+                const int nkb = jb.kp / C::kStageT;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!ptx::mbar_wait_bounded(bar_empty + 8 * s, ph ^ 1u, abort_flag, prm.wait_limit_ns)) {
                         record_error(prm.status, abort_flag, kDevTimeoutEmpty, kb);
@@ -492,9 +549,9 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                         const uint32_t st = ptx::smem_u32(rawring + s * prm.raw_stage_bytes);
                         // one box covers cpi adjacent channels (cpi x 64 inputs per sample row)
                         ptx::mbar_expect_tx(fb, (same ? (uint32_t)jb.cpi : 2u) * (uint32_t)C::kRawTileBytes);
-                        tma_load_4d(st, &jb.map, I * C::kMapX, it.c0, kb * kTimeBlock, (int)it.d, fb);
+                        tma_load_4d(st, &jb.map, I * C::kMapX, it.c0, kb * C::kStageT, (int)it.d, fb);
                         if (!same)
-                            tma_load_4d(st + C::kRawTileBytes, &jb.map, J * C::kMapX, it.c0, kb * kTimeBlock,
+                            tma_load_4d(st + C::kRawTileBytes, &jb.map, J * C::kMapX, it.c0, kb * C::kStageT,
                                         (int)it.d, fb);
                     } else {
                         const uint32_t st = ptx::smem_u32(ring + s * prm.op_stage_bytes);
@@ -561,7 +618,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 decode_item(prm, item, jc, it);
                 const TcJob& jb = prm.jobs[it.j];
                 const bool same = it.same;
-                const int nkb = jb.kp / kTimeBlock;
+                const int nkb = jb.kp / C::kStageT;
                 for (int kb0 = 0; ok && kb0 < nkb; kb0 += jb.chunk_kb) {
                     const int kb1 = min(nkb, kb0 + jb.chunk_kb);
                     if (!ptx::mbar_wait_bounded(bar_acc_empty + 8 * abuf, aph ^ 1u, abort_flag, prm.wait_limit_ns)) {
@@ -606,15 +663,15 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 const uint32_t acc = (k > 0) | acc0;
-                                ptx::mma_f16_lo(dset, a0 + 2u * k, a0 + 2u * k, desc_hi, idesc, acc);
-                                ptx::mma_f16_lo(dset + 128u, a0 + 1024u + 2u * k, a0 + 1024u + 2u * k, desc_hi, idesc,
-                                                acc);
+                                mma_op<C::kF8>(dset, a0 + 2u * k, a0 + 2u * k, desc_hi, idesc, acc);
+                                mma_op<C::kF8>(dset + 128u, a0 + 1024u + 2u * k, a0 + 1024u + 2u * k, desc_hi, idesc,
+                                               acc);
                             }
                         } else {
                             const uint32_t b0 = same ? a0 : a0 + boff16;
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
-                                ptx::mma_f16_lo(dset, a0 + 2u * k, b0 + 2u * k, desc_hi, idesc, (k > 0) | acc0);
+                                mma_op<C::kF8>(dset, a0 + 2u * k, b0 + 2u * k, desc_hi, idesc, (k > 0) | acc0);
                         }
                         any = true;
                         ptx::mma_commit(bar_op_empty + 8 * s);
@@ -659,7 +716,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             const int n_in = jb.n_inputs;
             const int64_t P = (int64_t)n_in * (n_in + 1) / 2;
             const int I = it.I, J = it.J;
-            const int nkb = jb.kp / kTimeBlock;
+            const int nkb = jb.kp / C::kStageT;
             const int i = I * kBlockInputs + i_loc;
             const bool row_ok = i < n_in;
             // baseline b(i, j) = row_off + j within one channel's [P] block
@@ -922,7 +979,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
             decode_item(prm, item, jc, it);
             const int cpi = prm.jobs[it.j].cpi;
             const bool same = it.same;
-            const int nkb = prm.jobs[it.j].kp / kTimeBlock;
+            const int nkb = prm.jobs[it.j].kp / C::kStageT;
             // The stage holds n_tl packed tiles: cpi channels side by side in each sample row
             // (diagonal items, row pitch cpi x kRow), or blocks I and J (off-diagonal items,
             // pitch kRow).  Each tile splits into warp-sized slices (8 for 8-bit, 4 for 4-bit);
@@ -946,6 +1003,20 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     const uint32_t raw_tile = ptx::smem_u32(rawring + rs * prm.raw_stage_bytes);
                     for (int sl = cwarp; sl < kTimeBlock / 8; sl += C::kConvWarps)
                         convert_slice_f32(raw_tile, dst, sl, lane);
+                } else if constexpr (C::kF8) {
+                    // e4m3 operands: a slice is 32 samples of one tile, lanes 0..15 taking
+                    // samples 16c .. 16c + 15 and lanes 16..31 the next 16 (c = 2 part + l / 16)
+                    const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
+                    for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
+                        const int tl = sl / kSlices, part = sl % kSlices;
+                        const int c = 2 * part + (lane >> 4);
+                        const uint32_t src = (same ? raw + tl * kRow : raw + tl * C::kRawTileBytes) +
+                                             (uint32_t)c * 16u * pitch;
+                        uint32_t w[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) w[e] = ld_shared_u32(src + (uint32_t)e * pitch);
+                        convert_words4_f8(w, dst + (same ? tl * kTileBytes : tl * prm.b_offset), c, cl);
+                    }
                 } else {
                 const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
                 // all loads of the warp's slices (slices cwarp and cwarp + 8) are issued before
@@ -1035,13 +1106,13 @@ bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CU
 // x 64 samples.
 // Out-of-range inputs (ragged last block) and samples (ragged last block) read as zero.
 bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, int n_time, int n_dumps, int bps,
-                  int box_chans) {
+                  int box_chans, int box_t) {
     auto enc = get_encode();
     if (!enc) return false;
     const cuuint64_t row = (cuuint64_t)n_inputs * bps;
     cuuint64_t dims[4] = {row, (cuuint64_t)n_chan, (cuuint64_t)n_time, (cuuint64_t)n_dumps};
     cuuint64_t strides[3] = {row, row * n_chan, row * n_chan * n_time};
-    cuuint32_t box[4] = {(cuuint32_t)(kBlockInputs * bps), (cuuint32_t)box_chans, (cuuint32_t)kTimeBlock, 1};
+    cuuint32_t box[4] = {(cuuint32_t)(kBlockInputs * bps), (cuuint32_t)box_chans, (cuuint32_t)box_t, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1089,18 +1160,20 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         jb.n_inputs = sp.n_inputs;
         jb.n_chan = sp.n_chan;
         jb.nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
-        jb.kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+        jb.kp = (sp.n_time + C::kStageT - 1) / C::kStageT * C::kStageT;   // whole stages (zeros past n_time)
         jb.n_tiles = jb.tw == 2 ? wide_items(jb.nb) : jb.nb * (jb.nb + 1) / 2;
         jb.cpi = sp.cpi;
         jb.n_groups = (sp.n_chan + jb.cpi - 1) / jb.cpi;
         // samples per exact chunk: 8-bit 1024 (|sum| <= 1024 * 2^14 = 2^24), 4-bit 131072, float: all
-        jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock) : (sp.sample_bits == 4 ? 2048 : 16);
+        // (in stages: 64 samples each, 128 for e4m3 operands)
+        jb.chunk_kb = C::kSplit ? (jb.kp / kTimeBlock)
+                                : (sp.sample_bits == 4 ? 131072 / C::kStageT : 1024 / C::kStageT);
         // |D| <= chunk samples x max |x_a x_b|: 4-bit 2^17 x 2^6 = 2^23, 8-bit 512 x 2^14 = 2^23
         jb.f32_combine = !C::kSplit && (sp.sample_bits == 4 || jb.kp <= 512) ? 1 : 0;
         jb.out_mode = sp.out_mode;
         jb.phasor = static_cast<const float2*>(sp.phasor);
         jb.inv_n = sp.inv_n;
-        if (jb.out_mode && (accumulate || jb.kp > jb.chunk_kb * kTimeBlock)) {   // one exact chunk per dump
+        if (jb.out_mode && (accumulate || jb.kp > jb.chunk_kb * C::kStageT)) {   // one exact chunk per dump
             delete prm;
             return cudaErrorInvalidValue;
         }
@@ -1164,9 +1237,9 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->bar_offset = prm->staging_offset + stage_space;
     const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
     auto kern = xeng_tc_kernel<MODE, MAXJ, false>;
-    if constexpr (C::kRaw && !C::kFloat && MAXJ == 1) {
+    if constexpr (C::kRaw && !C::kFloat && !C::kF8 && MAXJ == 1) {
         if (any_dump) kern = xeng_tc_kernel<MODE, MAXJ, true>;
-    } else if (any_dump) {   // dump mode is built for single-job packed-sample launches only
+    } else if (any_dump) {   // dump mode is built for single-job fp16-operand packed-sample launches only
         delete prm;
         return cudaErrorInvalidValue;
     }
@@ -1213,7 +1286,7 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
 
 bool tc_use_planes(const Plan& p) {
     if (!tc_raw_supported(p)) return true;
-    if (p.tc_operands == 1) return false;
+    if (p.tc_operands == 1 || p.tc_operands == 3) return false;
     if (p.tc_operands == 2) return true;
     return p.nb >= kPlaneMinBlocks;
 }
@@ -1235,9 +1308,10 @@ int tc_default_cpi(int n_inputs, int64_t channels, int n_sm) {
     return channels >= 2 * (int64_t)n_sm ? 2 : 1;
 }
 
-bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp) {
+bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp, bool f8) {
     const int bps = sp.sample_bits == 8 ? 2 : 1;
-    return make_raw_map(map, sp.data, sp.n_inputs, sp.n_chan, sp.n_time, sp.n_dumps, bps, sp.cpi);
+    return make_raw_map(map, sp.data, sp.n_inputs, sp.n_chan, sp.n_time, sp.n_dumps, bps, sp.cpi,
+                        f8 ? Cfg<kRaw4F8>::kStageT : kTimeBlock);
 }
 
 cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
@@ -1248,6 +1322,10 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
         if (specs[j].sample_bits != bits || !tc_raw_supported(specs[j].n_inputs, bits) ||
             (specs[j].cpi != 1 && specs[j].cpi != 2) || (specs[j].cpi == 2 && specs[j].n_inputs > kBlockInputs))
             return cudaErrorInvalidValue;
+    if (tune.f8_operands) {   // e4m3 operands: 4-bit samples, single-job launches (maps with 128-sample boxes)
+        if (bits != 4 || n_jobs != 1) return cudaErrorInvalidValue;
+        return launch_jobs<kRaw4F8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+    }
     if (n_jobs == 1) {
         if (bits == 8) return launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
         return launch_jobs<kRaw4, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
@@ -1293,6 +1371,11 @@ cudaError_t launch_raw_impl(const Plan& p, const void* d_packed, int n_dumps, vo
     if (!tc_raw_supported(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u)) return cudaErrorInvalidValue;
     TcTuning plan_tune;
     plan_tune.op_stages = p.tc_op_stages;
+    // 4-bit samples take e4m3 operands unless the plan asks for fp16 (CORR_OPERANDS_PACKED):
+    // the same bits, half the operand bytes and MMAs per sample (the fused dump keeps fp16)
+    const bool f8 = p.sample_bits == 4 && (p.tc_operands == 0 || p.tc_operands == 3) && out_mode == 0;
+    TcTuning run_tune = tune ? *tune : plan_tune;
+    run_tune.f8_operands = f8 ? 1 : 0;
     const int cpi = tc_default_cpi(p.n_inputs, (int64_t)n_dumps * p.n_chan, p.n_sm);
     // one launch covers fewer than 2^31 work items (the kernel decodes 32-bit item indices)
     const int64_t items_per_dump = (int64_t)((p.n_chan + cpi - 1) / cpi) * (p.nb * (p.nb + 1) / 2);
@@ -1309,9 +1392,8 @@ cudaError_t launch_raw_impl(const Plan& p, const void* d_packed, int n_dumps, vo
         sp.phasor = phasor;
         sp.inv_n = inv_n;
         CUtensorMap m;
-        if (!tc_make_raw_map(&m, sp)) return cudaErrorInvalidValue;
-        const cudaError_t e =
-            launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, tune ? *tune : plan_tune, s);
+        if (!tc_make_raw_map(&m, sp, f8)) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_xeng_tc_raw_jobs(&sp, &m, 1, accumulate, p.d_status, p.n_sm, run_tune, s);
         if (e != cudaSuccess) return e;
         d0 += nd;
     }

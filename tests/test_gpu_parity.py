@@ -101,6 +101,37 @@ def test_operand_feeds_and_item_shapes_bit_exact(feed, n, c, t, bits):
     assert np.array_equal(v, 2 * ref)
 
 
+# 4-bit samples through e4m3 operands (kind::f8f6f4, 128 samples per stage): ragged tails on
+# both sides of a stage, single-block arrays with one channel or channel pairs per item,
+# multi-block arrays with ragged last blocks, several dumps and accumulate
+F8_CASES = [(16, 3, 64), (32, 2, 1000), (64, 2, 127), (64, 2, 128), (64, 2, 129), (64, 1, 1),
+            (64, 320, 100), (32, 331, 300), (96, 1, 77), (128, 2, 256), (192, 1, 65), (48, 2, 300),
+            (256, 2, 64), (448, 1, 200), (1008, 1, 130)]
+
+
+@pytest.mark.parametrize("n,c,t", F8_CASES)
+def test_e4m3_operands_4bit_bit_exact(n, c, t):
+    p = np.concatenate([int_case(9400 + n + c + t + k, n, c, t, 4) for k in range(2)])
+    ref = np.stack([oracle.xcorr_int(p[k * t:(k + 1) * t], n, c, t, 4) for k in range(2)])
+    v = run_engine(p, n, c, t, 4, TC, n_dumps=2, operands=(3, 0))
+    assert np.array_equal(v, ref)
+    v = run_engine(p, n, c, t, 4, TC, n_dumps=2, accumulate=True, vis_init=ref, operands=(3, 0))
+    assert np.array_equal(v, 2 * ref)
+
+
+@pytest.mark.parametrize("t", [128, 131072, 131072 + 128, 131072 + 1])
+def test_e4m3_operands_extremes_and_chunk_flush(t):
+    # -8 - 8j everywhere but one -8 + 7j input: every product at its largest magnitude, odd
+    # imaginary sums, and partial sums at 2^23 per exact chunk of 131072 samples
+    n = 32
+    re = np.full((t, 1, n), -8, np.int16)
+    im = np.full((t, 1, n), -8, np.int16)
+    im[:, 0, 3] = 7
+    p = synth.pack(re, im, 4)
+    v = run_engine(p, n, 1, t, 4, TC, operands=(3, 0))[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, 1, t, 4))
+
+
 @pytest.mark.parametrize("n", [64, 192])
 def test_fused_dumps_and_accumulate(n):
     c, t, bits, d = 3, 200, 8, 3
@@ -338,5 +369,10 @@ def test_invalid_arguments_rejected():
         plan.set_operands(corr.OPERANDS_PACKED, 0)
     assert e.value.status == corr.EUNSUPPORTED
     with pytest.raises(corr.CorrError):
-        plan.set_operands(3, 0)
+        plan.set_operands(4, 0)
+    plan.close()
+    plan = corr.Plan(64, 1, 16, 8)                 # e4m3 cannot hold 8-bit samples
+    with pytest.raises(corr.CorrError) as e:
+        plan.set_operands(corr.OPERANDS_PACKED_F8, 0)
+    assert e.value.status == corr.EUNSUPPORTED
     plan.close()
