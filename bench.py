@@ -693,7 +693,8 @@ def run_shape(args):
     stream = torch.cuda.current_stream(dev)
     plan = corr.Plan(n, c, t, bits)
     engine = {"tc": corr.ENGINE_TC, "fp32": corr.ENGINE_FP32}[args.engine]
-    plan.set_operands({"auto": corr.OPERANDS_AUTO, "packed": corr.OPERANDS_PACKED, "planes": corr.OPERANDS_PLANES}[args.feed],
+    plan.set_operands({"auto": corr.OPERANDS_AUTO, "packed": corr.OPERANDS_PACKED, "planes": corr.OPERANDS_PLANES,
+                       "packed_f8": corr.OPERANDS_PACKED_F8}[args.feed],
                       {"auto": corr.ITEMS_AUTO, "tiles": corr.ITEMS_TILES, "wide": corr.ITEMS_WIDE}[args.items])
     if args.op_stages:
         plan.set_tuning(args.op_stages, 0)
@@ -913,7 +914,8 @@ def main():
                     choices=["stream", "mwa32t", "large", "batch", "serve", "fx", "dump", "float", "shape"])
     ap.add_argument("--shape", default="512,128,2048,8", help="shape workload: N,C,T,BITS")
     ap.add_argument("--engine", default="tc", choices=["tc", "fp32"], help="shape workload: X engine")
-    ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes"], help="shape workload: operand feed")
+    ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes", "packed_f8"],
+                    help="shape workload: operand feed (packed = fp16 operands; packed_f8 = e4m3, 4-bit samples)")
     ap.add_argument("--items", default="auto", choices=["auto", "tiles", "wide"], help="shape workload: item shape")
     ap.add_argument("--op-stages", type=int, default=0, help="shape workload: operand-ring depth (0: default)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)

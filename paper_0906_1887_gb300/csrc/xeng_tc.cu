@@ -264,6 +264,10 @@ struct ConvLane {
     uint32_t sel[4];
     uint32_t rowoff[4];
     uint32_t r7x16[4];
+    // 4-bit: the lane writes its two rows of an input in the order (re, im) or (im, re): the
+    // nibble shift of the first row's values and the byte offset of the second row from the first
+    uint32_t first_shift;
+    int32_t second_delta;
 };
 
 // 8-bit: lane l takes inputs 2l, 2l+1; byte lane k of a loaded word is re(2l), im(2l),
@@ -280,22 +284,29 @@ __device__ __forceinline__ ConvLane conv_lane8(int l) {
         c.rowoff[kk] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
         c.r7x16[kk] = (uint32_t)((row & 7) << 4);
     }
+    c.first_shift = 0;
+    c.second_delta = 0;
     return c;
 }
 
 // 4-bit: lane l takes inputs 4m .. 4m+3 (m = l & 15); at step kk input 4m + k with
-// k = (kk + m) & 3, rows 2(4m + k) (re) and 2(4m + k) + 1 (im).
+// k = (kk + m/2) & 3, and writes rows 2(4m + k) (re) and 2(4m + k) + 1 (im), the im row first
+// when m is odd.  A quarter-warp's first rows then have (row & 7) = 2k + (m & 1), eight distinct
+// values, and so do its second rows: each 16-byte store of the quarter-warp lands in its own
+// swizzle chunk, free of bank conflicts.
 __device__ __forceinline__ ConvLane conv_lane4(int l) {
     ConvLane c;
     const int m = l & 15;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        const int k = (kk + m) & 3;
-        const int row = 2 * (4 * m + k);
+        const int k = (kk + (m >> 1)) & 3;
+        const int row = 2 * (4 * m + k) + (m & 1);
         c.sel[kk] = lane_selector(k);
         c.rowoff[kk] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
         c.r7x16[kk] = (uint32_t)((row & 7) << 4);
     }
+    c.first_shift = (m & 1) ? 0u : 4u;           // re is the high nibble, im the low one
+    c.second_delta = (m & 1) ? -128 : 128;
     return c;
 }
 
@@ -316,29 +327,50 @@ __device__ __forceinline__ void convert_words8(const uint32_t (&w)[8], uint32_t 
 }
 
 // Packed 4-bit words (high nibble re, low nibble im): lane l holds w[e] = inputs 4m .. 4m+3
-// (m = l & 15) of sample 8q + e, q = 2s + (l >> 4) for slice s.
+// (m = l & 15) of the 8 samples of group q; writes the 16-byte chunk q of each of its 8 rows.
 __device__ __forceinline__ void convert_words4(const uint32_t (&w)[8], uint32_t dst, int q, const ConvLane& cl) {
     const __half2 bias = conv::bias4();
     const uint32_t flip = conv::kFlip4;   // exponent bytes 0x64, sign bit of each 4-bit sample flipped
-    uint32_t hi[8], lo[8];
+    uint32_t a[8], b[8];                  // nibbles of the first and the second row, one per byte
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
-        lo[e] = w[e] & 0x0F0F0F0Fu;         // im nibble per byte
+        a[e] = (w[e] >> cl.first_shift) & 0x0F0F0F0Fu;
+        b[e] = (w[e] >> (4u - cl.first_shift)) & 0x0F0F0F0Fu;
     }
     const uint32_t q16 = (uint32_t)q << 4;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const uint32_t sel = cl.sel[kk];
         const uint32_t at = dst + cl.rowoff[kk];
-        st_shared_v4(at + (q16 ^ cl.r7x16[kk]), pair_to_half2(hi[0], hi[1], sel, flip, bias),
-                     pair_to_half2(hi[2], hi[3], sel, flip, bias), pair_to_half2(hi[4], hi[5], sel, flip, bias),
-                     pair_to_half2(hi[6], hi[7], sel, flip, bias));
-        // the im row is the next row: +128 bytes, (row & 7) one higher
-        st_shared_v4(at + 128u + (q16 ^ (cl.r7x16[kk] + 16u)), pair_to_half2(lo[0], lo[1], sel, flip, bias),
-                     pair_to_half2(lo[2], lo[3], sel, flip, bias), pair_to_half2(lo[4], lo[5], sel, flip, bias),
-                     pair_to_half2(lo[6], lo[7], sel, flip, bias));
+        st_shared_v4(at + (q16 ^ cl.r7x16[kk]), pair_to_half2(a[0], a[1], sel, flip, bias),
+                     pair_to_half2(a[2], a[3], sel, flip, bias), pair_to_half2(a[4], a[5], sel, flip, bias),
+                     pair_to_half2(a[6], a[7], sel, flip, bias));
+        // the other row of the input: 128 bytes away, (row & 7) differing in its lowest bit
+        st_shared_v4(at + (uint32_t)cl.second_delta + (q16 ^ (cl.r7x16[kk] ^ 16u)),
+                     pair_to_half2(b[0], b[1], sel, flip, bias), pair_to_half2(b[2], b[3], sel, flip, bias),
+                     pair_to_half2(b[4], b[5], sel, flip, bias), pair_to_half2(b[6], b[7], sel, flip, bias));
     }
+}
+
+// The e4m3 converter's lane constants: input 4m + k at step kk with k = (kk + m) & 3, its re row
+// 2(4m + k) first and the im row after it.  Its stores are half as many as the fp16 ones and
+// conflict in pairs; the conflict-free order of conv_lane4 and its loads (a variable shift per
+// word, permuted row addresses) measured slower here (1.51-1.55 against 1.45 ms on a 4-bit
+// stream of 64 inputs x 768 channels x 50 dumps) though faster for the fp16 converter.
+__device__ __forceinline__ ConvLane conv_lane4_f8(int l) {
+    ConvLane c;
+    const int m = l & 15;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int k = (kk + m) & 3;
+        const int row = 2 * (4 * m + k);
+        c.sel[kk] = lane_selector(k);
+        c.rowoff[kk] = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
+        c.r7x16[kk] = (uint32_t)((row & 7) << 4);
+    }
+    c.first_shift = 4;
+    c.second_delta = 128;
+    return c;
 }
 
 // Four exact e4m3 bytes (samples in order) from two fp16 pairs whose values are integers in
@@ -360,11 +392,11 @@ __device__ __forceinline__ uint32_t e4m3x4(uint32_t h01, uint32_t h23) {
 __device__ __forceinline__ void convert_words4_f8(const uint32_t (&w)[16], uint32_t dst, int c, const ConvLane& cl) {
     const __half2 bias = conv::bias4();
     const uint32_t flip = conv::kFlip4;
-    uint32_t hi[16], lo[16];
+    uint32_t a[16], b[16];                // re and im nibbles, one per byte (conv_lane4_f8)
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-        hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;  // re nibble per byte
-        lo[e] = w[e] & 0x0F0F0F0Fu;         // im nibble per byte
+        a[e] = (w[e] >> 4) & 0x0F0F0F0Fu;
+        b[e] = w[e] & 0x0F0F0F0Fu;
     }
     const uint32_t c16 = (uint32_t)c << 4;
 #pragma unroll
@@ -374,13 +406,13 @@ __device__ __forceinline__ void convert_words4_f8(const uint32_t (&w)[16], uint3
         uint32_t r[4], m[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
-            r[o] = e4m3x4(pair_to_half2(hi[4 * o], hi[4 * o + 1], sel, flip, bias),
-                          pair_to_half2(hi[4 * o + 2], hi[4 * o + 3], sel, flip, bias));
-            m[o] = e4m3x4(pair_to_half2(lo[4 * o], lo[4 * o + 1], sel, flip, bias),
-                          pair_to_half2(lo[4 * o + 2], lo[4 * o + 3], sel, flip, bias));
+            r[o] = e4m3x4(pair_to_half2(a[4 * o], a[4 * o + 1], sel, flip, bias),
+                          pair_to_half2(a[4 * o + 2], a[4 * o + 3], sel, flip, bias));
+            m[o] = e4m3x4(pair_to_half2(b[4 * o], b[4 * o + 1], sel, flip, bias),
+                          pair_to_half2(b[4 * o + 2], b[4 * o + 3], sel, flip, bias));
         }
         st_shared_v4(at + (c16 ^ cl.r7x16[kk]), r[0], r[1], r[2], r[3]);
-        st_shared_v4(at + 128u + (c16 ^ (cl.r7x16[kk] + 16u)), m[0], m[1], m[2], m[3]);
+        st_shared_v4(at + 128u + (c16 ^ (cl.r7x16[kk] + 16u)), m[0], m[1], m[2], m[3]);   // the im row
     }
 }
 
@@ -967,7 +999,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
     } else if constexpr (C::kRaw) {
         // ---------------- converters (the last kConvWarps warps) ----------------
         const int cwarp = warp - 2 - C::kEpiWarps;   // 0 .. kConvWarps - 1
-        const ConvLane cl = C::kBits8 ? conv_lane8(lane) : conv_lane4(lane);
+        const ConvLane cl = C::kBits8 ? conv_lane8(lane) : (C::kF8 ? conv_lane4_f8(lane) : conv_lane4(lane));
         constexpr uint32_t kRow = kBlockInputs * C::kBps;   // packed bytes of 64 inputs
         const uint32_t lane_byte = C::kBits8 ? 4u * lane : 4u * (lane & 15);
         int rs = 0, os = 0;
@@ -1004,12 +1036,14 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                     for (int sl = cwarp; sl < kTimeBlock / 8; sl += C::kConvWarps)
                         convert_slice_f32(raw_tile, dst, sl, lane);
                 } else if constexpr (C::kF8) {
-                    // e4m3 operands: a slice is 32 samples of one tile, lanes 0..15 taking
-                    // samples 16c .. 16c + 15 and lanes 16..31 the next 16 (c = 2 part + l / 16)
+                    // e4m3 operands, a slice per warp: 32 samples of one tile, lanes 0..15 chunk
+                    // c = 2 part (samples 16c .. 16c + 15) and 16..31 chunk c + 1.  (The fp16
+                    // converter's conflict-free orders below measured slower here: this converter
+                    // is bound by its instruction count, not by shared-memory conflicts.)
                     const uint32_t pitch = pair_pitch ? 2 * kRow : kRow;
                     for (int sl = cwarp; sl < n_tl * kSlices; sl += C::kConvWarps) {
-                        const int tl = sl / kSlices, part = sl % kSlices;
-                        const int c = 2 * part + (lane >> 4);
+                        const int tl = sl / kSlices;
+                        const int c = 2 * (sl % kSlices) + (lane >> 4);
                         const uint32_t src = (same ? raw + tl * kRow : raw + tl * C::kRawTileBytes) +
                                              (uint32_t)c * 16u * pitch;
                         uint32_t w[16];
@@ -1023,26 +1057,32 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                 // the first conversion, so their shared-memory latencies overlap
                 constexpr int kSlots = (2 * kSlices + C::kConvWarps - 1) / C::kConvWarps;
                 uint32_t w[kSlots][8];
+                // 4-bit slices (8 samples of 64 inputs per half-warp) split like the e4m3 ones:
+                // by channel with channel pairs, else by sample group with the upper half-warp
+                // reading rows in the order e ^ 1 (adjacent samples swapped alike in every odd
+                // group of every operand row: a permutation of the sample axis shared by A and B)
+                const bool split_ch = !C::kBits8 && pair_pitch;
+                const int eflip = (!C::kBits8 && !pair_pitch) ? (lane >> 4) : 0;
 #pragma unroll
                 for (int v = 0; v < kSlots; ++v) {
                     const int sl = cwarp + C::kConvWarps * v;
                     if (sl < n_tl * kSlices) {
-                        const int tl = sl / kSlices, part = sl % kSlices;
-                        const int q = C::kBits8 ? part : 2 * part + (lane >> 4);
+                        const int tl = split_ch ? (lane >> 4) : sl / kSlices, part = sl % kSlices;
+                        const int q = C::kBits8 ? part : (split_ch ? sl : 2 * part + (lane >> 4));
                         const uint32_t src = (same ? raw + tl * kRow : raw + tl * C::kRawTileBytes) +
                                              (uint32_t)q * 8u * pitch;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) w[v][e] = ld_shared_u32(src + (uint32_t)e * pitch);
+                        for (int e = 0; e < 8; ++e) w[v][e] = ld_shared_u32(src + (uint32_t)(e ^ eflip) * pitch);
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < kSlots; ++v) {
                     const int sl = cwarp + C::kConvWarps * v;
                     if (sl < n_tl * kSlices) {
-                        const int tl = sl / kSlices, part = sl % kSlices;
+                        const int tl = split_ch ? (lane >> 4) : sl / kSlices, part = sl % kSlices;
                         const uint32_t out = dst + (same ? tl * kTileBytes : tl * prm.b_offset);
                         if constexpr (C::kBits8) convert_words8(w[v], out, part, cl);
-                        else convert_words4(w[v], out, 2 * part + (lane >> 4), cl);
+                        else convert_words4(w[v], out, split_ch ? sl : 2 * part + (lane >> 4), cl);
                     }
                 }
                 }   // packed integers
