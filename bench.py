@@ -46,9 +46,9 @@ SIGMA, RHO, SEED = 16.0, 0.1, 2000
 CHANNEL_RATE_HZ = 1.28e6 / 128.0
 WORKLOAD = "stream64_8bit: 64 inputs x 768 channels x 1000 samples/dump x 200 dumps, 8-bit complex Gaussian sigma=16 rho=0.1"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per dump of the fused kernel on this
-# workload, from one ncu capture of an 8-dump launch of this build (786.63 MB read + 176.83 MB
+# workload, from one ncu capture of an 8-dump launch of this build (786.62 MB read + 177.14 MB
 # written), scaled by dumps; set to None whenever the kernel changes until it is captured again.
-DRAM_BYTES_PER_DUMP = (786626560 + 176831232) / 8
+DRAM_BYTES_PER_DUMP = (786617856 + 177139200) / 8
 
 
 def rank_max(x: float, dist, device) -> float:
