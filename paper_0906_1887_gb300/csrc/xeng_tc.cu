@@ -17,7 +17,9 @@
 // (|p| <= 2^14) are exact, and each D element sums one product per sample, so a chunk of
 // at most 1024 samples keeps every partial sum at or below 2^24 in magnitude, where fp32
 // holds every integer.  Each D element is converted to int64 before the re/im sums, and
-// chunks are flushed to int64; results are bit-exact.
+// chunks are flushed to int64; results are bit-exact.  4-bit samples (-8..7) are exact in
+// fp8 e4m3 as well: their packed feed converts them to e4m3 operand bytes and issues
+// kind::f8f6f4 MMAs (K = 32), with the same fp32 accumulation and chunking.
 //
 // Float samples (BF16x3): x = h + l with bf16 h, l; MMAs for h h^T, h l^T and l h^T with
 // fp32 accumulation.
