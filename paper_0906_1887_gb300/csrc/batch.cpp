@@ -143,12 +143,14 @@ bool build_groups(corr_batch_s* b, const TuneChoice& ch) {
                     return job_cost_per_item(b->jobs[x], cpi_of(b->jobs[x])) >
                            job_cost_per_item(b->jobs[y], cpi_of(b->jobs[y]));
                 });
+            // packed 4-bit samples take e4m3 operands (128-sample boxes), as single-job calls do
+            const bool f8 = bits == 4 && !planes;
             for (int k : g.job_index) {
                 const corr_job& j = b->jobs[k];
                 const void* data = planes ? static_cast<const void*>(b->d_planes + b->plane_off[k]) : j.packed;
                 TcJobSpec sp{j.n_inputs, j.n_chan, j.n_time, 1, j.sample_bits, data, j.vis, cpi_of(j)};
                 CUtensorMap m, mw{};
-                if (!(planes ? tc_make_plane_map(&m, sp) : tc_make_raw_map(&m, sp))) return false;
+                if (!(planes ? tc_make_plane_map(&m, sp) : tc_make_raw_map(&m, sp, f8))) return false;
                 const int nb = blocks_of(j);
                 if (planes && ch.wide && nb >= 2 && tc_make_plane_map_wide(&mw, sp)) sp.tw = 2;
                 g.specs.push_back(sp);
@@ -158,6 +160,7 @@ bool build_groups(corr_batch_s* b, const TuneChoice& ch) {
                 b->items += (int64_t)((j.n_chan + sp.cpi - 1) / sp.cpi) * per_chan;
             }
             g.tune.op_stages = ch.op_stages;
+            g.tune.f8_operands = f8 ? 1 : 0;
             b->groups.push_back(std::move(g));
         }
     }

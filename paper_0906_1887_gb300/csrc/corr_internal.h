@@ -104,7 +104,7 @@ struct TcTuning {
     int smem_reserve = 0;         // plane feed: shared memory per SM left free for a concurrent kernel
     uint64_t wait_limit_ns = 0;   // 0: the default bound (2 s)
     int64_t stall_item = -1;      // self-test of the bounded waits (-1: off)
-    int f8_operands = 0;          // packed 4-bit samples: e4m3 operands (kind::f8f6f4), single-job launches
+    int f8_operands = 0;          // packed 4-bit samples: e4m3 operands (kind::f8f6f4; maps with 128-sample boxes)
 };
 int tc_default_cpi(int n_inputs, int64_t channels, int n_sm);   // channels = dumps x n_chan of the launch
 // BF16x3 on float samples with the hi/lo split done in the tensor-core kernel (single-block arrays)

@@ -1364,9 +1364,11 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
         if (specs[j].sample_bits != bits || !tc_raw_supported(specs[j].n_inputs, bits) ||
             (specs[j].cpi != 1 && specs[j].cpi != 2) || (specs[j].cpi == 2 && specs[j].n_inputs > kBlockInputs))
             return cudaErrorInvalidValue;
-    if (tune.f8_operands) {   // e4m3 operands: 4-bit samples, single-job launches (maps with 128-sample boxes)
-        if (bits != 4 || n_jobs != 1) return cudaErrorInvalidValue;
-        return launch_jobs<kRaw4F8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+    if (tune.f8_operands) {   // e4m3 operands: 4-bit samples (maps with 128-sample boxes)
+        if (bits != 4) return cudaErrorInvalidValue;
+        if (n_jobs == 1) return launch_jobs<kRaw4F8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
+        if (n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+        return launch_jobs<kRaw4F8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
     }
     if (n_jobs == 1) {
         if (bits == 8) return launch_jobs<kRaw8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s);
