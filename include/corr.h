@@ -366,7 +366,8 @@ enum {
                                    Kp x 2 bytes each); jobs of at least plane_min_nb 64-input blocks
                                    are unpacked into them and the tensor-core kernel reads the planes
                                    instead of converting packed samples itself (tuned, or 4 blocks
-                                   when not tuned).  Results are identical either way. */
+                                   when not tuned; packed 4-bit samples are converted to e4m3
+                                   operands, 8-bit ones to fp16).  Results are identical either way. */
 };
 
 typedef struct {
