@@ -269,12 +269,26 @@ def run_mwa32t(args):
     steps = max(args.steps, 20)
     tc = lambda: plan.run(x, vis, None, engine=corr.ENGINE_TC, stream=stream)   # noqa: E731
     f32 = lambda: plan.run(x, vis, ws32, engine=corr.ENGINE_FP32, stream=stream)   # noqa: E731
+    # the same dump with fp16 operands (the plan's default feeds 4-bit samples as e4m3 operands,
+    # kind::f8f6f4): identical results, twice the operand bytes and MMAs per sample
+    plan16 = corr.Plan(n, c, t, 4)
+    plan16.set_operands(corr.OPERANDS_PACKED, 0)
+    vis16 = plan16.empty_vis(1, dev)
+    f16 = lambda: plan16.run(x, vis16, None, engine=corr.ENGINE_TC, stream=stream)   # noqa: E731
     for _ in range(args.warmup):
         tc()
+        f16()
         f32()
     torch.cuda.synchronize()
-    assert plan.check_device() == 0
-    ms = _event_ms(tc, steps, stream, flush)
+    assert plan.check_device() == 0 and plan16.check_device() == 0
+    f16()
+    tc()
+    torch.cuda.synchronize()
+    assert torch.equal(vis, vis16)
+    # a 20 us launch: two interleaved rounds of `steps` launches per operand type, the better
+    # round's mean kept for each
+    rounds = [(_event_ms(tc, steps, stream, flush), _event_ms(f16, steps, stream, flush)) for _ in range(2)]
+    ms, ms16 = min(r[0] for r in rounds), min(r[1] for r in rounds)
     ms32 = _event_ms(f32, steps, stream, flush)
     hbm, _, src = _peaks()
     by = t * c * n + c * P * 16
@@ -287,19 +301,8 @@ def run_mwa32t(args):
                         "note": "one 4.3 MB dump is launch- and latency-bound, far from either roofline"},
            "fp32_path": {"kernel_ms": ms32, "value": cm / (ms32 / 1e3) / 1e12, "speedup_tc_over_fp32": ms32 / ms},
            "l2": "256 MB written between timed steps"}
-    # the plan's default feeds 4-bit samples as e4m3 operands (kind::f8f6f4); the same dump with
-    # fp16 operands: identical results, twice the operand bytes and MMAs per sample
-    plan16 = corr.Plan(n, c, t, 4)
-    plan16.set_operands(corr.OPERANDS_PACKED, 0)
-    vis16 = plan16.empty_vis(1, dev)
-    f16 = lambda: plan16.run(x, vis16, None, engine=corr.ENGINE_TC, stream=stream)   # noqa: E731
-    for _ in range(args.warmup):
-        f16()
-    tc()
-    torch.cuda.synchronize()
-    assert plan16.check_device() == 0 and torch.equal(vis, vis16)
-    ms16 = _event_ms(f16, steps, stream, flush)
     res["operands"] = "e4m3 (tcgen05 kind::f8f6f4)"
+    res["timing"] = f"best of 2 interleaved rounds of {steps} launches per operand type"
     res["fp16_operands"] = {"kernel_ms": ms16, "value": cm / (ms16 / 1e3) / 1e12, "same_bits": True}
     plan16.close()
     plan.close()
