@@ -28,6 +28,12 @@ size_t planes_bytes(const Plan& p, int n_dumps) {
     return (size_t)n_dumps * (size_t)p.n_chan * (size_t)p.nb * kBlockRows * (size_t)p.kp * plane_elem_bytes(p);
 }
 
+size_t tc_workspace_planes_bytes(const Plan& p, int n_dumps) {
+    if (tc_planes_e4m3(p))
+        return (size_t)n_dumps * (size_t)p.n_chan * (size_t)p.nb * kBlockRows * (size_t)tc_kp_e4m3(p);
+    return planes_bytes(p, n_dumps);
+}
+
 static size_t packed_bytes_one(const Plan& p) {
     size_t per = p.sample_bits == 4 ? 1 : (p.sample_bits == 8 ? 2 : 8);
     return (size_t)p.n_time * (size_t)p.n_chan * (size_t)p.n_inputs * per;
@@ -150,7 +156,7 @@ corr_status corr_workspace_size(corr_plan plan, int engine, int n_dumps, size_t*
         case CORR_ENGINE_TC:
             // fp16 planes when the kernel reads planes (required where TMA cannot address the
             // packed rows; optional otherwise: without a workspace it converts packed samples)
-            *bytes = tc_use_planes(*p) ? planes_bytes(*p, n_dumps) : 0;
+            *bytes = tc_use_planes(*p) ? tc_workspace_planes_bytes(*p, n_dumps) : 0;
             return CORR_OK;
         case CORR_ENGINE_FP32:
             *bytes = 0;   // reads the packed samples directly
@@ -211,8 +217,7 @@ corr_status corr_xengine_run_batch(corr_plan plan, const void* d_packed, int n_d
         if (!d_workspace || !tc_use_planes(*p)) {
             e = launch_xeng_tc_raw(*p, d_packed, n_dumps, d_vis, accumulate, s);
         } else {
-            e = launch_unpack_fp16(*p, d_packed, n_dumps, d_workspace, s);
-            if (e == cudaSuccess) e = launch_xeng_tc(*p, d_workspace, nullptr, n_dumps, d_vis, accumulate, s);
+            e = launch_tc_plane_path(*p, d_packed, n_dumps, d_workspace, d_vis, accumulate, s);
         }
     } else if (engine == CORR_ENGINE_FP32) {
         e = launch_xeng_fp32_packed(*p, d_packed, n_dumps, d_vis, accumulate, s);

@@ -83,6 +83,18 @@ bool tc_raw_supported(const Plan& p);
 constexpr int kPlaneMinBlocks = 4;
 bool tc_use_planes(const Plan& p);
 bool tc_raw_supported(int n_inputs, int sample_bits);
+// The workspace's planes: e4m3 bytes for 4-bit samples of TMA-addressable rows (rows of
+// tc_kp_e4m3 = n_time rounded up to 128 bytes, read by kind::f8f6f4 MMAs), fp16 otherwise.  The
+// public planes calls (corr_unpack, corr_xengine_run_planes) keep fp16 planes.
+bool tc_planes_e4m3(const Plan& p);
+int tc_kp_e4m3(const Plan& p);
+size_t tc_workspace_planes_bytes(const Plan& p, int n_dumps);
+cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s);
+cudaError_t launch_xeng_tc_e4m3_planes(const Plan& p, const void* d_planes, int n_dumps, void* d_vis, int accumulate,
+                                       cudaStream_t s);
+// unpack into the workspace's planes, then the plane-fed tensor-core X stage
+cudaError_t launch_tc_plane_path(const Plan& p, const void* d_packed, int n_dumps, void* d_ws, void* d_vis,
+                                 int accumulate, cudaStream_t s);
 struct TcTuning;
 cudaError_t launch_xeng_tc_raw(const Plan& p, const void* d_packed, int n_dumps, void* d_vis, int accumulate,
                                cudaStream_t s, const TcTuning* tune = nullptr);

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cstdint>
 
 namespace corr {
@@ -35,6 +36,19 @@ __device__ __forceinline__ __half2 bias4() {
     return __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));   // 1032
 }
 constexpr uint32_t kFlip4 = 0x64086408u;
+
+// Four exact e4m3 bytes (samples in order) from two fp16 pairs whose values are integers in
+// -8..7, which e4m3 (3 mantissa bits) holds exactly: the conversion cannot round.
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t h01, uint32_t h23) {
+    __half2_raw a, b;
+    a.x = (unsigned short)(h01 & 0xFFFFu);
+    a.y = (unsigned short)(h01 >> 16);
+    b.x = (unsigned short)(h23 & 0xFFFFu);
+    b.y = (unsigned short)(h23 >> 16);
+    const uint32_t lo = __nv_cvt_halfraw2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_halfraw2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
+    return (lo & 0xFFFFu) | (hi << 16);
+}
 
 }  // namespace conv
 }  // namespace corr

@@ -176,7 +176,7 @@ size_t footprint(const corr_job_desc& d, bool* raw) {
     // single-block arrays (split into bf16 hi/lo inside the kernel)
     *raw = d.sample_bits == 32 ? tc_rawf32_supported(p) : !tc_use_planes(p);
     size_t ws = 0;
-    if (!*raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : planes_bytes(p, 1);
+    if (!*raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : tc_workspace_planes_bytes(p, 1);
     return round_up(16) + round_up(packed_bytes(d)) + round_up(vis_bytes(d)) + round_up(ws);
 }
 
@@ -195,7 +195,7 @@ size_t stream_layout(StreamState& st, char* base) {
     const corr_job_desc d = shape_of(st.d);
     Plan p = plan_of(d, 0, 0);
     size_t ws = 0;
-    if (!st.raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : planes_bytes(p, 1);
+    if (!st.raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : tc_workspace_planes_bytes(p, 1);
     const bool avg = st.d.dump_mode == CORR_STREAM_DUMP_AVERAGED;
     st.slot_bytes = round_up(packed_bytes(d));
     size_t off = 0;
@@ -317,8 +317,7 @@ cudaError_t run_x(const Plan& p, const corr_job_desc& d, bool raw, const char* d
         cudaError_t e = launch_unpack_bf16x2(p, d_packed, 1, d_ws, d_ws + half, s);
         return e == cudaSuccess ? launch_xeng_tc(p, d_ws, d_ws + half, 1, d_vis, accumulate, s) : e;
     }
-    cudaError_t e = launch_unpack_fp16(p, d_packed, 1, d_ws, s);
-    return e == cudaSuccess ? launch_xeng_tc(p, d_ws, nullptr, 1, d_vis, accumulate, s) : e;
+    return launch_tc_plane_path(p, d_packed, 1, d_ws, d_vis, accumulate, s);
 }
 
 // Issue one admitted job on its stream (called with the lock released).

@@ -125,7 +125,7 @@ extern "C" corr_status corr_xengine_run_static(const void* d_packed, int n_input
     p.nb = nb;
     p.kp = kp;
     p.n_baselines = n_baselines(n_inputs);
-    if (planes_bytes(p, 1) > kStaticScratchBytes)   // cannot happen after the check above
+    if (tc_workspace_planes_bytes(p, 1) > kStaticScratchBytes)   // cannot happen after the check above
         return set_error(CORR_EINVAL, "corr_xengine_run_static: plane size check failed");
     cudaError_t e = cudaGetDevice(&p.device);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -137,8 +137,7 @@ extern "C" corr_status corr_xengine_run_static(const void* d_packed, int n_input
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(p.d_status, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(status)");
-    e = launch_unpack_fp16(p, d_packed, 1, scratch, s);
-    if (e == cudaSuccess) e = launch_xeng_tc(p, scratch, nullptr, 1, d_vis, accumulate, s);
+    e = launch_tc_plane_path(p, d_packed, 1, scratch, d_vis, accumulate, s);
     if (e != cudaSuccess) return cuda_error(e, "X-stage launch");
     return CORR_OK;
 }

@@ -128,11 +128,14 @@ struct FastTile {
 };
 
 // kGroup: tiles whose loads a block issues together (1 for the full grid; 8 for a launch of one
-// block per SM beside a tensor-core launch, 64 KB in flight per block)
-template <int BITS, int kGroup>
+// block per SM beside a tensor-core launch, 64 KB in flight per block).  F8 (4-bit only): the
+// planes hold e4m3 bytes instead of fp16 (rows of kp bytes), for the e4m3 plane feed.
+template <int BITS, int kGroup, bool F8 = false>
 __global__ void __launch_bounds__(FastTile<BITS>::kThreads) unpack_fast_kernel(
     const unsigned char* __restrict__ packed, int n_inputs, int n_chan, int n_time, int nb_count, int kp,
-    int64_t n_tiles, __half* __restrict__ planes) {
+    int64_t n_tiles, void* __restrict__ planes_out) {
+    static_assert(!F8 || BITS == 4, "e4m3 planes hold 4-bit samples only");
+    __half* __restrict__ planes = static_cast<__half*>(planes_out);
     using F = FastTile<BITS>;
     __shared__ __align__(16) uint32_t tile[F::kTileBytes / 4];
     const int tid = threadIdx.x;
@@ -211,6 +214,32 @@ __global__ void __launch_bounds__(FastTile<BITS>::kThreads) unpack_fast_kernel(
                     o.w = conv::pair_to_half2(w[6], w[7], sel, conv::kFlip8, bias);
                     *reinterpret_cast<uint4*>(out + (int64_t)(4 * pw + k) * kp) = o;
                 }
+            } else if constexpr (F8) {
+                // as below, each row's 8 samples written as 8 e4m3 bytes (rows of kp bytes)
+                const __half2 bias = conv::bias4();
+                unsigned char* out8 = static_cast<unsigned char*>(planes_out) + row0 * kp +
+                                      (int64_t)tb * kTimeBlock + 8 * q;
+                uint32_t hi[8], lo[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    hi[e] = (w[e] >> 4) & 0x0F0F0F0Fu;
+                    lo[e] = w[e] & 0x0F0F0F0Fu;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t sel = conv::lane_selector(k);
+                    uint2 o;
+                    o.x = conv::e4m3x4(conv::pair_to_half2(hi[0], hi[1], sel, conv::kFlip4, bias),
+                                       conv::pair_to_half2(hi[2], hi[3], sel, conv::kFlip4, bias));
+                    o.y = conv::e4m3x4(conv::pair_to_half2(hi[4], hi[5], sel, conv::kFlip4, bias),
+                                       conv::pair_to_half2(hi[6], hi[7], sel, conv::kFlip4, bias));
+                    *reinterpret_cast<uint2*>(out8 + (int64_t)(8 * pw + 2 * k) * kp) = o;
+                    o.x = conv::e4m3x4(conv::pair_to_half2(lo[0], lo[1], sel, conv::kFlip4, bias),
+                                       conv::pair_to_half2(lo[2], lo[3], sel, conv::kFlip4, bias));
+                    o.y = conv::e4m3x4(conv::pair_to_half2(lo[4], lo[5], sel, conv::kFlip4, bias),
+                                       conv::pair_to_half2(lo[6], lo[7], sel, conv::kFlip4, bias));
+                    *reinterpret_cast<uint2*>(out8 + (int64_t)(8 * pw + 2 * k + 1) * kp) = o;
+                }
             } else {
                 // word pw = inputs 4pw .. 4pw + 3, high nibble re, low nibble im -> rows 8pw + 2k (+1)
                 const __half2 bias = conv::bias4();
@@ -262,6 +291,20 @@ cudaError_t launch_fast(const Plan& p, const void* d_packed, int n_dumps, void* 
     return cudaGetLastError();
 }
 
+// 4-bit samples into e4m3 planes with rows of kp8 bytes (n_time rounded up to 128 samples)
+cudaError_t launch_fast_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* planes, int kp8,
+                             cudaStream_t s) {
+    using F = FastTile<4>;
+    const int64_t n_tiles = (int64_t)n_dumps * p.n_chan * p.nb * (kp8 / kTimeBlock);
+    if (n_tiles < 1) return cudaSuccess;
+    const int64_t cap = (int64_t)p.n_sm * 16;
+    const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+    unpack_fast_kernel<4, 1, true><<<grid, F::kThreads, 0, s>>>(static_cast<const unsigned char*>(d_packed),
+                                                                p.n_inputs, p.n_chan, p.n_time, p.nb, kp8, n_tiles,
+                                                                planes);
+    return cudaGetLastError();
+}
+
 template <int BITS, int OUT>
 cudaError_t launch(const Plan& p, const void* d_packed, int n_dumps, void* o0, void* o1, cudaStream_t s) {
     const int64_t n_tiles = (int64_t)n_dumps * p.n_chan * p.nb * (p.kp / kTimeBlock);
@@ -285,6 +328,12 @@ cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps,
                     : launch<4, kOutF16>(p, d_packed, n_dumps, d_planes, nullptr, s);
     return fast ? launch_fast<8>(p, d_packed, n_dumps, d_planes, s, blocks_per_sm)
                 : launch<8, kOutF16>(p, d_packed, n_dumps, d_planes, nullptr, s);
+}
+
+cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s) {
+    if (!tc_planes_e4m3(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u) || (reinterpret_cast<uintptr_t>(d_planes) & 15u))
+        return cudaErrorInvalidValue;
+    return launch_fast_e4m3(p, d_packed, n_dumps, d_planes, tc_kp_e4m3(p), s);
 }
 
 cudaError_t launch_unpack_f32(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s) {

@@ -80,7 +80,7 @@ constexpr int kStageBytes = 4 * 16 * kStageRowBytes;
 // slot and its destination are 16-byte aligned together and the bulk copies stay aligned.
 constexpr int kStageRowBytesF = 66 * 8;
 
-enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRawF32 = 4, kRaw4F8 = 5 };
+enum Mode : int { kPlanesF16 = 0, kPlanesBF16x3 = 1, kRaw8 = 2, kRaw4 = 3, kRawF32 = 4, kRaw4F8 = 5, kPlanesF8 = 6 };
 
 template <int MODE>
 struct Cfg {
@@ -88,9 +88,10 @@ struct Cfg {
     // warps (the BF16x3 products of the planes path, without the planes in memory)
     static constexpr bool kFloat = MODE == kRawF32;
     // kRaw4F8: 4-bit samples converted to e4m3 operand bytes (kind::f8f6f4): a 128-byte operand
-    // row then holds 128 samples, so a stage covers 128 samples in four K = 32 MMAs
-    static constexpr bool kF8 = MODE == kRaw4F8;
-    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || kFloat || kF8);
+    // row then holds 128 samples, so a stage covers 128 samples in four K = 32 MMAs.  kPlanesF8:
+    // the same operands read from e4m3 planes.
+    static constexpr bool kF8 = MODE == kRaw4F8 || MODE == kPlanesF8;
+    static constexpr bool kRaw = (MODE == kRaw8 || MODE == kRaw4 || kFloat || MODE == kRaw4F8);
     static constexpr bool kBits8 = MODE == kRaw8;
     static constexpr bool kSplit = (MODE == kPlanesBF16x3 || kFloat);
     static constexpr int kEpiWarps = 4;     // one per tensor-memory lane quarter
@@ -375,19 +376,6 @@ __device__ __forceinline__ ConvLane conv_lane4_f8(int l) {
     return c;
 }
 
-// Four exact e4m3 bytes (samples in order) from two fp16 pairs whose values are integers in
-// -8..7, which e4m3 (3 mantissa bits) holds exactly: the conversion cannot round.
-__device__ __forceinline__ uint32_t e4m3x4(uint32_t h01, uint32_t h23) {
-    __half2_raw a, b;
-    a.x = (unsigned short)(h01 & 0xFFFFu);
-    a.y = (unsigned short)(h01 >> 16);
-    b.x = (unsigned short)(h23 & 0xFFFFu);
-    b.y = (unsigned short)(h23 >> 16);
-    const uint32_t lo = __nv_cvt_halfraw2_to_fp8x2(a, __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi = __nv_cvt_halfraw2_to_fp8x2(b, __NV_SATFINITE, __NV_E4M3);
-    return (lo & 0xFFFFu) | (hi << 16);
-}
-
 // Packed 4-bit words -> e4m3 operand tile (128 samples per 128-byte row): lane l holds
 // w[e] = inputs 4m .. 4m+3 (m = l & 15) of sample 16c + e, e = 0..15, and writes, for the re
 // and im rows of each of its four inputs, the row's 16-byte chunk c (16 samples).
@@ -408,9 +396,9 @@ __device__ __forceinline__ void convert_words4_f8(const uint32_t (&w)[16], uint3
         uint32_t r[4], m[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
-            r[o] = e4m3x4(pair_to_half2(a[4 * o], a[4 * o + 1], sel, flip, bias),
+            r[o] = conv::e4m3x4(pair_to_half2(a[4 * o], a[4 * o + 1], sel, flip, bias),
                           pair_to_half2(a[4 * o + 2], a[4 * o + 3], sel, flip, bias));
-            m[o] = e4m3x4(pair_to_half2(b[4 * o], b[4 * o + 1], sel, flip, bias),
+            m[o] = conv::e4m3x4(pair_to_half2(b[4 * o], b[4 * o + 1], sel, flip, bias),
                           pair_to_half2(b[4 * o + 2], b[4 * o + 3], sel, flip, bias));
         }
         st_shared_v4(at + (c16 ^ cl.r7x16[kk]), r[0], r[1], r[2], r[3]);
@@ -598,15 +586,15 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             // diagonal the first half of the B box itself
                             const uint32_t nB = (uint32_t)it.nsub;
                             ptx::mbar_expect_tx(fb, (nB + (same ? 0u : 1u)) * (uint32_t)kTileBytes);
-                            if (!same) ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
-                            ptx::tma_load_2d(st + bo, nB == 2 ? &jb.map_wide : &jb.map, kb * kTimeBlock, rowB, fb);
+                            if (!same) ptx::tma_load_2d(st, &jb.map, kb * C::kStageT, rowA, fb);
+                            ptx::tma_load_2d(st + bo, nB == 2 ? &jb.map_wide : &jb.map, kb * C::kStageT, rowB, fb);
                         } else {
                             ptx::mbar_expect_tx(fb, (same ? 1u : 2u) * (uint32_t)(C::kTilesPerOperand * kTileBytes));
-                            ptx::tma_load_2d(st, &jb.map, kb * kTimeBlock, rowA, fb);
-                            if (!same) ptx::tma_load_2d(st + bo, &jb.map, kb * kTimeBlock, rowB, fb);
+                            ptx::tma_load_2d(st, &jb.map, kb * C::kStageT, rowA, fb);
+                            if (!same) ptx::tma_load_2d(st + bo, &jb.map, kb * C::kStageT, rowB, fb);
                             if (C::kSplit) {
-                                ptx::tma_load_2d(st + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowA, fb);
-                                if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * kTimeBlock, rowB, fb);
+                                ptx::tma_load_2d(st + kTileBytes, &prm.map_lo, kb * C::kStageT, rowA, fb);
+                                if (!same) ptx::tma_load_2d(st + bo + kTileBytes, &prm.map_lo, kb * C::kStageT, rowB, fb);
                             }
                         }
                     }
@@ -681,7 +669,7 @@ __global__ void __launch_bounds__(Cfg<MODE>::kThreads, 1) xeng_tc_kernel(const _
                             const uint32_t id = it.nsub == 2 ? idesc_wide : idesc;
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
-                                ptx::mma_f16_lo(dset, aw + 2u * k, b0 + 2u * k, desc_hi, id, (k > 0) | acc0);
+                                mma_op<C::kF8>(dset, aw + 2u * k, b0 + 2u * k, desc_hi, id, (k > 0) | acc0);
                         } else if constexpr (C::kSplit) {
                             const uint32_t b0 = same ? a0 : a0 + boff16;
 #pragma unroll
@@ -1130,13 +1118,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 // 2-D map over plane rows: dim0 = Kp samples (fp16/bf16), dim1 = all 128-row blocks; boxes of
 // one block (128 rows) or, for wide items, of two adjacent blocks (256 rows).
+// Planes [rows][kp] of 2-byte elements (fp16/bf16: boxes of 64 samples) or of e4m3 bytes
+// (UINT8: boxes of 128 samples); either way a box row is 128 bytes, loaded with 128-byte swizzle.
 bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CUtensorMapDataType dt,
                     int box_rows = kBlockRows) {
     auto enc = get_encode();
     if (!enc) return false;
+    const int elem = dt == CU_TENSOR_MAP_DATA_TYPE_UINT8 ? 1 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTimeBlock, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1196,7 +1187,7 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
         TcJob& jb = prm->jobs[j];
         jb.map = maps[j];
         // wide items only where the MMA feed reads fp16 planes (two blocks per TMA box)
-        jb.tw = (MODE == kPlanesF16 && sp.tw == 2 && maps_wide) ? 2 : 1;
+        jb.tw = ((MODE == kPlanesF16 || MODE == kPlanesF8) && sp.tw == 2 && maps_wide) ? 2 : 1;
         if (jb.tw == 2) jb.map_wide = maps_wide[j];
         jb.vis = sp.vis;
         jb.n_inputs = sp.n_inputs;
@@ -1324,6 +1315,40 @@ cudaError_t launch_xeng_tc(const Plan& p, const void* d_planes, const void* d_pl
         return launch_jobs<kPlanesF16, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s, &mw);
     }
     return launch_jobs<kPlanesF16, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s);
+}
+
+bool tc_planes_e4m3(const Plan& p) { return p.sample_bits == 4 && tc_raw_supported(p); }
+
+int tc_kp_e4m3(const Plan& p) { return (p.n_time + 127) / 128 * 128; }
+
+cudaError_t launch_xeng_tc_e4m3_planes(const Plan& p, const void* d_planes, int n_dumps, void* d_vis, int accumulate,
+                                       cudaStream_t s) {
+    const int64_t rows = (int64_t)n_dumps * p.n_chan * p.nb * kBlockRows;
+    if (rows >= (int64_t)1 << 31 || !tc_planes_e4m3(p)) return cudaErrorInvalidValue;
+    const int kp8 = tc_kp_e4m3(p);
+    CUtensorMap mh, mw;
+    TcJobSpec sp{p.n_inputs, p.n_chan, p.n_time, n_dumps, p.sample_bits, d_planes, d_vis, 1};
+    TcTuning tune{};
+    tune.op_stages = p.tc_op_stages;
+    if (!make_plane_map(&mh, d_planes, kp8, rows, CU_TENSOR_MAP_DATA_TYPE_UINT8)) return cudaErrorInvalidValue;
+    // item shape as for fp16 planes
+    const bool wide = p.tc_items == 2 || (p.tc_items == 0 && !(accumulate && kp8 < 1024));
+    if (p.nb >= 2 && wide &&
+        make_plane_map(&mw, d_planes, kp8, rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2 * kBlockRows)) {
+        sp.tw = 2;
+        return launch_jobs<kPlanesF8, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s, &mw);
+    }
+    return launch_jobs<kPlanesF8, 1>(&sp, 1, &mh, nullptr, accumulate, p.d_status, p.n_sm, tune, s);
+}
+
+cudaError_t launch_tc_plane_path(const Plan& p, const void* d_packed, int n_dumps, void* d_ws, void* d_vis,
+                                 int accumulate, cudaStream_t s) {
+    if (tc_planes_e4m3(p)) {
+        const cudaError_t e = launch_unpack_e4m3(p, d_packed, n_dumps, d_ws, s);
+        return e == cudaSuccess ? launch_xeng_tc_e4m3_planes(p, d_ws, n_dumps, d_vis, accumulate, s) : e;
+    }
+    const cudaError_t e = launch_unpack_fp16(p, d_packed, n_dumps, d_ws, s);
+    return e == cudaSuccess ? launch_xeng_tc(p, d_ws, nullptr, n_dumps, d_vis, accumulate, s) : e;
 }
 
 bool tc_use_planes(const Plan& p) {

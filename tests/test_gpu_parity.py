@@ -132,6 +132,34 @@ def test_e4m3_operands_extremes_and_chunk_flush(t):
     assert np.array_equal(v, oracle.xcorr_int(p, n, 1, t, 4))
 
 
+# 4-bit samples of arrays that take the plane feed: the workspace holds e4m3 planes (rows of
+# n_time rounded up to 128 bytes) read by kind::f8f6f4 MMAs, single tiles and wide items, ragged
+# last blocks and sample tails, several dumps and accumulate
+E4M3_PLANE_CASES = [(256, 2, 64), (272, 3, 129), (448, 1, 200), (320, 2, 255), (512, 2, 1000), (1008, 1, 130)]
+
+
+@pytest.mark.parametrize("items", [1, 2])
+@pytest.mark.parametrize("n,c,t", E4M3_PLANE_CASES)
+def test_e4m3_planes_4bit_bit_exact(items, n, c, t):
+    p = np.concatenate([int_case(9600 + n + c + t + k, n, c, t, 4) for k in range(2)])
+    ref = np.stack([oracle.xcorr_int(p[k * t:(k + 1) * t], n, c, t, 4) for k in range(2)])
+    v = run_engine(p, n, c, t, 4, TC, n_dumps=2, operands=(2, items))
+    assert np.array_equal(v, ref)
+    v = run_engine(p, n, c, t, 4, TC, n_dumps=2, accumulate=True, vis_init=ref, operands=(2, items))
+    assert np.array_equal(v, 2 * ref)
+
+
+def test_e4m3_planes_chunk_flush():
+    # -8 - 8j everywhere but one -8 + 7j input, one sample past the exact 131072-sample chunk
+    n, t = 128, 131073
+    re = np.full((t, 1, n), -8, np.int16)
+    im = np.full((t, 1, n), -8, np.int16)
+    im[:, 0, 100] = 7
+    p = synth.pack(re, im, 4)
+    v = run_engine(p, n, 1, t, 4, TC, operands=(2, 2))[0]
+    assert np.array_equal(v, oracle.xcorr_int(p, n, 1, t, 4))
+
+
 @pytest.mark.parametrize("n", [64, 192])
 def test_fused_dumps_and_accumulate(n):
     c, t, bits, d = 3, 200, 8, 3
