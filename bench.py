@@ -696,8 +696,10 @@ def run_shape(args):
     stream = torch.cuda.current_stream(dev)
     plan = corr.Plan(n, c, t, bits)
     engine = {"tc": corr.ENGINE_TC, "fp32": corr.ENGINE_FP32}[args.engine]
+    # planes_fp16: the public planes calls (corr_unpack into fp16 planes, then the plane-fed X
+    # stage), which 4-bit plans otherwise replace by e4m3 planes in their workspace
     plan.set_operands({"auto": corr.OPERANDS_AUTO, "packed": corr.OPERANDS_PACKED, "planes": corr.OPERANDS_PLANES,
-                       "packed_f8": corr.OPERANDS_PACKED_F8}[args.feed],
+                       "planes_fp16": corr.OPERANDS_PLANES, "packed_f8": corr.OPERANDS_PACKED_F8}[args.feed],
                       {"auto": corr.ITEMS_AUTO, "tiles": corr.ITEMS_TILES, "wide": corr.ITEMS_WIDE}[args.items])
     if args.op_stages:
         plan.set_tuning(args.op_stages, 0)
@@ -711,8 +713,15 @@ def run_shape(args):
     if x.numel() * x.element_size() != plan.info()[1]:
         raise ValueError("sample buffer does not match the plan's packed size")
     vis = plan.empty_vis(1, dev)
-    ws = plan.empty_workspace(engine, 1, dev) if args.feed != "packed" else None
-    run = lambda: plan.run(x, vis, ws, engine=engine, stream=stream)   # noqa: E731
+    if args.feed == "planes_fp16":
+        ws = torch.empty(plan.planes_size(1), dtype=torch.uint8, device=dev)
+
+        def run():
+            plan.unpack(x, ws, stream=stream)
+            plan.run_planes(ws, vis, engine=engine, stream=stream)
+    else:
+        ws = plan.empty_workspace(engine, 1, dev) if args.feed != "packed" else None
+        run = lambda: plan.run(x, vis, ws, engine=engine, stream=stream)   # noqa: E731
     for _ in range(args.warmup):
         run()
     torch.cuda.synchronize()
@@ -917,8 +926,9 @@ def main():
                     choices=["stream", "mwa32t", "large", "batch", "serve", "fx", "dump", "float", "shape"])
     ap.add_argument("--shape", default="512,128,2048,8", help="shape workload: N,C,T,BITS")
     ap.add_argument("--engine", default="tc", choices=["tc", "fp32"], help="shape workload: X engine")
-    ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes", "packed_f8"],
-                    help="shape workload: operand feed (packed = fp16 operands; packed_f8 = e4m3, 4-bit samples)")
+    ap.add_argument("--feed", default="auto", choices=["auto", "packed", "planes", "packed_f8", "planes_fp16"],
+                    help="shape workload: operand feed (packed = fp16 operands; packed_f8 = e4m3, 4-bit samples; "
+                         "planes = the workspace's planes, e4m3 for 4-bit samples; planes_fp16 = fp16 planes)")
     ap.add_argument("--items", default="auto", choices=["auto", "tiles", "wide"], help="shape workload: item shape")
     ap.add_argument("--op-stages", type=int, default=0, help="shape workload: operand-ring depth (0: default)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
