@@ -143,16 +143,22 @@ bool build_groups(corr_batch_s* b, const TuneChoice& ch) {
                     return job_cost_per_item(b->jobs[x], cpi_of(b->jobs[x])) >
                            job_cost_per_item(b->jobs[y], cpi_of(b->jobs[y]));
                 });
-            // packed 4-bit samples take e4m3 operands (128-sample boxes), as single-job calls do
-            const bool f8 = bits == 4 && !planes;
+            // 4-bit samples take e4m3 operands (128-sample boxes), as single-job calls do: converted
+            // in the kernel, or read from e4m3 planes.  Batch jobs have TMA-addressable rows, so the
+            // plane workspace holds e4m3 planes for every 4-bit job; anything else is refused here
+            // rather than written as fp16 planes into a slot sized for e4m3 ones.
+            const bool f8 = bits == 4;
+            if (f8 && planes)
+                for (int k : g.job_index)
+                    if (!tc_planes_e4m3(plan_of_job(b->jobs[k], b->n_sm))) return false;
             for (int k : g.job_index) {
                 const corr_job& j = b->jobs[k];
                 const void* data = planes ? static_cast<const void*>(b->d_planes + b->plane_off[k]) : j.packed;
                 TcJobSpec sp{j.n_inputs, j.n_chan, j.n_time, 1, j.sample_bits, data, j.vis, cpi_of(j)};
                 CUtensorMap m, mw{};
-                if (!(planes ? tc_make_plane_map(&m, sp) : tc_make_raw_map(&m, sp, f8))) return false;
+                if (!(planes ? tc_make_plane_map(&m, sp, f8) : tc_make_raw_map(&m, sp, f8))) return false;
                 const int nb = blocks_of(j);
-                if (planes && ch.wide && nb >= 2 && tc_make_plane_map_wide(&mw, sp)) sp.tw = 2;
+                if (planes && ch.wide && nb >= 2 && tc_make_plane_map_wide(&mw, sp, f8)) sp.tw = 2;
                 g.specs.push_back(sp);
                 g.maps.push_back(m);
                 g.maps_wide.push_back(mw);
@@ -172,8 +178,9 @@ cudaError_t unpack_range(corr_batch_s* b, const ModeGroup& g, size_t i0, size_t 
     for (size_t i = i0; i < i1; ++i) {   // each plane job writes its own planes
         const corr_job& j = b->jobs[g.job_index[i]];
         const Plan p = plan_of_job(j, b->n_sm);
-        const cudaError_t e =
-            launch_unpack_fp16(p, j.packed, 1, const_cast<void*>(g.specs[i].data), s, blocks_per_sm);
+        void* planes = const_cast<void*>(g.specs[i].data);
+        const cudaError_t e = g.tune.f8_operands ? launch_unpack_e4m3(p, j.packed, 1, planes, s, blocks_per_sm)
+                                                 : launch_unpack_fp16(p, j.packed, 1, planes, s, blocks_per_sm);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -495,7 +502,8 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
         corr_batch_destroy(b);
         return cuda_error(e, "corr_batch_create");
     }
-    // plane workspace: one set of fp16 planes per multi-block job, owned by the batch
+    // plane workspace: one set of planes per multi-block job (fp16, or e4m3 for 4-bit samples of
+    // TMA-addressable rows), owned by the batch
     b->plane_off.assign(n_jobs, SIZE_MAX);
     if (flags & CORR_BATCH_PLANES) {
         b->allow_planes = true;
@@ -504,7 +512,7 @@ corr_status corr_batch_create(corr_batch* out, const corr_job* jobs, int n_jobs,
             const Plan p = plan_of_job(b->jobs[k], b->n_sm);
             if (p.nb < 2) continue;
             b->plane_off[k] = total;
-            total += (planes_bytes(p, 1) + 255) / 256 * 256;
+            total += (tc_workspace_planes_bytes(p, 1) + 255) / 256 * 256;   // e4m3 planes for 4-bit jobs
         }
         if (total) {
             e = cudaMalloc((void**)&b->d_planes, total);

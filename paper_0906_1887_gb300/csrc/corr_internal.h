@@ -89,7 +89,8 @@ bool tc_raw_supported(int n_inputs, int sample_bits);
 bool tc_planes_e4m3(const Plan& p);
 int tc_kp_e4m3(const Plan& p);
 size_t tc_workspace_planes_bytes(const Plan& p, int n_dumps);
-cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s);
+cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s,
+                               int blocks_per_sm = 0);
 cudaError_t launch_xeng_tc_e4m3_planes(const Plan& p, const void* d_planes, int n_dumps, void* d_vis, int accumulate,
                                        cudaStream_t s);
 // unpack into the workspace's planes, then the plane-fed tensor-core X stage
@@ -132,9 +133,9 @@ cudaError_t launch_phasors(const Plan& p, const double* d_delays, const double* 
 bool tc_make_raw_map(CUtensorMap* map, const TcJobSpec& sp, bool f8 = false);   // f8: 128-sample boxes
 // Jobs whose samples the unpack kernel already turned into fp16 planes (TcJobSpec::data = the
 // planes, [n_dumps][C][NB][128][Kp]); one channel per work item.
-bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp);
+bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp, bool f8 = false);   // f8: e4m3 planes
 // the same planes in boxes of two adjacent blocks, for wide items (TcJobSpec::tw = 2)
-bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp);
+bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp, bool f8 = false);   // f8: e4m3 planes
 cudaError_t launch_xeng_tc_plane_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
                                       int* status, int n_sm, const TcTuning& tune, cudaStream_t s,
                                       const CUtensorMap* maps_wide = nullptr);

@@ -291,17 +291,25 @@ cudaError_t launch_fast(const Plan& p, const void* d_packed, int n_dumps, void* 
     return cudaGetLastError();
 }
 
-// 4-bit samples into e4m3 planes with rows of kp8 bytes (n_time rounded up to 128 samples)
+// 4-bit samples into e4m3 planes with rows of kp8 bytes (n_time rounded up to 128 samples);
+// blocks_per_sm as for launch_fast
 cudaError_t launch_fast_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* planes, int kp8,
-                             cudaStream_t s) {
+                             cudaStream_t s, int blocks_per_sm) {
     using F = FastTile<4>;
     const int64_t n_tiles = (int64_t)n_dumps * p.n_chan * p.nb * (kp8 / kTimeBlock);
     if (n_tiles < 1) return cudaSuccess;
-    const int64_t cap = (int64_t)p.n_sm * 16;
-    const int grid = (int)(n_tiles < cap ? n_tiles : cap);
-    unpack_fast_kernel<4, 1, true><<<grid, F::kThreads, 0, s>>>(static_cast<const unsigned char*>(d_packed),
-                                                                p.n_inputs, p.n_chan, p.n_time, p.nb, kp8, n_tiles,
-                                                                planes);
+    const auto* src = static_cast<const unsigned char*>(d_packed);
+    if (blocks_per_sm > 0) {
+        const int64_t cap = (int64_t)p.n_sm * blocks_per_sm;
+        const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+        unpack_fast_kernel<4, 8, true><<<grid, F::kThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb, kp8,
+                                                                    n_tiles, planes);
+    } else {
+        const int64_t cap = (int64_t)p.n_sm * 16;
+        const int grid = (int)(n_tiles < cap ? n_tiles : cap);
+        unpack_fast_kernel<4, 1, true><<<grid, F::kThreads, 0, s>>>(src, p.n_inputs, p.n_chan, p.n_time, p.nb, kp8,
+                                                                    n_tiles, planes);
+    }
     return cudaGetLastError();
 }
 
@@ -330,10 +338,11 @@ cudaError_t launch_unpack_fp16(const Plan& p, const void* d_packed, int n_dumps,
                 : launch<8, kOutF16>(p, d_packed, n_dumps, d_planes, nullptr, s);
 }
 
-cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s) {
+cudaError_t launch_unpack_e4m3(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s,
+                               int blocks_per_sm) {
     if (!tc_planes_e4m3(p) || (reinterpret_cast<uintptr_t>(d_packed) & 15u) || (reinterpret_cast<uintptr_t>(d_planes) & 15u))
         return cudaErrorInvalidValue;
-    return launch_fast_e4m3(p, d_packed, n_dumps, d_planes, tc_kp_e4m3(p), s);
+    return launch_fast_e4m3(p, d_packed, n_dumps, d_planes, tc_kp_e4m3(p), s, blocks_per_sm);
 }
 
 cudaError_t launch_unpack_f32(const Plan& p, const void* d_packed, int n_dumps, void* d_planes, cudaStream_t s) {

@@ -1404,20 +1404,23 @@ cudaError_t launch_xeng_tc_raw_jobs(const TcJobSpec* specs, const CUtensorMap* m
     return launch_jobs<kRaw4, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s);
 }
 
-bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp) {
+bool tc_make_plane_map(CUtensorMap* map, const TcJobSpec& sp, bool f8) {
     const int nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
-    const int kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    const int step = f8 ? Cfg<kPlanesF8>::kStageT : kTimeBlock;
+    const int kp = (sp.n_time + step - 1) / step * step;
     const int64_t rows = (int64_t)sp.n_dumps * sp.n_chan * nb * kBlockRows;
     if (rows >= (int64_t{1} << 31)) return false;   // TMA row coordinates are int32
-    return make_plane_map(map, sp.data, kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    return make_plane_map(map, sp.data, kp, rows, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
 }
 
-bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp) {
+bool tc_make_plane_map_wide(CUtensorMap* map, const TcJobSpec& sp, bool f8) {
     const int nb = (sp.n_inputs + kBlockInputs - 1) / kBlockInputs;
-    const int kp = (sp.n_time + kTimeBlock - 1) / kTimeBlock * kTimeBlock;
+    const int step = f8 ? Cfg<kPlanesF8>::kStageT : kTimeBlock;
+    const int kp = (sp.n_time + step - 1) / step * step;
     const int64_t rows = (int64_t)sp.n_dumps * sp.n_chan * nb * kBlockRows;
     if (rows >= (int64_t{1} << 31) || rows < 2 * kBlockRows) return false;
-    return make_plane_map(map, sp.data, kp, rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2 * kBlockRows);
+    return make_plane_map(map, sp.data, kp, rows, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                          2 * kBlockRows);
 }
 
 cudaError_t launch_xeng_tc_plane_jobs(const TcJobSpec* specs, const CUtensorMap* maps, int n_jobs, int accumulate,
@@ -1428,6 +1431,14 @@ cudaError_t launch_xeng_tc_plane_jobs(const TcJobSpec* specs, const CUtensorMap*
         if ((specs[j].sample_bits != 4 && specs[j].sample_bits != 8) || specs[j].cpi != 1 ||
             (specs[j].tw == 2 && !maps_wide))
             return cudaErrorInvalidValue;
+    if (tune.f8_operands) {   // e4m3 planes of 4-bit samples (maps of tc_make_plane_map(..., true))
+        for (int j = 0; j < n_jobs; ++j)
+            if (specs[j].sample_bits != 4) return cudaErrorInvalidValue;
+        if (n_jobs == 1)
+            return launch_jobs<kPlanesF8, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s, maps_wide);
+        return launch_jobs<kPlanesF8, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s,
+                                                maps_wide);
+    }
     if (n_jobs == 1)
         return launch_jobs<kPlanesF16, 1>(specs, 1, maps, nullptr, accumulate, status, n_sm, tune, s, maps_wide);
     return launch_jobs<kPlanesF16, kMaxJobs>(specs, n_jobs, maps, nullptr, accumulate, status, n_sm, tune, s,

@@ -14,6 +14,8 @@ pytestmark = pytest.mark.gpu
 JOBS = [  # (n_inputs, n_chan, n_time, bits): every array size and mode the batch path takes
     (32, 65, 200, 8), (64, 33, 1100, 8), (128, 7, 300, 8), (256, 3, 129, 8), (64, 64, 64, 8),
     (16, 9, 77, 4), (64, 12, 513, 4), (96, 5, 2100, 8), (48, 3, 256, 4), (512, 1, 128, 8),
+    # 4-bit arrays of several blocks: e4m3 operands, converted in the kernel or read from e4m3 planes
+    (256, 3, 300, 4), (192, 2, 129, 4),
 ]
 
 
