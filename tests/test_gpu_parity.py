@@ -265,7 +265,8 @@ def test_plane_path_tc_and_fp32(n, c, t, bits):
     plan.close()
 
 
-@pytest.mark.parametrize("n,bits,chunk", [(64, 8, 2), (40, 8, 3), (128, 4, 0)])
+# (256, 4): the pipeline's workspace holds e4m3 planes (4 blocks take the plane feed)
+@pytest.mark.parametrize("n,bits,chunk", [(64, 8, 2), (40, 8, 3), (128, 4, 0), (256, 4, 3)])
 def test_host_pipeline_end_to_end(n, bits, chunk):
     # host buffers in, host buffers out: pipelined copies and X stage over chunks of dumps
     from paper_0906_1887_gb300 import corr
