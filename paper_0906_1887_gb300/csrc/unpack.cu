@@ -8,7 +8,8 @@
 //
 // Output planes: [dump][chan][NB][128][Kp]; row 2r holds the real parts and row 2r + 1
 // the imaginary parts of input r of the block's 64 inputs; Kp = n_time rounded up to 64;
-// padded inputs and samples are zero.
+// padded inputs and samples are zero.  Elements are fp16, or, for the e4m3 plane feed of 4-bit
+// samples, e4m3 bytes with Kp = n_time rounded up to 128.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
