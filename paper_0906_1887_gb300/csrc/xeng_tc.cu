@@ -25,12 +25,14 @@
 // fp32 accumulation.
 //
 // Two ways to feed the operands:
-//   planes  -- the unpack kernel has written fp16 (or bf16 hi/lo) sample planes in the
-//              interleaved row order; TMA loads 128-row x 64-sample tiles with 128-byte
-//              swizzle straight into the operand ring.
+//   planes  -- the unpack kernel has written fp16 (or bf16 hi/lo; e4m3 for 4-bit samples)
+//              sample planes in the interleaved row order; TMA loads 128-row x 128-byte tiles
+//              (64 fp16 or 128 e4m3 samples) with 128-byte swizzle straight into the operand
+//              ring.
 //   raw     -- (4/8-bit samples) TMA loads the packed [time][chan][input] bytes of a
-//              64-input x 64-sample block and eight converter warps turn them into the
-//              swizzled fp16 operand tiles in shared memory: the unpack/transpose step
+//              64-input x 64-sample block (128 samples for 4-bit e4m3 operands) and eight
+//              converter warps turn them into the swizzled operand tiles in shared memory: the
+//              unpack/transpose step
 //              (Sec. 4) fused into the X kernel, so the samples cross HBM once.  Float
 //              samples of single-block arrays go the same way (8-byte complex floats in,
 //              bf16 hi and lo tiles out) instead of through planes.
@@ -122,7 +124,7 @@ struct TcJob {
     int tw;              // 2: wide items (block I against blocks J0, J0 + 1, one N = 256 MMA); 1: tiles
     int cpi;             // channels per work item (2: adjacent channel pair, single-block arrays)
     int n_groups;        // channel groups per dump = ceil(n_chan / cpi)
-    int chunk_kb;        // 64-sample blocks per exactly-flushed chunk
+    int chunk_kb;        // stages (64 samples; 128 with e4m3 operands) per exactly-flushed chunk
     // division by n_tiles and n_groups as q = (umulhi(n, m) + n) >> s (n < 2^31; Granlund and
     // Montgomery, division by invariant integers using multiplication)
     uint32_t tiles_m, groups_m;
@@ -1136,7 +1138,7 @@ bool make_plane_map(CUtensorMap* map, const void* base, int kp, int64_t rows, CU
 }
 
 // 4-D map over packed bytes [dump][time][chan][input*bps]; box = 64 inputs x box_chans channels
-// x 64 samples.
+// x box_t samples (64, or 128 for e4m3 operands).
 // Out-of-range inputs (ragged last block) and samples (ragged last block) read as zero.
 bool make_raw_map(CUtensorMap* map, const void* base, int n_inputs, int n_chan, int n_time, int n_dumps, int bps,
                   int box_chans, int box_t) {
