@@ -32,10 +32,9 @@
 //   raw     -- (4/8-bit samples) TMA loads the packed [time][chan][input] bytes of a
 //              64-input x 64-sample block (128 samples for 4-bit e4m3 operands) and eight
 //              converter warps turn them into the swizzled operand tiles in shared memory: the
-//              unpack/transpose step
-//              (Sec. 4) fused into the X kernel, so the samples cross HBM once.  Float
-//              samples of single-block arrays go the same way (8-byte complex floats in,
-//              bf16 hi and lo tiles out) instead of through planes.
+//              unpack/transpose step (Sec. 4) fused into the X kernel, so the samples cross
+//              HBM once.  Float samples of single-block arrays go the same way (8-byte
+//              complex floats in, bf16 hi and lo tiles out) instead of through planes.
 //
 // CTA roles (one CTA per SM, persistent over work items = (dump, channel, I, J)):
 //   warp 0       TMA producer
