@@ -139,7 +139,7 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
  *                         -8..7 exactly and halve the operand bytes per sample; fp32 accumulation
  *                         as for fp16, so results stay bit-exact (CORR_EUNSUPPORTED for 8-bit
  *                         samples, whose range e4m3 does not hold, or rows that are not 16-byte
- *                         multiples).  The fused dump call keeps fp16 operands.
+ *                         multiples).
  * items (plane feed): CORR_ITEMS_WIDE = work items of block I against blocks J and J + 1 in one
  * M = 128, N = 256 MMA (a quarter fewer operand loads per tile); CORR_ITEMS_TILES = one 64 x 64
  * input tile per item; CORR_ITEMS_AUTO = wide, except single tiles for accumulating dumps of

@@ -1271,9 +1271,9 @@ cudaError_t launch_jobs(const TcJobSpec* specs, int n_jobs, const CUtensorMap* m
     prm->bar_offset = prm->staging_offset + stage_space;
     const int smem_bytes = prm->bar_offset + kBarBytes + 1024;
     auto kern = xeng_tc_kernel<MODE, MAXJ, false>;
-    if constexpr (C::kRaw && !C::kFloat && !C::kF8 && MAXJ == 1) {
+    if constexpr (C::kRaw && !C::kFloat && MAXJ == 1) {
         if (any_dump) kern = xeng_tc_kernel<MODE, MAXJ, true>;
-    } else if (any_dump) {   // dump mode is built for single-job fp16-operand packed-sample launches only
+    } else if (any_dump) {   // dump mode is built for single-job packed-sample launches only
         delete prm;
         return cudaErrorInvalidValue;
     }
@@ -1453,8 +1453,8 @@ cudaError_t launch_raw_impl(const Plan& p, const void* d_packed, int n_dumps, vo
     TcTuning plan_tune;
     plan_tune.op_stages = p.tc_op_stages;
     // 4-bit samples take e4m3 operands unless the plan asks for fp16 (CORR_OPERANDS_PACKED):
-    // the same bits, half the operand bytes and MMAs per sample (the fused dump keeps fp16)
-    const bool f8 = p.sample_bits == 4 && (p.tc_operands == 0 || p.tc_operands == 3) && out_mode == 0;
+    // the same bits, half the operand bytes and MMAs per sample
+    const bool f8 = p.sample_bits == 4 && (p.tc_operands == 0 || p.tc_operands == 3);
     TcTuning run_tune = tune ? *tune : plan_tune;
     run_tune.f8_operands = f8 ? 1 : 0;
     const int cpi = tc_default_cpi(p.n_inputs, (int64_t)n_dumps * p.n_chan, p.n_sm);

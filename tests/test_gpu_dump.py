@@ -111,6 +111,8 @@ def test_dump_rejects_bad_arguments():
 @pytest.mark.parametrize("n,c,t,bits,n_dumps,n_accum,delays", [
     (64, 5, 1000, 8, 1, 1, True), (64, 4, 1024, 8, 2, 3, False), (136, 3, 200, 8, 1, 1, True),
     (16, 4, 300, 4, 3, 2, True), (192, 2, 256, 8, 2, 1, True), (8, 3, 64, 8, 1, 5, False),
+    # 4-bit samples take e4m3 operands here too: single and multi-block, tails around 128 samples
+    (64, 6, 500, 4, 2, 4, True), (128, 2, 129, 4, 1, 1, True),
 ])
 def test_fused_dump_matches_oracle(n, c, t, bits, n_dumps, n_accum, delays):
     from paper_0906_1887_gb300 import corr
