@@ -855,6 +855,8 @@ def run_serve(args):
     for jid in warm:
         srv.wait(jid, 300.0)
         srv.release(jid)
+    clocks = ClockSampler(0)
+    clocks.start()
     t_start = time.time()
     t_next = t_start
     n_sub = 0
@@ -877,6 +879,7 @@ def run_serve(args):
     done_evt.set()
     th.join(timeout=600)
     wall = time.time() - t_start
+    clk = clocks.stop()
     for s_ in range(n_streams):
         srv.close_stream(s_, 60.0)
     srv.close()
@@ -904,6 +907,7 @@ def run_serve(args):
             "tera_cmac_per_s": cm / wall / 1e12, "offered_tera_cmac_per_s": offered / 1e12,
             "device_state_bytes": arena_state,
             "per_stream": [_stream_latency(ok, s_, shapes[s_][2] / CHANNEL_RATE_HZ * 1e3) for s_ in range(n_streams)],
+            "clocks": clk,
             "latency": "submit to the job's samples accumulated on the device (closing jobs: to the dump in "
                        "pinned host memory); target p99 below the job's own sample time and every dump within "
                        "its dump interval"}

@@ -128,7 +128,8 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
  * per tile it meets, about N/128 times per channel) or reads fp16 sample planes that the unpack
  * kernel wrote into the workspace first (each block converted once; the planes cost HBM
  * traffic).  operands:
- *   CORR_OPERANDS_AUTO    planes for arrays of at least 256 inputs (4 blocks) when a workspace
+ *   CORR_OPERANDS_AUTO    planes for arrays of at least 256 inputs (4 blocks; 192 inputs, 3
+ *                         blocks, for 4-bit samples, whose planes are e4m3) when a workspace
  *                         is given, and always where the packed rows are not 16-byte multiples;
  *                         otherwise the fused conversion, into e4m3 operands for 4-bit samples;
  *   CORR_OPERANDS_PACKED  always the fused conversion into fp16 operands (CORR_EUNSUPPORTED

@@ -79,8 +79,12 @@ bool tc_raw_supported(const Plan& p);
 // Whether the tensor-core X stage of 4/8-bit samples reads fp16 planes (written by the unpack
 // kernel into the workspace) rather than converting the packed samples itself: always when the
 // packed rows are not TMA-addressable; otherwise as the plan's knob says, by default for arrays
-// of at least kPlaneMinBlocks 64-input blocks, whose tiles re-read every block nb / 2 times.
+// of at least kPlaneMinBlocks 64-input blocks, whose tiles re-read every block nb / 2 times
+// (kPlaneMinBlocksE4m3 for 4-bit samples, whose e4m3 planes cost half as much: measured, 192
+// inputs x 1024 channels x 1024 samples 0.269 ms on planes against 0.398 ms converted in the
+// kernel; at 128 inputs the two feeds trade places with the dump length).
 constexpr int kPlaneMinBlocks = 4;
+constexpr int kPlaneMinBlocksE4m3 = 3;
 bool tc_use_planes(const Plan& p);
 bool tc_raw_supported(int n_inputs, int sample_bits);
 // The workspace's planes: e4m3 bytes for 4-bit samples of TMA-addressable rows (rows of

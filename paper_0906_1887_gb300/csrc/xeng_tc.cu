@@ -1356,7 +1356,7 @@ bool tc_use_planes(const Plan& p) {
     if (!tc_raw_supported(p)) return true;
     if (p.tc_operands == 1 || p.tc_operands == 3) return false;
     if (p.tc_operands == 2) return true;
-    return p.nb >= kPlaneMinBlocks;
+    return p.nb >= (tc_planes_e4m3(p) ? kPlaneMinBlocksE4m3 : kPlaneMinBlocks);
 }
 
 bool tc_raw_supported(int n_inputs, int sample_bits) {
