@@ -34,3 +34,14 @@ def test_host_only_calls():
     assert corr.version() >= 100
     v = np.array([[3, -4], [10, 0]], dtype=np.int64)
     assert corr.average_host(v, 4).tolist() == [[0.75, -1.0], [2.5, 0.0]]
+
+
+def test_binding_constants_match_header():
+    # every CORR_* enum value of the header has the same value under its name in the binding
+    from paper_0906_1887_gb300 import corr
+    text = open(os.path.join(ROOT, "include", "corr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = re.findall(r"\bCORR_([A-Z0-9_]+)\s*=\s*(-?\d+)", text)
+    assert ("OPERANDS_PACKED_F8", "3") in consts
+    for name, value in consts:
+        assert getattr(corr, name) == int(value), name
