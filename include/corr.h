@@ -125,9 +125,10 @@ corr_status corr_plan_set_tuning(corr_plan plan, int op_stages, int float_planes
  * Operand feed of the tensor-core X stage for 4/8-bit samples (no counterpart in the paper; the
  * results are identical for every setting).  The kernel either converts the packed samples
  * itself (converter warps; the samples cross HBM once, but each 64-input block is converted once
- * per tile it meets, about N/128 times per channel) or reads fp16 sample planes that the unpack
+ * per tile it meets, about N/128 times per channel) or reads sample planes that the unpack
  * kernel wrote into the workspace first (each block converted once; the planes cost HBM
- * traffic).  operands:
+ * traffic; fp16 planes, or e4m3 ones for 4-bit samples of rows that are 16-byte multiples --
+ * the workspace's own format, not the fp16 exchange format of corr_unpack).  operands:
  *   CORR_OPERANDS_AUTO    planes for arrays of at least 256 inputs (4 blocks; 192 inputs, 3
  *                         blocks, for 4-bit samples, whose planes are e4m3) when a workspace
  *                         is given, and always where the packed rows are not 16-byte multiples;
