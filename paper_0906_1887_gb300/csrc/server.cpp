@@ -572,7 +572,8 @@ void completer_loop(corr_server_s* S) {
                 // first: settle the copy budget before the job can be released
                 S->copy_inflight -= j.copy_bytes;
                 j.copy_bytes = 0;
-                S->copying.erase(std::find(S->copying.begin(), S->copying.end(), S->running[k]));
+                const auto at = std::find(S->copying.begin(), S->copying.end(), S->running[k]);
+                if (at != S->copying.end()) S->copying.erase(at);
             }
             if (j.stream_job) {
                 // an averaged dump left on the device stays in the stream's dump buffer
