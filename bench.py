@@ -880,6 +880,7 @@ def run_serve(args):
     th.join(timeout=600)
     wall = time.time() - t_start
     clk = clocks.stop()
+    coalesced = srv.stats()["coalesced"]
     for s_ in range(n_streams):
         srv.close_stream(s_, 60.0)
     srv.close()
@@ -906,6 +907,7 @@ def run_serve(args):
             "real_time_factor": float(t_job.sum() / 1e3 / wall) if len(lat) else None,
             "tera_cmac_per_s": cm / wall / 1e12, "offered_tera_cmac_per_s": offered / 1e12,
             "device_state_bytes": arena_state,
+            "jobs_coalesced": int(coalesced),
             "per_stream": [_stream_latency(ok, s_, shapes[s_][2] / CHANNEL_RATE_HZ * 1e3) for s_ in range(n_streams)],
             "clocks": clk,
             "latency": "submit to the job's samples accumulated on the device (closing jobs: to the dump in "

@@ -461,6 +461,7 @@ typedef struct {
     int64_t submitted, completed, failed, rejected, cancelled, queued, running;
     size_t arena_bytes, bytes_in_use, peak_bytes;
     int64_t open_streams;     /* streams with device state (corr_server_open_stream) */
+    int64_t coalesced;        /* stream jobs issued in pairs (one X stage over two jobs' samples) */
 } corr_server_stats;
 
 enum { CORR_SERVER_START_PAUSED = 1 };   /* admit nothing until corr_server_resume */
@@ -498,6 +499,9 @@ corr_status corr_server_destroy(corr_server s, double drain_timeout_s);
  *     later jobs run ahead of the X stage of earlier ones;
  *   - accumulators [n_chan][P][2] (int64 for 4/8-bit samples, float32 for float samples) that
  *     every job of the stream adds into, in submission order (one CUDA stream per open stream);
+ *     when a 4/8-bit stream's next job is already queued, in the adjacent slot and within the
+ *     same interval, the two are issued together: one X stage over the 2 x n_time samples of
+ *     both slots (one accumulator pass instead of two; each job still completes on its own);
  *   - at every jobs_per_dump-th job the interval ends:
  *       CORR_STREAM_DUMP_SUMS      the accumulated sums are copied to that job's host_vis (the
  *                                  exact integer sums for 4/8-bit samples; host_vis must not be

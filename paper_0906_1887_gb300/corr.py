@@ -395,7 +395,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rejected", ctypes.c_int64), ("cancelled", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("running", ctypes.c_int64), ("arena_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
-                ("peak_bytes", ctypes.c_size_t), ("open_streams", ctypes.c_int64)]
+                ("peak_bytes", ctypes.c_size_t), ("open_streams", ctypes.c_int64), ("coalesced", ctypes.c_int64)]
 
 
 SERVER_START_PAUSED = 1

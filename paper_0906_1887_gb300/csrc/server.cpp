@@ -120,6 +120,8 @@ struct Job {
     double deadline = 0;       // t_submit + the job's own sample time (earliest-deadline-first issue)
     cudaEvent_t ev_copied = nullptr;   // recorded after the job's samples reached the device
     size_t copy_bytes = 0;     // its host-to-device bytes while they count against the copy budget
+    const int* h_status_pair = nullptr;   // issued with the next job of its stream: that job's
+                                          // status words carry the shared X stage's status
 };
 
 // Device state of one open input stream (corr_server_open_stream).
@@ -143,6 +145,9 @@ struct StreamState {
     std::vector<cudaEvent_t> slot_full, slot_free;
     int64_t n_submitted = 0, n_retired = 0;
     bool closing = false;
+    // adjacent ring slots form one [2T][C][N] block (no padding between slots): two queued jobs
+    // of the stream can then run as one X stage over 2T samples, the workspace sized for it
+    bool pairable = false;
 };
 
 size_t packed_bytes(const corr_job_desc& d) {
@@ -194,10 +199,17 @@ corr_job_desc shape_of(const corr_stream_desc& sd) {
 size_t stream_layout(StreamState& st, char* base) {
     const corr_job_desc d = shape_of(st.d);
     Plan p = plan_of(d, 0, 0);
+    // slots 16-byte aligned (TMA and the vectorised unpack need no more), so for rows of whole
+    // 16-byte pieces they abut and two adjacent slots are one [2T][C][N] block
+    st.slot_bytes = (packed_bytes(d) + 15) / 16 * 16;
+    st.pairable = d.sample_bits != 32 && st.d.ring_slots >= 2 && st.slot_bytes == packed_bytes(d) &&
+                  d.n_time <= (1 << 28);
+    corr_job_desc d2 = d;
+    if (st.pairable) d2.n_time = 2 * d.n_time;
     size_t ws = 0;
-    if (!st.raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2 : tc_workspace_planes_bytes(p, 1);
+    if (!st.raw) ws = d.sample_bits == 32 ? 2 * (size_t)p.n_chan * p.nb * kBlockRows * p.kp * 2
+                                          : tc_workspace_planes_bytes(plan_of(d2, 0, 0), 1);
     const bool avg = st.d.dump_mode == CORR_STREAM_DUMP_AVERAGED;
-    st.slot_bytes = round_up(packed_bytes(d));
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char* ptr = base ? base + off : nullptr;
@@ -356,54 +368,71 @@ cudaError_t issue(corr_server_s* S, Job& j) {
 // issued in submission order by the single dispatcher thread).  The copy stream fills ring
 // slot seq mod R once the X stage of job seq - R has read it; the compute stream runs the X
 // stage into the stream's accumulators and, for the job that ends an interval, the dump.
-cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st) {
+// With `b` (job seq + 1, in the adjacent slot of a pairable stream) both jobs' samples are
+// copied and one X stage over the 2T samples of the two slots adds them into the accumulators:
+// one accumulator pass for two jobs.  The later job's status words carry the kernels' status.
+cudaError_t issue_stream(corr_server_s* S, Job& j, StreamState& st, Job* b = nullptr) {
     const int R = st.d.ring_slots;
     const int slot = (int)(j.seq % R);
     char* d_packed = st.slots + (size_t)slot * st.slot_bytes;
-    Plan p = plan_of(j.desc, S->device, S->n_sm);
-    p.d_status = j.d_status;   // mapped pinned status words (see issue())
+    Job& last = b ? *b : j;    // the job that may end the interval
+    corr_job_desc dx = j.desc;
+    if (b) dx.n_time = 2 * j.desc.n_time;
+    Plan p = plan_of(dx, S->device, S->n_sm);
+    p.d_status = last.d_status;   // mapped pinned status words (see issue())
     const bool sums = st.d.dump_mode == CORR_STREAM_DUMP_SUMS;
     // an interval's first job overwrites the accumulators (the previous interval's dump, issued
     // earlier on the same stream, has read them): that is the reset of Fig. 1, with no extra pass
     const int accumulate = j.seq % st.d.jobs_per_dump == 0 ? 0 : 1;
     cudaError_t e = cudaSuccess;
     if (j.seq >= R) e = cudaStreamWaitEvent(st.copy_s, st.slot_free[slot], 0);
+    if (b && e == cudaSuccess && b->seq >= R) e = cudaStreamWaitEvent(st.copy_s, st.slot_free[slot + 1], 0);
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_start, st.copy_s);
     if (e == cudaSuccess)
         e = copy_in(d_packed, j.desc.host_packed, packed_bytes(j.desc), st.copy_s);
     if (e == cudaSuccess) e = cudaEventRecord(j.ev_copied, st.copy_s);
-    if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[slot], st.copy_s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[slot], 0);
-    if (e == cudaSuccess) e = run_x(p, j.desc, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
+    if (b) {
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_start, st.copy_s);
+        if (e == cudaSuccess)
+            e = copy_in(d_packed + st.slot_bytes, b->desc.host_packed, packed_bytes(b->desc), st.copy_s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_copied, st.copy_s);
+    }
+    const int full = b ? slot + 1 : slot;
+    if (e == cudaSuccess) e = cudaEventRecord(st.slot_full[full], st.copy_s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.comp_s, st.slot_full[full], 0);
+    if (e == cudaSuccess) e = run_x(p, dx, st.raw, d_packed, st.acc, st.ws, accumulate, st.comp_s);
     if (e == cudaSuccess) e = cudaEventRecord(st.slot_free[slot], st.comp_s);
-    if (e == cudaSuccess && j.closes) {
+    if (b && e == cudaSuccess) e = cudaEventRecord(st.slot_free[slot + 1], st.comp_s);
+    if (b && e == cudaSuccess) e = cudaEventRecord(j.ev_done, st.comp_s);   // the first job: X stage done
+    Job& jl = last;
+    if (e == cudaSuccess && jl.closes) {
         if (sums) {
-            e = cudaMemcpyAsync(j.desc.host_vis, st.acc, vis_bytes(j.desc), cudaMemcpyDeviceToHost, st.comp_s);
+            e = cudaMemcpyAsync(jl.desc.host_vis, st.acc, vis_bytes(jl.desc), cudaMemcpyDeviceToHost, st.comp_s);
         } else {
             // Fig. 1: read out and divide by the update count (the next job's overwrite resets).
             // The dump buffer must have reached the host from the previous dump first.
             if (st.out_pending) e = cudaStreamWaitEvent(st.comp_s, st.ev_out, 0);
             if (e == cudaSuccess) {
-                const corr_status cs = corr_dump(reinterpret_cast<corr_plan>(&p), st.acc, (int)j.n_accum,
+                const corr_status cs = corr_dump(reinterpret_cast<corr_plan>(&p), st.acc, (int)jl.n_accum,
                                                  st.d.d_delays, st.d.d_freqs, st.phasor, st.dumpbuf, 0, st.comp_s);
                 if (cs != CORR_OK) e = cudaErrorLaunchFailure;
             }
-            if (e == cudaSuccess && j.desc.host_vis) {
+            if (e == cudaSuccess && jl.desc.host_vis) {
                 e = cudaEventRecord(st.ev_dumped, st.comp_s);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(st.out_s, st.ev_dumped, 0);
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(j.desc.host_vis, st.dumpbuf, (size_t)p.n_baselines * p.n_chan * 8,
+                    e = cudaMemcpyAsync(jl.desc.host_vis, st.dumpbuf, (size_t)p.n_baselines * p.n_chan * 8,
                                         cudaMemcpyDeviceToHost, st.out_s);
                 if (e == cudaSuccess) e = cudaEventRecord(st.ev_out, st.out_s);
                 if (e == cudaSuccess) {
                     st.out_pending = true;
                     // the job is done when its dump is in host memory
-                    return cudaEventRecord(j.ev_done, st.out_s);
+                    return cudaEventRecord(jl.ev_done, st.out_s);
                 }
             }
         }
     }
-    if (e == cudaSuccess) e = cudaEventRecord(j.ev_done, st.comp_s);
+    if (e == cudaSuccess) e = cudaEventRecord(jl.ev_done, st.comp_s);
     return e;
 }
 
@@ -450,6 +479,27 @@ bool pick_next(corr_server_s* S, std::deque<uint64_t>::iterator* pick) {
     return found && copy_fits(S, packed_bytes(S->jobs[**pick].desc));
 }
 
+// The queued job that can join a picked stream job in one X stage (issue_stream with `b`): the
+// stream's next job, already queued, in the adjacent ring slot (no wrap), the picked job not
+// ending the interval, the later slot free on the device and both copies within the budget.
+// Called with the lock held; returns the partner's queue position or end().
+std::deque<uint64_t>::iterator pair_partner(corr_server_s* S, std::deque<uint64_t>::iterator pick) {
+    const Job& j = S->jobs[*pick];
+    const StreamState* st = j.st;
+    const int R = st->d.ring_slots;
+    if (!st->pairable || j.closes || (int)(j.seq % R) + 1 >= R) return S->queue.end();
+    for (auto it = std::next(pick); it != S->queue.end(); ++it) {
+        const Job& c = S->jobs[*it];
+        if (!c.stream_job || c.st != st) continue;
+        // a stream's jobs queue in submission order, so this is job seq + 1
+        if (c.seq != j.seq + 1) return S->queue.end();
+        const bool free = c.seq < R || cudaEventQuery(st->slot_free[(int)(c.seq % R)]) != cudaErrorNotReady;
+        if (!free || !copy_fits(S, packed_bytes(j.desc) + packed_bytes(c.desc))) return S->queue.end();
+        return it;
+    }
+    return S->queue.end();
+}
+
 void dispatcher_loop(corr_server_s* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lock(S->mu);
@@ -470,15 +520,30 @@ void dispatcher_loop(corr_server_s* S) {
         const uint64_t id = *pick;
         Job& j = S->jobs[id];
         cudaError_t e = cudaSuccess;
+        Job* b = nullptr;   // a stream job's partner in one X stage (pair_partner)
         if (j.stream_job) {
-            S->queue.erase(pick);
+            const auto partner = pair_partner(S, pick);
+            const uint64_t id_b = partner != S->queue.end() ? *partner : 0;
+            S->queue.erase(pick);   // invalidates `partner`
+            if (id_b) {
+                S->queue.erase(std::find(S->queue.begin(), S->queue.end(), id_b));
+                b = &S->jobs[id_b];
+            }
             j.state = kRunning;
             j.t_start = now_s();
             StreamState* st = j.st;
             j.copy_bytes = packed_bytes(j.desc);
             S->copy_inflight += j.copy_bytes;
+            if (b) {
+                b->state = kRunning;
+                b->t_start = j.t_start;
+                b->copy_bytes = packed_bytes(b->desc);
+                S->copy_inflight += b->copy_bytes;
+                j.h_status_pair = b->h_status;
+                S->stats.coalesced += 2;
+            }
             lock.unlock();
-            e = issue_stream(S, j, *st);
+            e = issue_stream(S, j, *st, b);
             lock.lock();
         } else {
             size_t off;
@@ -503,10 +568,12 @@ void dispatcher_loop(corr_server_s* S) {
         if (e == cudaSuccess) {
             S->running.push_back(id);
             S->copying.push_back(id);
+            if (b) {
+                S->running.push_back(b->id);
+                S->copying.push_back(b->id);
+            }
         }
         if (e != cudaSuccess) {
-            S->copy_inflight -= j.copy_bytes;
-            j.copy_bytes = 0;
             // nothing of this job is queued behind a failed call that we can rely on; mark it
             // failed once its stream has drained the calls that were accepted
             cudaStreamSynchronize(j.stream_job ? j.st->comp_s : S->streams[j.stream]);
@@ -514,15 +581,20 @@ void dispatcher_loop(corr_server_s* S) {
                 cudaStreamSynchronize(j.st->copy_s);
                 cudaStreamSynchronize(j.st->out_s);
             }
-            j.state = kFailed;
-            j.final_status = CORR_ECUDA;
-            j.t_done = now_s();
-            if (j.holds_arena) {
-                S->arena->release(j.off, j.bytes);
-                j.holds_arena = false;
+            for (Job* f : {&j, b}) {
+                if (!f) continue;
+                S->copy_inflight -= f->copy_bytes;
+                f->copy_bytes = 0;
+                f->state = kFailed;
+                f->final_status = CORR_ECUDA;
+                f->t_done = now_s();
+                if (f->holds_arena) {
+                    S->arena->release(f->off, f->bytes);
+                    f->holds_arena = false;
+                }
+                if (f->stream_job) f->st->n_retired++;
+                S->stats.failed++;
             }
-            if (j.stream_job) j.st->n_retired++;
-            S->stats.failed++;
             S->cv_done.notify_all();
         }
     }
@@ -558,7 +630,9 @@ void completer_loop(corr_server_s* S) {
             if (q != cudaSuccess) {
                 j.state = kFailed;
                 j.final_status = CORR_ECUDA;
-            } else if (j.h_status[0] != 0) {
+            } else if ((j.h_status_pair ? j.h_status_pair : j.h_status)[0] != 0) {
+                // (a job issued with its stream's next one reads that job's words, which stay
+                // valid: the partner's completion event follows this one's)
                 j.state = kFailed;
                 j.final_status = CORR_ETIMEOUT;   // a bounded device wait gave up
             } else {

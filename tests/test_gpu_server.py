@@ -326,3 +326,37 @@ def test_earliest_deadline_first_issue_order():
     for tag in specs:
         assert srv.close_stream(tag) == corr.OK
     srv.close()
+
+
+@pytest.mark.parametrize("n,c,t,bits,ring", [(64, 12, 300, 8, 4), (256, 2, 70, 4, 4), (96, 5, 130, 4, 3)])
+def test_open_stream_coalesced_jobs_equal_oracle(n, c, t, bits, ring):
+    # jobs queued while the dispatcher is paused run in pairs of adjacent ring slots (one X stage
+    # over both jobs' samples, packed feed or planes); the interval sums still equal the
+    # correlation of the concatenated samples, and every job completes with its own status
+    from paper_0906_1887_gb300 import corr
+    k = 5
+    packs = _stream_jobs(7300 + n, 2 * k, n, c, t, bits)
+    host_in = [torch.from_numpy(p.reshape(-1).view(np.uint8)).pin_memory() for p in packs]
+    P = n * (n + 1) // 2
+    outs = [torch.full((c, P, 2), -1, dtype=torch.int64).pin_memory() for _ in range(2)]
+    srv = corr.Server(256 * MiB, n_streams=2, flags=corr.SERVER_START_PAUSED)
+    srv.open_stream(11, n, c, t, bits, ring_slots=ring, jobs_per_dump=k)
+    ids = []
+    for m in range(2 * k):
+        closes = (m + 1) % k == 0
+        ids.append(srv.submit(n, c, t, bits, host_in[m], outs[m // k] if closes else None, stream_tag=11))
+    srv.resume()
+    for m, jid in enumerate(ids):
+        st, r = srv.wait(jid, 60.0)
+        assert st == corr.OK, (m, st, corr.last_error())
+        assert r.closed_interval == int((m + 1) % k == 0)
+        srv.release(jid)
+    for iv in range(2):
+        allp = np.concatenate([packs[iv * k + m].reshape(t, c, -1) for m in range(k)])
+        assert np.array_equal(outs[iv].numpy(), oracle.xcorr_int(allp, n, c, k * t, bits)), iv
+    s = srv.stats()
+    # the first interval's jobs 0+1 and (with 4 slots) 2+3 pair up for certain: their slots are
+    # free from the start (the closing job 4 runs alone, and a pair never wraps around the ring)
+    assert s["coalesced"] >= (4 if ring >= 4 else 2) and s["completed"] == 2 * k and s["failed"] == 0, s
+    assert srv.close_stream(11) == corr.OK
+    srv.close()
