@@ -84,7 +84,10 @@ typedef enum {
 
 typedef struct corr_plan_s *corr_plan;   /* opaque, owned by the library */
 
-/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH; CORR_VERSION is the value of the
+ * header a caller was built with.  0.2.0: corr_server_stats gained `coalesced` and the operand
+ * feeds CORR_OPERANDS_PACKED_F8. */
+#define CORR_VERSION 200
 int corr_version(void);
 
 /* Last error message of the calling thread ("" if none).  Valid until the next call

@@ -52,7 +52,7 @@ using namespace corr;
 
 extern "C" {
 
-int corr_version(void) { return 100; }  // 0.1.0
+int corr_version(void) { return CORR_VERSION; }  // 0.2.0
 
 const char* corr_last_error(void) { return g_msg; }
 

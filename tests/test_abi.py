@@ -31,7 +31,8 @@ def test_binding_covers_header():
 def test_host_only_calls():
     from paper_0906_1887_gb300 import corr
     import numpy as np
-    assert corr.version() >= 100
+    text = open(os.path.join(ROOT, "include", "corr.h")).read()
+    assert corr.version() == int(re.search(r"#define CORR_VERSION (\d+)", text).group(1))
     v = np.array([[3, -4], [10, 0]], dtype=np.int64)
     assert corr.average_host(v, 4).tolist() == [[0.75, -1.0], [2.5, 0.0]]
 
